@@ -1,0 +1,117 @@
+"""Pins of the oracle's 1D overdamped dynamics and quadrature (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import _clib, estimators as est, quadrature as quad
+from paper_1105_4840_gb300 import inputs
+
+
+def test_quadrature_closed_forms():
+    # a = 0: pure harmonic trap, F = -kT ln sqrt(2 pi kT / k), <x> = lambda, var = kT/k
+    for k in (5.0, 20.0):
+        assert quad.od1d_free_energy(0.3, k, a=0.0) == pytest.approx(
+            -math.log(math.sqrt(2 * math.pi / k)), rel=1e-10)
+        m, v = quad.od1d_moments(0.3, k, a=0.0)
+        assert m == pytest.approx(0.3, abs=1e-10)
+        assert v == pytest.approx(1.0 / k, rel=1e-8)
+    # Gaussian chain with a vanishing trap: normalised density, Maxwell mean
+    s2 = 0.7
+    assert quad.gaussian_chain_free_energy(1.0, 1e-12, s2, 1.0) == pytest.approx(0.0, abs=1e-8)
+    assert quad.gaussian_chain_mean_x(1.0, 1e-12, s2, 1.0) == pytest.approx(
+        2 * math.sqrt(s2) * math.sqrt(2 / math.pi), rel=1e-8)
+
+
+def test_quadrature_thermodynamic_identity():
+    """dF/dlambda = k (lambda - <x>_lambda): the derivative of the quadrature
+    free energy against the independently integrated mean."""
+    k, h = 20.0, 1e-5
+    for lam in (-1.2, -0.3, 0.0, 0.8):
+        dF = (quad.od1d_free_energy(lam + h, k) - quad.od1d_free_energy(lam - h, k)) / (2 * h)
+        m, _ = quad.od1d_moments(lam, k)
+        assert dF == pytest.approx(k * (lam - m), abs=1e-6)
+
+
+def test_euler_maruyama_harmonic_stationary_variance():
+    """a = 0: the discrete OU chain x' = x - k (x - lambda) dt + sqrt(2 dt) xi
+    has stationary variance 2 dt / (1 - (1 - k dt)^2) exactly."""
+    k, dt, lam = 20.0, 1e-3, 0.4
+    xs = []
+    for uid in range(8):
+        x, _ = _clib.od1d_run(0.0, lam, k, 1.0, 1.0, dt, 200000, 2000, 10, 3, uid, lam)
+        xs.append(x)
+    x = np.concatenate(xs)
+    want = 2 * dt / (1 - (1 - k * dt) ** 2)
+    assert abs(x.mean() - lam) < 0.01
+    assert x.var() == pytest.approx(want, rel=0.03)
+
+
+def _od1d_config_samples():
+    w = inputs.od1d_workload()
+    r = w["run"]
+    samples = []
+    for i, lam in enumerate(r.lambdas):
+        rows = []
+        for rep in range(r.replicas):
+            uid = i * r.replicas + rep
+            x, _ = _clib.od1d_run(w["a"], lam, r.k, r.kT, r.gamma, r.dt, r.n_steps, r.n_equil,
+                                  r.stride, r.seed, uid, w["x0"])
+            rows.append(x)
+        samples.append(np.array(rows))
+    return w, samples
+
+
+def test_od1d_workload_matches_quadrature():
+    """The 1D workload (21 windows, 8 replicas, 2e4 steps): the JE profile is
+    within 0.1 kT of F(lambda_j, k) - F(lambda_1, k) by quadrature, the full
+    path is ~0 by symmetry, and Eq. (14) matches its quadrature Riemann sum."""
+    w, samples = _od1d_config_samples()
+    r = w["run"]
+    prof = est.free_energy_profile(samples, r.lambdas, r.k, r.kT)
+    exact = np.array([quad.od1d_free_energy(l, r.k) for l in r.lambdas])
+    exact -= exact[0]
+    assert np.max(np.abs(prof["dF_JE"] - exact)) < 0.1
+    assert abs(exact[-1]) < 1e-8
+    means = np.array([quad.od1d_moments(l, r.k)[0] for l in r.lambdas])
+    riemann = np.concatenate([[0.0], np.cumsum(r.k * np.diff(r.lambdas) * (r.lambdas[:-1] - means[:-1]))])
+    assert np.max(np.abs(prof["dF_fluct"] - riemann) / np.maximum(prof["se_fluct"], 1e-9)) < 4.0
+    # per-window means agree with the quadrature
+    assert np.max(np.abs(prof["mean_x"] - means)) < 0.02
+
+
+def test_single_step_identities_eq5_eq6_eq7():
+    """Eq. (5), Eq. (6) and the bounds Eq. (7) for one window of the double
+    well: sampled averages against the quadrature dF(lambda, k) = F(lambda,k) - F_0."""
+    k, lam = 2.0, 0.5
+    x1 = np.concatenate([_clib.od1d_run(2.0, lam, k, 1.0, 1.0, 1e-3, 200000, 2000, 20, 11, u, 0.5)[0]
+                         for u in range(8)])
+    x0 = np.concatenate([_clib.od1d_run(2.0, 0.0, 0.0, 1.0, 1.0, 1e-3, 400000, 2000, 20, 12, u, -1.0)[0]
+                         for u in range(8)])
+    dF = quad.od1d_free_energy(lam, k) - quad.od1d_unbiased_free_energy()
+    eq5 = math.log(np.mean(np.exp(0.5 * k * (x1 - lam) ** 2)))
+    eq6 = -math.log(np.mean(np.exp(-0.5 * k * (x0 - lam) ** 2)))
+    assert eq5 == pytest.approx(dF, abs=0.05)
+    assert eq6 == pytest.approx(dF, abs=0.05)
+    lower = np.mean(0.5 * k * (x1 - lam) ** 2)
+    upper = np.mean(0.5 * k * (x0 - lam) ** 2)
+    assert lower <= dF <= upper
+
+
+def test_total_work_identity_eq10():
+    """Eq. (10): <exp(-beta W_total)> over independent ensembles x_0..x_s is 1,
+    i.e. the x_0 factor, the JE factor of Eq. (12) and the x_s factor of
+    Eq. (5) multiply to one."""
+    k = 2.0
+    lam = np.array([-0.6, -0.2, 0.2, 0.6])
+    runs = []
+    for i, l in enumerate(lam):
+        runs.append(np.concatenate([_clib.od1d_run(2.0, l, k, 1.0, 1.0, 1e-3, 200000, 2000, 20, 21,
+                                                   100 * i + u, l)[0] for u in range(8)]))
+    x0 = np.concatenate([_clib.od1d_run(2.0, 0.0, 0.0, 1.0, 1.0, 1e-3, 400000, 2000, 20, 22, u, -1.0)[0]
+                         for u in range(8)])
+    ln_first = math.log(np.mean(np.exp(-0.5 * k * (x0 - lam[0]) ** 2)))
+    ln_last = math.log(np.mean(np.exp(0.5 * k * (runs[-1] - lam[-1]) ** 2)))
+    prof = est.free_energy_profile([r[None, :] for r in runs], lam, k, 1.0)
+    ln_total = ln_first - prof["dF_JE"][-1] + ln_last
+    assert abs(ln_total) < 0.06

@@ -1,0 +1,323 @@
+"""Benchmark of the parallel pulling protocol hot path on GB300.
+
+One step = the whole PPP workload of the 104-bead chain: 21 windows x 32
+replicas, 4e5 BAOAB steps each (0.4 ns at 1 fs), x recorded every 100 steps,
+then the FP64 reductions into dF_JE / dF_fluct / dF_G / dF_com.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is replica-steps/s of the whole job
+with inputs resident on the device; `e2e` is the same metric through the C
+ABI with host buffers (system upload, run, result download inside the timed
+region); `roofline` reports the chain kernel against the FP32 ALU peak;
+`cpu_baseline` times the FP64 oracle on a bounded sample on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "chain104_ppp"
+N_BEADS = 104
+
+
+def flops_per_replica_step(n: int) -> int:
+    """Algorithmic FP32 flops of one BAOAB step of an n-bead chain (FMA = 2):
+    36 per nonbonded pair (|i-j| >= 3), 20 per bond, 60 per angle, 110 per
+    three-term dihedral, 33 per bead for the B, A, O, A, B updates."""
+    pairs = n * (n - 1) // 2 - (2 * n - 3)
+    return 36 * pairs + 20 * (n - 1) + 60 * (n - 2) + 110 * (n - 3) + 33 * n
+
+
+def _workload(n_steps=None):
+    from paper_1105_4840_gb300 import inputs
+
+    w = inputs.chain_workload()
+    if n_steps is not None:
+        w["run"].n_steps = n_steps
+        w["run"].n_equil = n_steps // 10
+    return w
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle samples during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def _ncu_traffic():
+    """DRAM bytes per chain-kernel launch from the committed ncu summary, if current."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "chain_kernel_traffic.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return None
+
+
+def cpu_baseline(budget_s=12.0, n_steps=200):
+    """The FP64 oracle as it stands, on the host cores: replicas of the
+    104-bead chain (windows round-robin), one thread per core."""
+    import concurrent.futures as cf
+
+    from oracle import _clib
+
+    w = _workload()
+    p, start, run = w["params"], w["start"], w["run"]
+    ch = _clib.Chain(p)
+    cores = os.cpu_count() or 1
+    lam = run.lambdas
+
+    def one(uid):
+        ch.run(start, lam[uid % lam.size], run.k, run.kT, run.dt, run.gamma, n_steps, n_steps, 1,
+               run.seed, uid)
+        return n_steps
+
+    done = 0
+    t0 = time.perf_counter()
+    uid = 0
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        while time.perf_counter() - t0 < budget_s:
+            futs = [ex.submit(one, uid + i) for i in range(cores)]
+            uid += cores
+            done += sum(f.result() for f in futs)
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": "replica-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{uid} replicas x {n_steps} BAOAB steps of the 104-bead chain (FP64, "
+                      f"{cores} threads, {el:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(budget_s=2.0)
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(budget_s=8.0))
+    v = statistics.median([b["value"] for b in vals])
+    line = {"impl": "reference", "metric": "replica-steps/s", "value": v, "unit": "replica-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * 21 * 32 * 400000 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "oracle": "FP64 CPU, bounded sample per step"},
+            "cpu_baseline": {**vals[-1], "value": v},
+            "e2e": {"value": v, "unit": "replica-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--md-steps", type=int, default=400000, help="BAOAB steps per window (workload: 4e5)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from __graft_entry__ import build
+
+    if rank == 0 or world == 1:
+        build()
+    if dist is not None:
+        dist.barrier()
+    from paper_1105_4840_gb300 import pmf
+
+    stream = torch.cuda.current_stream()
+    pmf.pmf_set_stream(stream.cuda_stream)
+    w = _workload(args.md_steps)
+    p, start, run = w["params"], w["start"], w["run"]
+    s, R = run.lambdas.size, run.replicas
+    n_rep = s * R
+    uid_base = rank * n_rep
+    sysh = pmf.pmf_create_system_chain([p], [start])
+    rr = pmf.pmf_run_prepare(sysh, run.lambdas, pmf.make_params(run, uid_base=uid_base))
+    replica_steps = n_rep * run.n_steps
+    chunks = math.ceil(run.n_steps / 100000)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one_step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        rr.launch()
+        if ev is not None:
+            ev[1].record(stream)
+        rr.reduce()
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        one_step()
+    torch.cuda.synchronize()
+    rr.wait()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))  # L2 flush (256 MB) between timed steps, outside the events
+        one_step(evs[i])
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks.stop()
+    rr.wait()
+    res = rr.free_energy()
+    sim_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    red_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    step_ms = [a + b for a, b in zip(sim_ms, red_ms)]
+    t_step = sum(step_ms) / len(step_ms)
+    if dist is not None:
+        t = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    value = world * replica_steps / (t_step / 1000.0)
+
+    # end to end through the C ABI with host buffers: system upload, run, results
+    e2e_times = []
+    h2d = d2h = 0
+    for _ in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sys2 = pmf.pmf_create_system_chain([p], [start])
+        r2 = pmf.pmf_run_windows(sys2, run.lambdas, pmf.make_params(run, uid_base=uid_base))
+        out = r2.free_energy()
+        e2e_times.append(time.perf_counter() - t0)
+        h2d = 8 * (p.n * 7 + p.n * 6 + p.n * 3) + 4 + 8 * s * 1 + 8 * 4 * s
+        d2h = 8 * len(out) * s + 4
+        r2.close()
+        sys2.close()
+    e2e_value = world * replica_steps / statistics.median(e2e_times)
+
+    if rank != 0:
+        return
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    clk = clocks.summary()
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
+    chain_launch_ms = sum(sim_ms) / (len(sim_ms) * chunks)
+    flops_launch = n_rep * min(run.n_steps, 100000) * flops_per_replica_step(N_BEADS)
+    achieved = flops_launch / (chain_launch_ms / 1000.0) / 1e12
+    traffic = _ncu_traffic()
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops,
+            "traffic": (traffic or {}).get("dram_bytes_per_launch"),
+            "kernel": "chain_kernel<float,4>",
+            "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
+            "frac_at_sampled_clock": (achieved / (sm_count * 256 * clk["sm_mhz"] * 1e6 / 1e12)
+                                      if clk.get("sm_mhz") else None),
+            "flops_per_replica_step": flops_per_replica_step(N_BEADS),
+            "launch_ms": chain_launch_ms}
+    ns_per_day = replica_steps * world / (t_step / 1000.0) * run.dt * 86400.0 / 1e3
+    line = {"metric": "replica-steps/s", "value": value, "unit": "replica-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "beads": N_BEADS, "windows": s, "replicas_per_window": R,
+                       "md_steps_per_window": run.n_steps, "dt_ps": run.dt, "sample_stride": run.stride,
+                       "forces": "fp32", "reductions": "fp64", "parallelism": f"replicas x{world}",
+                       "l2": "256 MB flush between timed steps"},
+            "e2e": {"value": e2e_value, "unit": "replica-steps/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * (chunks + 3),
+            "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+                       "reasons": clk.get("reasons")},
+            "roofline": roof,
+            "aggregate_ns_per_day": ns_per_day,
+            "reduction_ms": sum(red_ms) / len(red_ms),
+            "dF_JE_end": float(res["dF_JE"][-1]), "dF_fluct_end": float(res["dF_fluct"][-1]),
+            "dF_com_end": float(res["dF_com"][-1]), "uncertainty_end": float(res["uncertainty"][-1])}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,251 @@
+/*
+ * pmf.h -- C ABI of the GB300 (sm_103a) parallel step-wise pulling library.
+ *
+ * The library computes free-energy differences with the parallel pulling
+ * protocol (PPP) of Ngo, "A Parallel-pulling Protocol for Free Energy
+ * Evaluation" (arXiv 1105.4840): s independent restrained simulations, one
+ * per window lambda_1..lambda_s, each started from the same state x_o and
+ * relaxed for tau_i (Sec. III (ii)); the recorded reaction-coordinate
+ * samples x_i give the step-wise work of Eq. (9), the Jarzynski estimate of
+ * Eq. (12), the Gaussian estimate of Eq. (13), the alternative formula of
+ * Eq. (14) and their combination (Sec. IV B, Sec. V).
+ *
+ * Conventions
+ *   - Every call returns a pmf_status; no C++ exception crosses the ABI.
+ *     On failure pmf_last_error() returns a thread-local message.
+ *   - Input arrays are host pointers unless stated, read during the call and
+ *     copied; the caller keeps ownership.  Output buffers are caller-owned
+ *     host memory unless stated.
+ *   - Handles are not thread-safe; use one handle per thread or lock.
+ *   - All GPU work runs on the library stream (pmf_set_stream); calls that
+ *     return host results synchronise that stream.
+ *   - There is no CPU fallback: without a CUDA device every compute call
+ *     fails with PMF_ECUDA.
+ */
+#ifndef PMF_H
+#define PMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PMF_OK = 0,
+    PMF_EINVAL = 1,   /* bad argument (sizes, monotone lambda, capacity ...)   */
+    PMF_ENOMEM = 2,   /* device or host allocation failed                      */
+    PMF_ECUDA = 3,    /* CUDA runtime error or no device                       */
+    PMF_ENUMERIC = 4, /* a trajectory became non-finite (device error flag)    */
+    PMF_ETIMEOUT = 5, /* the run exceeded pmf_run_params.timeout_s             */
+    PMF_ESTATE = 6    /* call out of order (e.g. results of an unfinished run) */
+} pmf_status;
+
+enum { PMF_MODEL_1D_DOUBLEWELL = 0, PMF_MODEL_CHAIN = 1 };
+enum { PMF_FP32 = 0, PMF_FP64 = 1 };
+
+typedef struct pmf_system pmf_system; /* opaque; device copy of the system    */
+typedef struct pmf_run pmf_run;       /* opaque; device x samples of one run  */
+
+/*
+ * System description: H_o of Sec. II plus the trap on the reaction
+ * coordinate x (Eq. (3)).  For PMF_MODEL_CHAIN, x = |r_{N-1} - r_0| (the
+ * end-to-end distance of a bead chain standing in for the deca-alanine of
+ * Sec. IV) and
+ *   H_o = sum_bonds bond_k/2 (r - bond_r0)^2
+ *       + sum_angles angle_k/2 (theta - angle_theta0)^2
+ *       + sum_dihedrals sum_{n=1..3} K_n [1 + cos(n phi - delta_n)]
+ *       + sum_{|i-j|>=3} 4 eps_ij [(s_ij/r)^12 - (s_ij/r)^6] + coulomb_k q_i q_j / r
+ * with s_ij = (sigma_i + sigma_j)/2 and eps_ij = sqrt(eps_i eps_j).
+ * For PMF_MODEL_1D_DOUBLEWELL, H_o = dw_a (x^2 - 1)^2 in units of kT.
+ */
+typedef struct {
+    int model;                  /* PMF_MODEL_*                                   */
+    int precision;              /* chain integration: PMF_FP32 or PMF_FP64       */
+    /* chain model (concatenated over chains; bead b of chain c is row
+       offset_c + b with offset_c = sum of n_beads of the chains before c)     */
+    int n_chains;               /* >= 1                                          */
+    const int *n_beads;         /* [n_chains], each 4 .. 1024                    */
+    const double *sigma;        /* [sum n_beads] nm                              */
+    const double *epsilon;      /* [sum n_beads] kJ/mol (>= 0)                   */
+    const double *charge;       /* [sum n_beads] e                               */
+    const double *mass;         /* [sum n_beads] amu (> 0)                       */
+    const double *dih_k;        /* [sum n_beads][3] K_1..K_3 of the dihedral
+                                   starting at that bead (ignored for the last 3) */
+    const double *dih_phase;    /* [sum n_beads][3] delta_n, each 0 or pi        */
+    const double *pos0;         /* [sum n_beads][3] start state x_o (nm)         */
+    double bond_k, bond_r0;     /* kJ/mol/nm^2, nm                               */
+    double angle_k;             /* kJ/mol/rad^2 (0 disables angles)              */
+    double angle_theta0;        /* rad                                           */
+    double coulomb_k;           /* kJ mol^-1 nm e^-2                             */
+    int nonbonded;              /* 0 disables the LJ and Coulomb terms           */
+    /* 1D model */
+    double dw_a;                /* U(x) = dw_a (x^2 - 1)^2                       */
+    double x0;                  /* start state x_o                               */
+} pmf_system_desc;
+
+/* Build the device copy of a system.  *out receives a library-owned handle
+ * (free with pmf_destroy_system).  PMF_EINVAL on inconsistent sizes or
+ * values; PMF_ECUDA without a device. */
+pmf_status pmf_create_system(const pmf_system_desc *desc, pmf_system **out);
+void pmf_destroy_system(pmf_system *sys);
+
+/*
+ * Run parameters: the paper's problem statement (Sec. III, Sec. IV B):
+ * trap stiffness k, temperature (as kT), relaxation time per window
+ * (n_steps * dt, or n_steps_per_window[i] * dt), plus the sampling of x
+ * (Sec. IV A: x recorded every 0.1 ps) and the Langevin settings.
+ * Chain: BAOAB Langevin with friction gamma (1/ps).  1D: overdamped
+ * Euler-Maruyama x += F dt/gamma + sqrt(2 kT dt/gamma) xi.
+ * Replica uid of (window w, replica r) = uid_base + w * replicas + r; the
+ * Langevin noise of a replica is Philox4x32-10 with key seed and counter
+ * (bead, uid, step, 0); initial velocities use counter (bead, uid, 0, 1).
+ */
+typedef struct {
+    double k;                   /* trap stiffness (energy / length^2)            */
+    double kT;                  /* k_B T in the system's energy unit             */
+    double dt;                  /* time step                                     */
+    double gamma;               /* friction                                      */
+    int64_t n_steps;            /* steps per window (used if the array is NULL)  */
+    const int64_t *n_steps_per_window; /* optional [n_windows]                   */
+    int64_t n_equil;            /* steps discarded before sampling; < 0: 10 %    */
+    int sample_stride;          /* steps between samples (>= 1)                  */
+    int replicas;               /* replicas per window (>= 1)                    */
+    uint64_t seed;              /* Philox key                                    */
+    uint32_t uid_base;          /* first replica uid (sharding across processes) */
+    int chain;                  /* chain index of a multi-chain system           */
+    double timeout_s;           /* wall-clock limit of pmf_run_wait; 0: none     */
+} pmf_run_params;
+
+/* PPP of Sec. III (ii): allocate the run, upload lambda[n_windows] (strictly
+ * monotone, n_windows >= 2), launch every window x replica simulation from
+ * the system's start state x_o, and wait.  Equivalent to pmf_run_prepare +
+ * pmf_run_launch + pmf_run_wait.  *out is library-owned (pmf_destroy_run);
+ * it is set even when the run fails with PMF_ENUMERIC / PMF_ETIMEOUT so the
+ * caller can inspect or destroy it. */
+pmf_status pmf_run_windows(pmf_system *sys, const double *lambda, int n_windows,
+                           const pmf_run_params *p, pmf_run **out);
+
+/* The three phases of pmf_run_windows.  prepare allocates and uploads (the
+ * only host-to-device traffic); launch enqueues the simulation on the
+ * library stream and returns at once; wait blocks until it finishes (or
+ * timeout_s passes: PMF_ETIMEOUT) and reports PMF_ENUMERIC if the device
+ * error flag was raised.  launch may be called again on a finished run to
+ * repeat it from x_o with the same streams (identical results). */
+pmf_status pmf_run_prepare(pmf_system *sys, const double *lambda, int n_windows,
+                           const pmf_run_params *p, pmf_run **out);
+pmf_status pmf_run_launch(pmf_run *run);
+pmf_status pmf_run_wait(pmf_run *run);
+void pmf_destroy_run(pmf_run *run);
+
+/* Shape of a run's sample store: x[w][r][t], t fastest; window w holds
+ * replicas * samples_per_window[w] floats starting at sample_offset[w]. */
+typedef struct {
+    int n_windows;
+    int replicas;
+    int64_t total_samples;
+    int64_t samples_per_window[1024];
+    int64_t sample_offset[1024];
+} pmf_run_info;
+pmf_status pmf_get_run_info(const pmf_run *run, pmf_run_info *info);
+
+/* Copy the recorded x samples (FP32, layout of pmf_run_info) to the host
+ * buffer out[capacity].  If capacity is too small: PMF_EINVAL and
+ * *n_written = the required count. */
+pmf_status pmf_x_samples(const pmf_run *run, float *out, size_t capacity, size_t *n_written);
+
+enum { PMF_WORK_PER_WINDOW_INCREMENT = 0, PMF_WORK_PAIRED_CUMULATIVE = 1 };
+/* Work samples of Eq. (9), FP64, computed on the GPU:
+ *   PER_WINDOW_INCREMENT: w_i = k/2 (lambda_{i+1} - lambda_i)(lambda_{i+1} + lambda_i - 2 x_i)
+ *     for windows i = 0..s-2, layout [i][r][t] (the sample layout without
+ *     the last window);
+ *   PAIRED_CUMULATIVE: W_j(r, t) = sum_{i < j} w_i(x_i[r][t]), the work of
+ *     the force-versus-extension curve formed by replica r, sample t in every
+ *     window, layout [j = 1..s-1][r][t]; needs equal samples per window.
+ * Capacity handling as for pmf_x_samples. */
+pmf_status pmf_work_samples(const pmf_run *run, int mode, double *out, size_t capacity,
+                            size_t *n_written);
+
+/*
+ * Free-energy estimates (all energies in the system's energy unit), per
+ * profile point j = 0..s-1 (value at lambda_1 is 0), computed on the GPU in
+ * FP64 from the x samples:
+ *   dF_JE       Eq. (12): sum_{i<j} -kT ln <exp(-w_i/kT)>_i  (the average over
+ *               all combinations of samples factorises over the independent
+ *               windows; max-shifted log-sum-exp with compensated sums)
+ *   dF_fluct    Eq. (14): sum_{i<j} k D_i (lambda_i - <x_i>), D_i = lambda_{i+1} - lambda_i
+ *   dF_G        Eq. (13): sum_{i<j} [k D_i^2/2 (1 - gamma_i^2) + k D_i (lambda_i - <x_i>)]
+ *   dF_com      (dF_JE + dF_fluct)/2, uncertainty (dF_JE - dF_fluct)/2 (Sec. V)
+ *   se_JE, se_fluct  delete-one-replica jackknife, variances summed over windows
+ *   var_ZW      sigma_W^2/Q + sigma_W^4/(2 kT^2 (Q-1)) (Sec. IV A), Q = min_i n_i
+ *   W_mean      <W_mech> = sum_{i<j} <w_i> (Fig. 3b)
+ *   acc_force   dF_fluct / (lambda_j - lambda_1), 0 at j = 0 (Fig. 4b)
+ * per window i: mean_x, var_x (divisor n), gamma2 = k var_x / kT (Eq. (13)).
+ * Any array pointer may be NULL; each non-NULL array holds >= n_windows.
+ */
+typedef struct {
+    int capacity;               /* length of every non-NULL array               */
+    double *lambda, *dF_JE, *dF_fluct, *dF_G, *dF_com, *uncertainty;
+    double *se_JE, *se_fluct, *var_ZW, *W_mean, *acc_force;
+    double *mean_x, *var_x, *gamma2;
+} pmf_free_energy_result;
+
+pmf_status pmf_free_energy(const pmf_run *run, pmf_free_energy_result *res);
+
+/* Enqueue the FP64 reductions behind pmf_free_energy on the library stream
+ * and return at once; the results stay in device memory until the next
+ * pmf_free_energy call copies them (without recomputing).  Needs a launched
+ * run (PMF_ESTATE otherwise). */
+pmf_status pmf_run_reduce(pmf_run *run);
+
+/* The same reduction on caller-supplied samples x (layout of pmf_run_info
+ * with `replicas` and samples_per_window[n_windows]); x is a host pointer
+ * (x_on_device = 0) or a device pointer (x_on_device = 1). */
+pmf_status pmf_free_energy_from_samples(const float *x, int x_on_device, const double *lambda,
+                                        int n_windows, int replicas,
+                                        const int64_t *samples_per_window, double k, double kT,
+                                        pmf_free_energy_result *res);
+
+/* Final state of every replica: pos/vel [window][replica][bead][3] (chain) or
+ * [window][replica] (1D, vel unused).  Capacity in doubles of each buffer. */
+pmf_status pmf_final_state(const pmf_run *run, double *pos, double *vel, size_t capacity,
+                           size_t *n_written);
+
+/* ---- kernel-level entry points used by the parity tests ---------------- */
+
+/* The integrator's Philox4x32-10 and Box-Muller on the GPU: blocks with
+ * counters (c0 + i, c1, c2, c3), key (seed lo, seed hi), i < n_blocks.
+ * raw[4 n_blocks] uint32 and normals[4 n_blocks] (FP32 as used by the FP32
+ * integrator) are host buffers; either may be NULL. */
+pmf_status pmf_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                      int n_blocks, uint32_t *raw, float *normals);
+
+/* Forces -grad H(lambda, x) of chain `chain` at positions pos[N][3] (host),
+ * evaluated by the integrator's own force phase in the system's precision;
+ * forces[N][3] host output. */
+pmf_status pmf_chain_forces(pmf_system *sys, int chain, const double *pos, double lambda,
+                            double k, double *forces);
+
+/* Host-side schedule of the nonbonded phase for a chain of N beads and NW
+ * warps per CTA (no GPU needed): the ring units each warp executes, as
+ * records of 6 ints (warp, I, J, t_begin, t_end, flags) in out[capacity];
+ * *n_written receives the record count.  Tiles are 32 beads except a last
+ * tile of 8, 16 or 32 (*padded receives the padded bead count).  PMF_EINVAL
+ * if capacity < 6 * records. */
+pmf_status pmf_chain_schedule(int N, int NW, int *out, size_t capacity, size_t *n_written, int *padded);
+
+/* Library stream: cudaStream_t passed as void* (NULL = legacy default). */
+pmf_status pmf_set_stream(void *stream);
+
+/* Thread-local description of the last failure ("" if none). */
+const char *pmf_last_error(void);
+
+/* Library version string. */
+const char *pmf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMF_H */

@@ -1,0 +1,603 @@
+// C ABI of libpmf: handles, argument checks, orchestration of the kernels.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/pmf.h"
+#include "internal.h"
+
+using namespace pmf;
+
+namespace {
+
+thread_local std::string g_err;
+cudaStream_t g_stream = nullptr;
+
+pmf_status fail(pmf_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+pmf_status cuda_fail(cudaError_t e, const char *where)
+{
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PMF_ENOMEM : PMF_ECUDA;
+}
+#define CK(call, where)                                          \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);      \
+    } while (0)
+
+pmf_status need_device()
+{
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) return fail(PMF_ECUDA, "no CUDA device available (libpmf has no CPU path)");
+    return PMF_OK;
+}
+
+template <typename T> cudaError_t upload(T **d, const T *h, size_t n)
+{
+    cudaError_t e = cudaMalloc(d, sizeof(T) * (n ? n : 1));
+    if (e != cudaSuccess) return e;
+    return n ? cudaMemcpy(*d, h, sizeof(T) * n, cudaMemcpyHostToDevice) : cudaSuccess;
+}
+
+}  // namespace
+
+struct pmf_system {
+    int model = 0, precision = 0;
+    std::vector<std::unique_ptr<ChainModel>> chains;
+    Od1dParams od;
+};
+
+struct pmf_run {
+    pmf_system *sys = nullptr;
+    int chain = 0, n_windows = 0, replicas = 0, stride = 1;
+    double k = 0, kT = 1, dt = 0, gamma = 1, timeout_s = 0;
+    unsigned long long seed = 0;
+    uint32_t uid_base = 0;
+    std::vector<double> lambda;
+    std::vector<long long> nsteps, nequil, off, tw;
+    long long total = 0, max_steps = 0;
+    double *d_lambda = nullptr;
+    long long *d_nsteps = nullptr, *d_nequil = nullptr, *d_off = nullptr, *d_tw = nullptr;
+    float *d_x = nullptr;
+    void *d_state = nullptr;
+    int *d_err = nullptr;
+    void *d_scratch = nullptr;
+    double *d_res = nullptr;
+    cudaEvent_t done = nullptr;
+    bool launched = false, finished = false, reduced = false;
+    size_t state_bytes = 0;
+    ~pmf_run()
+    {
+        if (launched && done) cudaEventSynchronize(done);  // kernels may still use the buffers
+        cudaFree(d_lambda);
+        cudaFree(d_nsteps);
+        cudaFree(d_nequil);
+        cudaFree(d_off);
+        cudaFree(d_tw);
+        cudaFree(d_x);
+        cudaFree(d_state);
+        cudaFree(d_err);
+        cudaFree(d_scratch);
+        cudaFree(d_res);
+        if (done) cudaEventDestroy(done);
+    }
+};
+
+extern "C" {
+
+const char *pmf_last_error(void) { return g_err.c_str(); }
+const char *pmf_version(void) { return "pmf-gb300 0.1 (sm_103a)"; }
+
+pmf_status pmf_set_stream(void *stream)
+{
+    g_stream = reinterpret_cast<cudaStream_t>(stream);
+    return PMF_OK;
+}
+
+pmf_status pmf_create_system(const pmf_system_desc *d, pmf_system **out)
+{
+    if (!d || !out) return fail(PMF_EINVAL, "pmf_create_system: null argument");
+    *out = nullptr;
+    auto sys = std::make_unique<pmf_system>();
+    sys->model = d->model;
+    sys->precision = d->precision;
+    if (d->model == PMF_MODEL_1D_DOUBLEWELL) {
+        if (!std::isfinite(d->dw_a) || !std::isfinite(d->x0)) return fail(PMF_EINVAL, "1D model: non-finite a or x0");
+        sys->od.a = d->dw_a;
+        sys->od.x0 = d->x0;
+        if (pmf_status s = need_device()) return s;
+        *out = sys.release();
+        return PMF_OK;
+    }
+    if (d->model != PMF_MODEL_CHAIN) return fail(PMF_EINVAL, "unknown model");
+    if (d->precision != PMF_FP32 && d->precision != PMF_FP64) return fail(PMF_EINVAL, "precision must be FP32 or FP64");
+    if (d->n_chains < 1 || !d->n_beads) return fail(PMF_EINVAL, "chain model: n_chains >= 1 and n_beads[] required");
+    if (!d->sigma || !d->epsilon || !d->charge || !d->mass || !d->dih_k || !d->dih_phase || !d->pos0)
+        return fail(PMF_EINVAL, "chain model: a per-bead array is null");
+    long long off = 0;
+    std::vector<ChainHost> hosts;
+    for (int c = 0; c < d->n_chains; ++c) {
+        const int N = d->n_beads[c];
+        if (N < 4 || N > 1024) return fail(PMF_EINVAL, "chain model: n_beads must be in [4, 1024]");
+        ChainHost h;
+        h.N = N;
+        auto take = [&](const double *src, int per) { return std::vector<double>(src + off * per, src + (off + N) * per); };
+        h.sigma = take(d->sigma, 1);
+        h.epsilon = take(d->epsilon, 1);
+        h.charge = take(d->charge, 1);
+        h.mass = take(d->mass, 1);
+        h.dih_k = take(d->dih_k, 3);
+        h.dih_phase = take(d->dih_phase, 3);
+        h.pos0 = take(d->pos0, 3);
+        for (int b = 0; b < N; ++b) {
+            if (!(h.mass[b] > 0) || !(h.epsilon[b] >= 0) || !std::isfinite(h.sigma[b]) || !std::isfinite(h.charge[b]))
+                return fail(PMF_EINVAL, "chain model: invalid mass / epsilon / sigma / charge");
+            for (int m = 0; m < 3; ++m) {
+                if (!std::isfinite(h.pos0[3 * b + m])) return fail(PMF_EINVAL, "chain model: non-finite start state");
+                const double ph = h.dih_phase[3 * b + m];
+                if (b + 3 < N && h.dih_k[3 * b + m] != 0.0 && std::fabs(ph) > 1e-9 && std::fabs(std::fabs(ph) - M_PI) > 1e-9)
+                    return fail(PMF_EINVAL, "chain model: dihedral phases must be 0 or pi");
+            }
+        }
+        h.bond_k = d->bond_k;
+        h.bond_r0 = d->bond_r0;
+        h.angle_k = d->angle_k;
+        h.angle_theta0 = d->angle_theta0;
+        h.coulomb_k = d->coulomb_k;
+        h.nonbonded = d->nonbonded;
+        if (!std::isfinite(h.bond_k) || !std::isfinite(h.bond_r0) || !std::isfinite(h.angle_k) ||
+            !std::isfinite(h.angle_theta0) || !std::isfinite(h.coulomb_k))
+            return fail(PMF_EINVAL, "chain model: non-finite force-field constant");
+        hosts.push_back(std::move(h));
+        off += N;
+    }
+    if (pmf_status s = need_device()) return s;
+    for (const ChainHost &h : hosts) {
+        auto m = std::make_unique<ChainModel>();
+        cudaError_t e = m->init(h, d->precision);
+        if (e != cudaSuccess) return cuda_fail(e, "pmf_create_system");
+        if (m->smem_bytes() > 227 * 1024) return fail(PMF_EINVAL, "chain too long for this precision (shared memory)");
+        sys->chains.push_back(std::move(m));
+    }
+    *out = sys.release();
+    return PMF_OK;
+}
+
+void pmf_destroy_system(pmf_system *sys) { delete sys; }
+
+pmf_status pmf_run_prepare(pmf_system *sys, const double *lambda, int n_windows, const pmf_run_params *p,
+                           pmf_run **out)
+{
+    if (!sys || !lambda || !p || !out) return fail(PMF_EINVAL, "pmf_run_prepare: null argument");
+    *out = nullptr;
+    if (n_windows < 2 || n_windows > 1024) return fail(PMF_EINVAL, "n_windows must be in [2, 1024]");
+    const double sgn = lambda[1] > lambda[0] ? 1.0 : -1.0;
+    for (int i = 0; i < n_windows; ++i) {
+        if (!std::isfinite(lambda[i])) return fail(PMF_EINVAL, "lambda must be finite");
+        if (i > 0 && !((lambda[i] - lambda[i - 1]) * sgn > 0)) return fail(PMF_EINVAL, "lambda must be strictly monotone");
+    }
+    if (!(p->k > 0) || !(p->kT > 0) || !(p->dt > 0) || !(p->gamma >= 0) || !std::isfinite(p->k))
+        return fail(PMF_EINVAL, "need k > 0, kT > 0, dt > 0, gamma >= 0");
+    if (sys->model == PMF_MODEL_1D_DOUBLEWELL && !(p->gamma > 0)) return fail(PMF_EINVAL, "1D model needs gamma > 0");
+    if (p->replicas < 1 || p->sample_stride < 1) return fail(PMF_EINVAL, "replicas >= 1 and sample_stride >= 1");
+    if (p->replicas > 65535 || (long long)n_windows * p->replicas > (1LL << 31) - 1)
+        return fail(PMF_EINVAL, "too many replicas (at most 65535 per window)");
+    if (sys->model == PMF_MODEL_CHAIN && (p->chain < 0 || p->chain >= (int)sys->chains.size()))
+        return fail(PMF_EINVAL, "chain index out of range");
+    auto run = std::make_unique<pmf_run>();
+    run->sys = sys;
+    run->chain = p->chain;
+    run->n_windows = n_windows;
+    run->replicas = p->replicas;
+    run->stride = p->sample_stride;
+    run->k = p->k;
+    run->kT = p->kT;
+    run->dt = p->dt;
+    run->gamma = p->gamma;
+    run->timeout_s = p->timeout_s;
+    run->seed = p->seed;
+    run->uid_base = p->uid_base;
+    run->lambda.assign(lambda, lambda + n_windows);
+    long long off = 0;
+    for (int i = 0; i < n_windows; ++i) {
+        const long long ns = p->n_steps_per_window ? p->n_steps_per_window[i] : p->n_steps;
+        const long long ne = p->n_equil >= 0 ? p->n_equil : ns / 10;
+        if (ns < 1 || ns >= (1LL << 32)) return fail(PMF_EINVAL, "n_steps must be in [1, 2^32)");
+        if (ne < 0 || ne >= ns) return fail(PMF_EINVAL, "n_equil must be < n_steps");
+        const long long T = (ns - ne) / p->sample_stride;
+        if (T < 1) return fail(PMF_EINVAL, "each window needs at least one sample (n_steps - n_equil >= stride)");
+        run->nsteps.push_back(ns);
+        run->nequil.push_back(ne);
+        run->tw.push_back(T);
+        run->off.push_back(off);
+        off += T * p->replicas;
+        run->max_steps = std::max(run->max_steps, ns);
+    }
+    run->total = off;
+    const int n_rep = n_windows * p->replicas;
+    if (sys->model == PMF_MODEL_CHAIN) run->state_bytes = sys->chains[p->chain]->state_bytes_per_replica() * n_rep;
+    else run->state_bytes = sizeof(double) * n_rep;
+    CK(upload(&run->d_lambda, run->lambda.data(), n_windows), "upload lambda");
+    CK(upload(&run->d_nsteps, run->nsteps.data(), n_windows), "upload steps");
+    CK(upload(&run->d_nequil, run->nequil.data(), n_windows), "upload equil");
+    CK(upload(&run->d_off, run->off.data(), n_windows), "upload offsets");
+    CK(upload(&run->d_tw, run->tw.data(), n_windows), "upload samples");
+    CK(cudaMalloc(&run->d_x, sizeof(float) * run->total), "alloc samples");
+    CK(cudaMalloc(&run->d_state, run->state_bytes), "alloc state");
+    CK(cudaMalloc(&run->d_err, sizeof(int)), "alloc flag");
+    CK(cudaMalloc(&run->d_scratch, reduce_scratch_bytes(n_windows, p->replicas)), "alloc scratch");
+    CK(cudaMalloc(&run->d_res, sizeof(double) * kResFields * n_windows), "alloc results");
+    CK(cudaEventCreateWithFlags(&run->done, cudaEventDisableTiming), "event");
+    *out = run.release();
+    return PMF_OK;
+}
+
+pmf_status pmf_run_launch(pmf_run *run)
+{
+    if (!run) return fail(PMF_EINVAL, "pmf_run_launch: null run");
+    CK(cudaMemsetAsync(run->d_err, 0, sizeof(int), g_stream), "clear flag");
+    RunLaunch L;
+    L.state = run->d_state;
+    L.xout = run->d_x;
+    L.lambda = run->d_lambda;
+    L.nsteps_w = run->d_nsteps;
+    L.nequil_w = run->d_nequil;
+    L.off_w = run->d_off;
+    L.tw = run->d_tw;
+    L.err = run->d_err;
+    L.replicas = run->replicas;
+    L.stride = run->stride;
+    L.uid_base = run->uid_base;
+    L.seed = run->seed;
+    L.k = run->k;
+    L.kT = run->kT;
+    L.dt = run->dt;
+    L.gamma = run->gamma;
+    const int n_rep = run->n_windows * run->replicas;
+    L.n_blocks = n_rep;
+    // chunks keep each launch bounded; state carries over in device memory
+    const long long chunk = run->sys->model == PMF_MODEL_CHAIN ? 100000 : (1LL << 40);
+    for (long long s0 = 0; s0 < run->max_steps; s0 += chunk) {
+        L.step_begin = s0;
+        L.step_end = std::min(run->max_steps, s0 + chunk);
+        cudaError_t e = run->sys->model == PMF_MODEL_CHAIN
+                            ? run->sys->chains[run->chain]->launch(L, g_stream)
+                            : od1d_launch(run->sys->od, L, n_rep, g_stream);
+        if (e != cudaSuccess) return cuda_fail(e, "launch simulation");
+    }
+    CK(cudaEventRecord(run->done, g_stream), "record");
+    run->launched = true;
+    run->finished = false;
+    run->reduced = false;
+    return PMF_OK;
+}
+
+pmf_status pmf_run_wait(pmf_run *run)
+{
+    if (!run || !run->launched) return fail(PMF_ESTATE, "pmf_run_wait: run not launched");
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaEventQuery(run->done);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return cuda_fail(q, "run");
+        if (run->timeout_s > 0) {
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > run->timeout_s) return fail(PMF_ETIMEOUT, "run exceeded timeout_s");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+    int err = 0;
+    CK(cudaMemcpy(&err, run->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read flag");
+    run->finished = true;
+    if (err) return fail(PMF_ENUMERIC, "a trajectory became non-finite");
+    return PMF_OK;
+}
+
+pmf_status pmf_run_windows(pmf_system *sys, const double *lambda, int n_windows, const pmf_run_params *p,
+                           pmf_run **out)
+{
+    pmf_status s = pmf_run_prepare(sys, lambda, n_windows, p, out);
+    if (s != PMF_OK) return s;
+    if ((s = pmf_run_launch(*out)) != PMF_OK) return s;
+    return pmf_run_wait(*out);
+}
+
+void pmf_destroy_run(pmf_run *run) { delete run; }
+
+pmf_status pmf_get_run_info(const pmf_run *run, pmf_run_info *info)
+{
+    if (!run || !info) return fail(PMF_EINVAL, "pmf_get_run_info: null argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n_windows = run->n_windows;
+    info->replicas = run->replicas;
+    info->total_samples = run->total;
+    for (int i = 0; i < run->n_windows; ++i) {
+        info->samples_per_window[i] = run->tw[i];
+        info->sample_offset[i] = run->off[i];
+    }
+    return PMF_OK;
+}
+
+static pmf_status need_finished(const pmf_run *run)
+{
+    if (!run) return fail(PMF_EINVAL, "null run");
+    if (!run->finished) return fail(PMF_ESTATE, "run has not finished (call pmf_run_wait)");
+    return PMF_OK;
+}
+
+pmf_status pmf_x_samples(const pmf_run *run, float *out, size_t capacity, size_t *n_written)
+{
+    if (pmf_status s = need_finished(run)) return s;
+    if (n_written) *n_written = (size_t)run->total;
+    if (!out || capacity < (size_t)run->total) return fail(PMF_EINVAL, "pmf_x_samples: capacity too small");
+    CK(cudaMemcpyAsync(out, run->d_x, sizeof(float) * run->total, cudaMemcpyDeviceToHost, g_stream), "copy samples");
+    CK(cudaStreamSynchronize(g_stream), "sync");
+    return PMF_OK;
+}
+
+static ReduceLayout layout_of(const pmf_run *run)
+{
+    ReduceLayout L;
+    L.x = run->d_x;
+    L.lambda = run->d_lambda;
+    L.off_w = run->d_off;
+    L.tw = run->d_tw;
+    L.n_windows = run->n_windows;
+    L.replicas = run->replicas;
+    L.k = run->k;
+    L.kT = run->kT;
+    return L;
+}
+
+pmf_status pmf_work_samples(const pmf_run *run, int mode, double *out, size_t capacity, size_t *n_written)
+{
+    if (pmf_status s = need_finished(run)) return s;
+    long long need = 0;
+    if (mode == PMF_WORK_PER_WINDOW_INCREMENT) {
+        need = run->off[run->n_windows - 1];
+    } else if (mode == PMF_WORK_PAIRED_CUMULATIVE) {
+        for (int i = 1; i < run->n_windows; ++i)
+            if (run->tw[i] != run->tw[0]) return fail(PMF_EINVAL, "paired work needs equal samples per window");
+        need = (long long)(run->n_windows - 1) * run->replicas * run->tw[0];
+    } else {
+        return fail(PMF_EINVAL, "unknown work mode");
+    }
+    if (n_written) *n_written = (size_t)need;
+    if (!out || capacity < (size_t)need) return fail(PMF_EINVAL, "pmf_work_samples: capacity too small");
+    double *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(double) * (need ? need : 1)), "alloc work");
+    cudaError_t e = work_samples_launch(layout_of(run), mode, run->tw[0], d, g_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, sizeof(double) * need, cudaMemcpyDeviceToHost, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "work samples");
+    return PMF_OK;
+}
+
+static pmf_status copy_result(const double *host, int s, pmf_free_energy_result *res)
+{
+    if (res->capacity < s) return fail(PMF_EINVAL, "result capacity smaller than n_windows");
+    double *dst[kResFields] = {res->lambda, res->dF_JE, res->dF_fluct, res->dF_G, res->dF_com, res->uncertainty,
+                               res->se_JE, res->se_fluct, res->var_ZW, res->W_mean, res->acc_force, res->mean_x,
+                               res->var_x, res->gamma2};
+    for (int q = 0; q < kResFields; ++q)
+        if (dst[q]) std::memcpy(dst[q], host + (size_t)q * s, sizeof(double) * s);
+    return PMF_OK;
+}
+
+pmf_status pmf_run_reduce(pmf_run *run)
+{
+    if (!run) return fail(PMF_EINVAL, "null run");
+    if (!run->launched) return fail(PMF_ESTATE, "pmf_run_reduce: run not launched");
+    cudaError_t e = reduce_launch(layout_of(run), run->d_scratch, run->d_res, g_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce");
+    run->reduced = true;
+    return PMF_OK;
+}
+
+pmf_status pmf_free_energy(const pmf_run *run, pmf_free_energy_result *res)
+{
+    if (pmf_status s = need_finished(run)) return s;
+    if (!res) return fail(PMF_EINVAL, "null result");
+    if (res->capacity < run->n_windows) return fail(PMF_EINVAL, "result capacity smaller than n_windows");
+    if (!run->reduced) {
+        cudaError_t e = reduce_launch(layout_of(run), run->d_scratch, run->d_res, g_stream);
+        if (e != cudaSuccess) return cuda_fail(e, "reduce");
+        const_cast<pmf_run *>(run)->reduced = true;
+    }
+    std::vector<double> h((size_t)kResFields * run->n_windows);
+    CK(cudaMemcpyAsync(h.data(), run->d_res, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g_stream), "copy");
+    CK(cudaStreamSynchronize(g_stream), "sync");
+    return copy_result(h.data(), run->n_windows, res);
+}
+
+pmf_status pmf_free_energy_from_samples(const float *x, int x_on_device, const double *lambda, int n_windows,
+                                        int replicas, const int64_t *samples_per_window, double k, double kT,
+                                        pmf_free_energy_result *res)
+{
+    if (!x || !lambda || !samples_per_window || !res) return fail(PMF_EINVAL, "null argument");
+    if (pmf_status s = need_device()) return s;
+    if (n_windows < 2 || n_windows > 1024 || replicas < 1 || replicas > 65535)
+        return fail(PMF_EINVAL, "bad window / replica count");
+    if (res->capacity < n_windows) return fail(PMF_EINVAL, "result capacity smaller than n_windows");
+    if (!(k > 0) || !(kT > 0)) return fail(PMF_EINVAL, "need k > 0, kT > 0");
+    std::vector<long long> off(n_windows), tw(n_windows);
+    long long total = 0;
+    for (int i = 0; i < n_windows; ++i) {
+        if (samples_per_window[i] < 1) return fail(PMF_EINVAL, "each window needs at least one sample");
+        tw[i] = samples_per_window[i];
+        off[i] = total;
+        total += tw[i] * replicas;
+    }
+    struct Tmp {
+        double *lam = nullptr, *res = nullptr;
+        long long *off = nullptr, *tw = nullptr;
+        float *x = nullptr;
+        void *scratch = nullptr;
+        ~Tmp() { cudaFree(lam); cudaFree(res); cudaFree(off); cudaFree(tw); cudaFree(x); cudaFree(scratch); }
+    } t;
+    CK(upload(&t.lam, lambda, n_windows), "upload lambda");
+    CK(upload(&t.off, off.data(), n_windows), "upload offsets");
+    CK(upload(&t.tw, tw.data(), n_windows), "upload counts");
+    const float *dx = x;
+    if (!x_on_device) {
+        CK(upload(&t.x, x, (size_t)total), "upload samples");
+        dx = t.x;
+    }
+    CK(cudaMalloc(&t.scratch, reduce_scratch_bytes(n_windows, replicas)), "alloc scratch");
+    CK(cudaMalloc(&t.res, sizeof(double) * kResFields * n_windows), "alloc result");
+    ReduceLayout L;
+    L.x = dx;
+    L.lambda = t.lam;
+    L.off_w = t.off;
+    L.tw = t.tw;
+    L.n_windows = n_windows;
+    L.replicas = replicas;
+    L.k = k;
+    L.kT = kT;
+    cudaError_t e = reduce_launch(L, t.scratch, t.res, g_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce");
+    std::vector<double> h((size_t)kResFields * n_windows);
+    CK(cudaMemcpyAsync(h.data(), t.res, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g_stream), "copy");
+    CK(cudaStreamSynchronize(g_stream), "sync");
+    return copy_result(h.data(), n_windows, res);
+}
+
+pmf_status pmf_final_state(const pmf_run *run, double *pos, double *vel, size_t capacity, size_t *n_written)
+{
+    if (pmf_status s = need_finished(run)) return s;
+    const int n_rep = run->n_windows * run->replicas;
+    if (run->sys->model == PMF_MODEL_1D_DOUBLEWELL) {
+        if (n_written) *n_written = (size_t)n_rep;
+        if (!pos || capacity < (size_t)n_rep) return fail(PMF_EINVAL, "pmf_final_state: capacity too small");
+        CK(cudaMemcpy(pos, run->d_state, sizeof(double) * n_rep, cudaMemcpyDeviceToHost), "copy state");
+        return PMF_OK;
+    }
+    const ChainModel &m = *run->sys->chains[run->chain];
+    const int N = m.n_beads(), Np = m.n_padded();
+    const size_t need = (size_t)n_rep * N * 3;
+    if (n_written) *n_written = need;
+    if ((!pos && !vel) || capacity < need) return fail(PMF_EINVAL, "pmf_final_state: capacity too small");
+    std::vector<unsigned char> raw(run->state_bytes);
+    CK(cudaMemcpy(raw.data(), run->d_state, run->state_bytes, cudaMemcpyDeviceToHost), "copy state");
+    const bool dbl = m.precision() == PMF_FP64;
+    for (int q = 0; q < n_rep; ++q)
+        for (int b = 0; b < N; ++b)
+            for (int a = 0; a < 3; ++a) {
+                const size_t ip = ((size_t)q * 2 * Np + b) * 4 + a, iv = ((size_t)q * 2 * Np + Np + b) * 4 + a;
+                const double pv = dbl ? reinterpret_cast<double *>(raw.data())[ip] : reinterpret_cast<float *>(raw.data())[ip];
+                const double vv = dbl ? reinterpret_cast<double *>(raw.data())[iv] : reinterpret_cast<float *>(raw.data())[iv];
+                if (pos) pos[((size_t)q * N + b) * 3 + a] = pv;
+                if (vel) vel[((size_t)q * N + b) * 3 + a] = vv;
+            }
+    return PMF_OK;
+}
+
+pmf_status pmf_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int n_blocks, uint32_t *raw,
+                      float *normals)
+{
+    if (n_blocks < 0) return fail(PMF_EINVAL, "n_blocks < 0");
+    if (pmf_status s = need_device()) return s;
+    if (n_blocks == 0) return PMF_OK;
+    uint32_t *dr = nullptr;
+    float *dn = nullptr;
+    CK(cudaMalloc(&dr, sizeof(uint32_t) * 4 * n_blocks), "alloc");
+    cudaError_t e = cudaMalloc(&dn, sizeof(float) * 4 * n_blocks);
+    if (e == cudaSuccess) e = philox_launch(seed, c0, c1, c2, c3, n_blocks, dr, dn, g_stream);
+    if (e == cudaSuccess && raw) e = cudaMemcpyAsync(raw, dr, sizeof(uint32_t) * 4 * n_blocks, cudaMemcpyDeviceToHost, g_stream);
+    if (e == cudaSuccess && normals) e = cudaMemcpyAsync(normals, dn, sizeof(float) * 4 * n_blocks, cudaMemcpyDeviceToHost, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    cudaFree(dr);
+    cudaFree(dn);
+    if (e != cudaSuccess) return cuda_fail(e, "philox");
+    return PMF_OK;
+}
+
+pmf_status pmf_chain_schedule(int N, int NW, int *out, size_t capacity, size_t *n_written, int *padded)
+{
+    if (N < 4 || N > 1024 || (NW != 4 && NW != 8)) return fail(PMF_EINVAL, "pmf_chain_schedule: N in [4,1024], NW 4 or 8");
+    const auto sched = chain_schedule(N, NW, kChainUnitPiece);
+    size_t n = 0;
+    for (const auto &v : sched) n += v.size();
+    if (n_written) *n_written = n;
+    if (padded) *padded = chain_geometry(N).Np;
+    if (!out || capacity < 6 * n) return fail(PMF_EINVAL, "pmf_chain_schedule: capacity too small");
+    size_t q = 0;
+    for (int w = 0; w < NW; ++w)
+        for (const UnitDesc &u : sched[w]) {
+            int *o = out + 6 * q++;
+            o[0] = w; o[1] = u.I; o[2] = u.J; o[3] = u.tb; o[4] = u.te; o[5] = u.flags;
+        }
+    return PMF_OK;
+}
+
+pmf_status pmf_chain_forces(pmf_system *sys, int chain, const double *pos, double lambda, double k, double *forces)
+{
+    if (!sys || !pos || !forces) return fail(PMF_EINVAL, "null argument");
+    if (sys->model != PMF_MODEL_CHAIN || chain < 0 || chain >= (int)sys->chains.size())
+        return fail(PMF_EINVAL, "not a chain system / bad chain index");
+    ChainModel &m = *sys->chains[chain];
+    const int N = m.n_beads(), Np = m.n_padded();
+    const bool dbl = m.precision() == PMF_FP64;
+    // a one-replica state holding pos, zero velocity, run for zero steps
+    const size_t es = dbl ? sizeof(double) : sizeof(float);
+    std::vector<unsigned char> st(m.state_bytes_per_replica(), 0);
+    for (int b = 0; b < Np; ++b)
+        for (int a = 0; a < 3; ++a) {
+            const double v = b < N ? pos[3 * b + a] : (a == 0 ? 1.0e4 + 100.0 * b : 1.0e4);
+            if (dbl) reinterpret_cast<double *>(st.data())[(size_t)b * 4 + a] = v;
+            else reinterpret_cast<float *>(st.data())[(size_t)b * 4 + a] = (float)v;
+        }
+    (void)es;
+    struct Tmp {
+        void *state = nullptr;
+        double *lam = nullptr, *f = nullptr;
+        long long *ns = nullptr;
+        int *err = nullptr;
+        float *x = nullptr;
+        ~Tmp() { cudaFree(state); cudaFree(lam); cudaFree(f); cudaFree(ns); cudaFree(err); cudaFree(x); }
+    } t;
+    long long one[4] = {1, 0, 0, 1};
+    CK(upload(reinterpret_cast<unsigned char **>(&t.state), st.data(), st.size()), "upload state");
+    CK(upload(&t.lam, &lambda, 1), "upload lambda");
+    CK(upload(&t.ns, one, 4), "upload counts");
+    CK(cudaMalloc(&t.f, sizeof(double) * 3 * N), "alloc forces");
+    CK(cudaMalloc(&t.x, sizeof(float)), "alloc");
+    CK(cudaMalloc(&t.err, sizeof(int)), "alloc");
+    CK(cudaMemset(t.err, 0, sizeof(int)), "clear");
+    RunLaunch L;
+    L.state = t.state;
+    L.xout = t.x;
+    L.lambda = t.lam;
+    L.nsteps_w = t.ns;
+    L.nequil_w = t.ns + 1;
+    L.off_w = t.ns + 2;
+    L.tw = t.ns + 3;
+    L.err = t.err;
+    L.force_out = t.f;
+    L.step_begin = 1;  // resume from the given state: no velocity draw
+    L.step_end = 1;
+    L.replicas = 1;
+    L.stride = 1;
+    L.n_blocks = 1;
+    L.k = k;
+    L.kT = 1.0;
+    L.dt = 1e-3;
+    L.gamma = 1.0;
+    cudaError_t e = m.launch(L, g_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "forces");
+    CK(cudaMemcpyAsync(forces, t.f, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, g_stream), "copy forces");
+    CK(cudaStreamSynchronize(g_stream), "sync");
+    return PMF_OK;
+}
+
+}  // extern "C"

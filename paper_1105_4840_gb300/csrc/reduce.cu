@@ -1,0 +1,279 @@
+// FP64 reductions of the recorded x samples into the paper's estimators.
+//
+// Stage 1 (one CTA per (window i, replica r)): work increments of Eq. (9),
+//   w = k/2 (lambda_{i+1} - lambda_i)(lambda_{i+1} + lambda_i - 2 x),
+//   the replica's minimum m_ir, the max-shifted exponential sum
+//   S_ir = sum exp(-(w - m_ir)/kT) (Eq. (12)), and the shifted moments
+//   sum (x - lambda_i), sum (x - lambda_i)^2, all with compensated sums.
+// Stage 2 (one CTA per window): merge the replicas (log-sum-exp aware),
+//   the per-window JE increment, the Eq. (14) and Eq. (13) increments and
+//   the delete-one-replica jackknife.
+// Stage 3 (one thread): prefix sums over windows into the profiles and the
+//   combined estimate of Sec. V.
+// The windows are independent (Sec. II: rho(W_mech) is the product of the
+// rho(x_i)), so the average of exp(-W_mech/kT) over all combinations of
+// samples is the product of the per-window averages.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pmf {
+
+struct Partial {
+    double m, S, n, sdx, sdx2;
+};
+struct WindowOut {
+    double je, fl, g, wmean, varw, n, jk_je, jk_fl, mean, var;
+};
+
+__device__ __forceinline__ void neumaier(double &s, double &c, double v)
+{
+    const double t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+}
+
+template <int NT> __device__ double block_sum(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NT / 32; ++q) t += red[q];
+        red[NT / 32] = t;
+    }
+    __syncthreads();
+    return red[NT / 32];
+}
+
+template <int NT> __device__ double block_min(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = red[0];
+        for (int q = 1; q < NT / 32; ++q) t = fmin(t, red[q]);
+        red[NT / 32] = t;
+    }
+    __syncthreads();
+    return red[NT / 32];
+}
+
+constexpr int kPartialThreads = 256;
+
+__global__ void __launch_bounds__(kPartialThreads) partial_kernel(const ReduceLayout L, Partial *out)
+{
+    __shared__ double red[kPartialThreads / 32 + 1];
+    const int w = blockIdx.x, r = blockIdx.y;
+    const long long T = L.tw[w];
+    const float *x = L.x + L.off_w[w] + (long long)r * T;
+    const double li = L.lambda[w];
+    const double ln = (w + 1 < L.n_windows) ? L.lambda[w + 1] : li;
+    const double hkd = 0.5 * L.k * (ln - li), ssum = ln + li;
+    double m = INFINITY, s1 = 0, c1 = 0, s2 = 0, c2 = 0;
+    for (long long t = threadIdx.x; t < T; t += kPartialThreads) {
+        const double xv = (double)x[t];
+        m = fmin(m, hkd * (ssum - 2.0 * xv));
+        const double d = xv - li;
+        neumaier(s1, c1, d);
+        neumaier(s2, c2, d * d);
+    }
+    m = block_min<kPartialThreads>(m, red);
+    const double sdx = block_sum<kPartialThreads>(s1 + c1, red);
+    const double sdx2 = block_sum<kPartialThreads>(s2 + c2, red);
+    double se = 0, ce = 0;
+    for (long long t = threadIdx.x; t < T; t += kPartialThreads) {
+        const double wv = hkd * (ssum - 2.0 * (double)x[t]);
+        neumaier(se, ce, exp(-(wv - m) / L.kT));
+    }
+    const double S = block_sum<kPartialThreads>(se + ce, red);
+    if (threadIdx.x == 0) out[(size_t)w * L.replicas + r] = Partial{m, S, (double)T, sdx, sdx2};
+}
+
+constexpr int kWindowThreads = 256;
+
+__global__ void __launch_bounds__(kWindowThreads) window_kernel(const ReduceLayout L, const Partial *P, WindowOut *wo)
+{
+    extern __shared__ double E[];  // [replicas]
+    __shared__ double red[kWindowThreads / 32 + 1];
+    const int w = blockIdx.x, R = L.replicas;
+    const Partial *p = P + (size_t)w * R;
+    const double li = L.lambda[w];
+    const double ln = (w + 1 < L.n_windows) ? L.lambda[w + 1] : li;
+    const double d = ln - li;
+    double m = INFINITY;
+    for (int r = threadIdx.x; r < R; r += kWindowThreads)
+        if (p[r].n > 0) m = fmin(m, p[r].m);
+    m = block_min<kWindowThreads>(m, red);
+    double se = 0, ce = 0, sn = 0, s1 = 0, c1 = 0, s2 = 0, c2 = 0;
+    for (int r = threadIdx.x; r < R; r += kWindowThreads) {
+        const double e = p[r].n > 0 ? p[r].S * exp(-(p[r].m - m) / L.kT) : 0.0;
+        E[r] = e;
+        neumaier(se, ce, e);
+        sn += p[r].n;
+        neumaier(s1, c1, p[r].sdx);
+        neumaier(s2, c2, p[r].sdx2);
+    }
+    const double S = block_sum<kWindowThreads>(se + ce, red);
+    const double n = block_sum<kWindowThreads>(sn, red);
+    const double sdx = block_sum<kWindowThreads>(s1 + c1, red);
+    const double sdx2 = block_sum<kWindowThreads>(s2 + c2, red);
+    const double je = m - L.kT * log(S / n);
+    const double mdx = sdx / n;
+    const double mean = li + mdx;
+    const double var = sdx2 / n - mdx * mdx;
+    const double fl = -L.k * d * mdx;
+    const double g2 = L.k * var / L.kT;
+    // delete-one-replica jackknife
+    double vje = 0, vfl = 0;
+    const bool jk = R >= 2;
+    if (jk) {
+        for (int r = threadIdx.x; r < R; r += kWindowThreads) {
+            double sm = 0, cm = 0;
+            for (int q = 0; q < R; ++q)
+                if (q != r) neumaier(sm, cm, E[q]);
+            const double nm = n - p[r].n;
+            vje += m - L.kT * log((sm + cm) / nm);
+            vfl += -L.k * d * (sdx - p[r].sdx) / nm;
+        }
+    }
+    const double mje = block_sum<kWindowThreads>(vje, red) / R;
+    const double mfl = block_sum<kWindowThreads>(vfl, red) / R;
+    double qje = 0, qfl = 0;
+    if (jk) {
+        for (int r = threadIdx.x; r < R; r += kWindowThreads) {
+            double sm = 0, cm = 0;
+            for (int q = 0; q < R; ++q)
+                if (q != r) neumaier(sm, cm, E[q]);
+            const double nm = n - p[r].n;
+            const double a = m - L.kT * log((sm + cm) / nm) - mje;
+            const double b = -L.k * d * (sdx - p[r].sdx) / nm - mfl;
+            qje += a * a;
+            qfl += b * b;
+        }
+    }
+    const double sje = block_sum<kWindowThreads>(qje, red);
+    const double sfl = block_sum<kWindowThreads>(qfl, red);
+    if (threadIdx.x == 0) {
+        WindowOut o;
+        o.je = je;
+        o.fl = fl;
+        o.g = L.k * d * d / 2.0 * (1.0 - g2) + fl;
+        o.wmean = 0.5 * L.k * d * (ln + li - 2.0 * mean);
+        o.varw = L.k * L.k * d * d * var;
+        o.n = n;
+        o.jk_je = jk ? (R - 1.0) / R * sje : NAN;
+        o.jk_fl = jk ? (R - 1.0) / R * sfl : NAN;
+        o.mean = mean;
+        o.var = var;
+        wo[w] = o;
+    }
+}
+
+__global__ void profile_kernel(const ReduceLayout L, const WindowOut *wo, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int s = L.n_windows;
+    double *f[kResFields];
+    for (int q = 0; q < kResFields; ++q) f[q] = out + (size_t)q * s;
+    double je = 0, fl = 0, g = 0, wm = 0, vje = 0, vfl = 0, vw = 0, Q = INFINITY;
+    for (int j = 0; j < s; ++j) {
+        if (j > 0) {
+            const WindowOut &o = wo[j - 1];
+            je += o.je;
+            fl += o.fl;
+            g += o.g;
+            wm += o.wmean;
+            vje += o.jk_je;
+            vfl += o.jk_fl;
+            vw += o.varw;
+            Q = fmin(Q, o.n);
+        }
+        const double lam = L.lambda[j];
+        f[kResLambda][j] = lam;
+        f[kResJE][j] = je;
+        f[kResFluct][j] = fl;
+        f[kResG][j] = g;
+        f[kResCom][j] = 0.5 * (je + fl);
+        f[kResUnc][j] = 0.5 * (je - fl);
+        f[kResSeJE][j] = j > 0 ? sqrt(vje) : 0.0;
+        f[kResSeFluct][j] = j > 0 ? sqrt(vfl) : 0.0;
+        f[kResVarZW][j] = (j > 0 && Q > 1) ? vw / Q + vw * vw / (2.0 * L.kT * L.kT * (Q - 1.0)) : (j > 0 ? NAN : 0.0);
+        f[kResWMean][j] = wm;
+        f[kResAccForce][j] = j > 0 ? fl / (lam - L.lambda[0]) : 0.0;
+        f[kResMeanX][j] = wo[j].mean;
+        f[kResVarX][j] = wo[j].var;
+        f[kResGamma2][j] = L.k * wo[j].var / L.kT;
+    }
+}
+
+size_t reduce_scratch_bytes(int n_windows, int replicas)
+{
+    return sizeof(Partial) * (size_t)n_windows * replicas + sizeof(WindowOut) * (size_t)n_windows + 256;
+}
+
+cudaError_t reduce_launch(const ReduceLayout &L, void *scratch, double *out, cudaStream_t st)
+{
+    Partial *P = reinterpret_cast<Partial *>(scratch);
+    WindowOut *wo = reinterpret_cast<WindowOut *>(reinterpret_cast<char *>(scratch) +
+                                                  sizeof(Partial) * (size_t)L.n_windows * L.replicas);
+    partial_kernel<<<dim3(L.n_windows, L.replicas), kPartialThreads, 0, st>>>(L, P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(double) * (size_t)L.replicas;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    window_kernel<<<L.n_windows, kWindowThreads, smem, st>>>(L, P, wo);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    profile_kernel<<<1, 32, 0, st>>>(L, wo, out);
+    return cudaGetLastError();
+}
+
+__global__ void work_increment_kernel(const ReduceLayout L, double *out)
+{
+    const int w = blockIdx.y, r = blockIdx.z;
+    const long long T = L.tw[w];
+    const double li = L.lambda[w], ln = L.lambda[w + 1];
+    const double hkd = 0.5 * L.k * (ln - li), ssum = ln + li;
+    const long long base = L.off_w[w] + (long long)r * T;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < T; t += (long long)gridDim.x * blockDim.x)
+        out[base + t] = hkd * (ssum - 2.0 * (double)L.x[base + t]);
+}
+
+__global__ void work_paired_kernel(const ReduceLayout L, long long T, double *out)
+{
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long n = (long long)L.replicas * T;
+    if (idx >= n) return;
+    double W = 0.0;
+    for (int i = 0; i + 1 < L.n_windows; ++i) {
+        const double li = L.lambda[i], ln = L.lambda[i + 1];
+        W += 0.5 * L.k * (ln - li) * (ln + li - 2.0 * (double)L.x[L.off_w[i] + idx]);
+        out[(size_t)i * n + idx] = W;
+    }
+}
+
+cudaError_t work_samples_launch(const ReduceLayout &L, int mode, long long samples_per_replica, double *out,
+                                cudaStream_t st)
+{
+    if (mode == 0) {
+        const int bx = (int)((samples_per_replica + 255) / 256 > 64 ? 64 : (samples_per_replica + 255) / 256);
+        work_increment_kernel<<<dim3(bx > 0 ? bx : 1, L.n_windows - 1, L.replicas), 256, 0, st>>>(L, out);
+    } else {
+        const long long n = (long long)L.replicas * samples_per_replica;
+        work_paired_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(L, samples_per_replica, out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pmf

@@ -1,0 +1,316 @@
+"""ctypes binding of libpmf.so (the C ABI declared in include/pmf.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Function names are those of the C ABI.  Importing this module
+loads libpmf.so and raises if it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpmf.so")
+
+PMF_OK, PMF_EINVAL, PMF_ENOMEM, PMF_ECUDA, PMF_ENUMERIC, PMF_ETIMEOUT, PMF_ESTATE = range(7)
+STATUS_NAMES = {0: "PMF_OK", 1: "PMF_EINVAL", 2: "PMF_ENOMEM", 3: "PMF_ECUDA", 4: "PMF_ENUMERIC",
+                5: "PMF_ETIMEOUT", 6: "PMF_ESTATE"}
+PMF_MODEL_1D_DOUBLEWELL, PMF_MODEL_CHAIN = 0, 1
+PMF_FP32, PMF_FP64 = 0, 1
+PMF_WORK_PER_WINDOW_INCREMENT, PMF_WORK_PAIRED_CUMULATIVE = 0, 1
+
+_D = C.POINTER(C.c_double)
+_F = C.POINTER(C.c_float)
+_I64 = C.POINTER(C.c_int64)
+
+
+class PmfError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SystemDesc(C.Structure):
+    _fields_ = [("model", C.c_int), ("precision", C.c_int), ("n_chains", C.c_int),
+                ("n_beads", C.POINTER(C.c_int)), ("sigma", _D), ("epsilon", _D), ("charge", _D),
+                ("mass", _D), ("dih_k", _D), ("dih_phase", _D), ("pos0", _D),
+                ("bond_k", C.c_double), ("bond_r0", C.c_double), ("angle_k", C.c_double),
+                ("angle_theta0", C.c_double), ("coulomb_k", C.c_double), ("nonbonded", C.c_int),
+                ("dw_a", C.c_double), ("x0", C.c_double)]
+
+
+class RunParams(C.Structure):
+    _fields_ = [("k", C.c_double), ("kT", C.c_double), ("dt", C.c_double), ("gamma", C.c_double),
+                ("n_steps", C.c_int64), ("n_steps_per_window", _I64), ("n_equil", C.c_int64),
+                ("sample_stride", C.c_int), ("replicas", C.c_int), ("seed", C.c_uint64),
+                ("uid_base", C.c_uint32), ("chain", C.c_int), ("timeout_s", C.c_double)]
+
+
+class RunInfo(C.Structure):
+    _fields_ = [("n_windows", C.c_int), ("replicas", C.c_int), ("total_samples", C.c_int64),
+                ("samples_per_window", C.c_int64 * 1024), ("sample_offset", C.c_int64 * 1024)]
+
+
+RESULT_FIELDS = ("lambda", "dF_JE", "dF_fluct", "dF_G", "dF_com", "uncertainty", "se_JE",
+                 "se_fluct", "var_ZW", "W_mean", "acc_force", "mean_x", "var_x", "gamma2")
+
+
+class FreeEnergyResult(C.Structure):
+    _fields_ = [("capacity", C.c_int)] + [(("lambda_" if f == "lambda" else f), _D) for f in RESULT_FIELDS]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1105_4840_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    L.pmf_create_system.argtypes = [C.POINTER(SystemDesc), C.POINTER(P)]
+    L.pmf_destroy_system.argtypes = [P]
+    L.pmf_destroy_system.restype = None
+    for name in ("pmf_run_windows", "pmf_run_prepare"):
+        getattr(L, name).argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.POINTER(P)]
+    L.pmf_run_launch.argtypes = [P]
+    L.pmf_run_wait.argtypes = [P]
+    L.pmf_destroy_run.argtypes = [P]
+    L.pmf_destroy_run.restype = None
+    L.pmf_get_run_info.argtypes = [P, C.POINTER(RunInfo)]
+    L.pmf_x_samples.argtypes = [P, _F, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.pmf_work_samples.argtypes = [P, C.c_int, _D, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.pmf_free_energy.argtypes = [P, C.POINTER(FreeEnergyResult)]
+    L.pmf_free_energy_from_samples.argtypes = [C.c_void_p, C.c_int, _D, C.c_int, C.c_int, _I64,
+                                               C.c_double, C.c_double, C.POINTER(FreeEnergyResult)]
+    L.pmf_final_state.argtypes = [P, _D, _D, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.pmf_philox.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int,
+                             C.POINTER(C.c_uint32), _F]
+    L.pmf_chain_forces.argtypes = [P, C.c_int, _D, C.c_double, C.c_double, _D]
+    L.pmf_chain_schedule.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_size_t,
+                                     C.POINTER(C.c_size_t), C.POINTER(C.c_int)]
+    L.pmf_run_reduce.argtypes = [P]
+    L.pmf_set_stream.argtypes = [C.c_void_p]
+    L.pmf_last_error.restype = C.c_char_p
+    L.pmf_version.restype = C.c_char_p
+    for name in ("pmf_create_system", "pmf_run_windows", "pmf_run_prepare", "pmf_run_launch",
+                 "pmf_run_wait", "pmf_get_run_info", "pmf_x_samples", "pmf_work_samples",
+                 "pmf_free_energy", "pmf_free_energy_from_samples", "pmf_final_state", "pmf_philox",
+                 "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_set_stream"):
+        getattr(L, name).restype = C.c_int
+    return L
+
+
+lib = _load()
+
+
+def _check(status, where):
+    if status != PMF_OK:
+        raise PmfError(status, where, lib.pmf_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D)
+
+
+def pmf_version() -> str:
+    return lib.pmf_version().decode()
+
+
+def pmf_set_stream(stream_handle: int | None):
+    """stream_handle: an integer cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)."""
+    _check(lib.pmf_set_stream(C.c_void_p(stream_handle or 0)), "pmf_set_stream")
+
+
+class System:
+    """Owner of a pmf_system handle (and of the arrays passed to it)."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def close(self):
+        if self.handle:
+            lib.pmf_destroy_system(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pmf_create_system_chain(chains, starts, precision=PMF_FP32) -> System:
+    """chains: list of inputs.ChainParams (same bonded constants); starts: list of [N, 3]."""
+    chains = list(chains)
+    starts = list(starts)
+    cat = lambda f: np.ascontiguousarray(np.concatenate([np.asarray(f(c), dtype=np.float64).ravel()
+                                                          for c in chains]))
+    keep = dict(n=np.array([c.n for c in chains], dtype=np.int32), sigma=cat(lambda c: c.sigma),
+                eps=cat(lambda c: c.epsilon), q=cat(lambda c: c.charge), m=cat(lambda c: c.mass),
+                dk=cat(lambda c: c.dih_k), dph=cat(lambda c: c.dih_phase),
+                pos=np.ascontiguousarray(np.concatenate([np.asarray(s, dtype=np.float64).ravel()
+                                                         for s in starts])))
+    c0 = chains[0]
+    d = SystemDesc(model=PMF_MODEL_CHAIN, precision=precision, n_chains=len(chains),
+                   n_beads=keep["n"].ctypes.data_as(C.POINTER(C.c_int)), sigma=_dp(keep["sigma"]),
+                   epsilon=_dp(keep["eps"]), charge=_dp(keep["q"]), mass=_dp(keep["m"]),
+                   dih_k=_dp(keep["dk"]), dih_phase=_dp(keep["dph"]), pos0=_dp(keep["pos"]),
+                   bond_k=c0.kb, bond_r0=c0.r0, angle_k=c0.ktheta, angle_theta0=c0.theta0,
+                   coulomb_k=c0.ke, nonbonded=int(c0.nonbonded))
+    h = C.c_void_p()
+    _check(lib.pmf_create_system(C.byref(d), C.byref(h)), "pmf_create_system")
+    return System(h, keep)
+
+
+def pmf_create_system_1d(a=2.0, x0=-1.0) -> System:
+    d = SystemDesc(model=PMF_MODEL_1D_DOUBLEWELL, dw_a=a, x0=x0)
+    h = C.c_void_p()
+    _check(lib.pmf_create_system(C.byref(d), C.byref(h)), "pmf_create_system")
+    return System(h, None)
+
+
+def make_params(run, chain=0, n_steps_per_window=None, timeout_s=0.0, uid_base=0):
+    """RunParams from an inputs.RunSettings."""
+    arr = None
+    if n_steps_per_window is not None:
+        arr = np.ascontiguousarray(n_steps_per_window, dtype=np.int64)
+    p = RunParams(k=run.k, kT=run.kT, dt=run.dt, gamma=run.gamma, n_steps=run.n_steps,
+                  n_steps_per_window=arr.ctypes.data_as(_I64) if arr is not None else None,
+                  n_equil=run.n_equil, sample_stride=run.stride, replicas=run.replicas,
+                  seed=run.seed, uid_base=uid_base, chain=chain, timeout_s=timeout_s)
+    return p, arr
+
+
+class Run:
+    """Owner of a pmf_run handle."""
+
+    def __init__(self, handle, lambdas, keep=None):
+        self.handle = handle
+        self.lambdas = np.asarray(lambdas, dtype=np.float64)
+        self._keep = keep
+
+    def close(self):
+        if self.handle:
+            lib.pmf_destroy_run(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch(self):
+        _check(lib.pmf_run_launch(self.handle), "pmf_run_launch")
+
+    def wait(self):
+        _check(lib.pmf_run_wait(self.handle), "pmf_run_wait")
+
+    def reduce(self):
+        _check(lib.pmf_run_reduce(self.handle), "pmf_run_reduce")
+
+    def info(self):
+        inf = RunInfo()
+        _check(lib.pmf_get_run_info(self.handle, C.byref(inf)), "pmf_get_run_info")
+        s = inf.n_windows
+        return dict(n_windows=s, replicas=inf.replicas, total_samples=inf.total_samples,
+                    samples_per_window=np.array(inf.samples_per_window[:s]),
+                    sample_offset=np.array(inf.sample_offset[:s]))
+
+    def x_samples(self):
+        """Per-window arrays [R, T_w] (float32)."""
+        inf = self.info()
+        out = np.zeros(inf["total_samples"], dtype=np.float32)
+        n = C.c_size_t()
+        _check(lib.pmf_x_samples(self.handle, out.ctypes.data_as(_F), out.size, C.byref(n)), "pmf_x_samples")
+        R = inf["replicas"]
+        return [out[o:o + R * t].reshape(R, t) for o, t in
+                zip(inf["sample_offset"], inf["samples_per_window"])]
+
+    def work_samples(self, mode=PMF_WORK_PER_WINDOW_INCREMENT):
+        n = C.c_size_t()
+        lib.pmf_work_samples(self.handle, mode, None, 0, C.byref(n))
+        out = np.zeros(n.value, dtype=np.float64)
+        _check(lib.pmf_work_samples(self.handle, mode, _dp(out), out.size, C.byref(n)), "pmf_work_samples")
+        return out
+
+    def free_energy(self):
+        return _fe_call(lambda res: lib.pmf_free_energy(self.handle, C.byref(res)), self.lambdas.size,
+                        "pmf_free_energy")
+
+    def final_state(self):
+        n = C.c_size_t()
+        lib.pmf_final_state(self.handle, None, None, 0, C.byref(n))
+        pos = np.zeros(n.value)
+        vel = np.zeros(n.value)
+        _check(lib.pmf_final_state(self.handle, _dp(pos), _dp(vel), n.value, C.byref(n)), "pmf_final_state")
+        return pos, vel
+
+
+def _fe_call(fn, s, where):
+    arrs = {f: np.zeros(s) for f in RESULT_FIELDS}
+    res = FreeEnergyResult(capacity=s, **{("lambda_" if f == "lambda" else f): _dp(a) for f, a in arrs.items()})
+    _check(fn(res), where)
+    return arrs
+
+
+def pmf_run_prepare(system: System, lambdas, params) -> Run:
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    p, keep = params
+    h = C.c_void_p()
+    _check(lib.pmf_run_prepare(system.handle, _dp(lam), lam.size, C.byref(p), C.byref(h)), "pmf_run_prepare")
+    return Run(h, lam, keep=(p, keep, system))
+
+
+def pmf_run_windows(system: System, lambdas, params) -> Run:
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    p, keep = params
+    h = C.c_void_p()
+    st = lib.pmf_run_windows(system.handle, _dp(lam), lam.size, C.byref(p), C.byref(h))
+    run = Run(h, lam, keep=(p, keep, system)) if h.value else None
+    if st != PMF_OK:
+        err = PmfError(st, "pmf_run_windows", lib.pmf_last_error().decode())
+        err.run = run
+        raise err
+    return run
+
+
+def pmf_free_energy_from_samples(x, lambdas, replicas, samples_per_window, k, kT, x_on_device=False):
+    """x: host float32 array in run layout, or (x_on_device=True) an integer device pointer."""
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    spw = np.ascontiguousarray(samples_per_window, dtype=np.int64)
+    if x_on_device:
+        xp = C.c_void_p(int(x))
+    else:
+        xa = np.ascontiguousarray(x, dtype=np.float32)
+        xp = xa.ctypes.data_as(C.c_void_p)
+    return _fe_call(lambda res: lib.pmf_free_energy_from_samples(xp, int(bool(x_on_device)), _dp(lam), lam.size,
+                                                                 replicas, spw.ctypes.data_as(_I64), k, kT,
+                                                                 C.byref(res)),
+                    lam.size, "pmf_free_energy_from_samples")
+
+
+def pmf_philox(seed, c0, c1, c2, c3, n_blocks):
+    raw = np.zeros((n_blocks, 4), dtype=np.uint32)
+    nor = np.zeros((n_blocks, 4), dtype=np.float32)
+    _check(lib.pmf_philox(seed, c0, c1, c2, c3, n_blocks, raw.ctypes.data_as(C.POINTER(C.c_uint32)),
+                          nor.ctypes.data_as(_F)), "pmf_philox")
+    return raw, nor
+
+
+def pmf_chain_forces(system: System, chain, pos, lam, k):
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    f = np.zeros_like(pos)
+    _check(lib.pmf_chain_forces(system.handle, chain, _dp(pos), lam, k, _dp(f)), "pmf_chain_forces")
+    return f
+
+
+def pmf_chain_schedule(N, NW=4):
+    """Host schedule: int array [units, 6] (warp, I, J, t_begin, t_end, flags), padded N."""
+    n = C.c_size_t()
+    pad = C.c_int()
+    lib.pmf_chain_schedule(N, NW, None, 0, C.byref(n), C.byref(pad))
+    out = np.zeros(6 * n.value, dtype=np.int32)
+    _check(lib.pmf_chain_schedule(N, NW, out.ctypes.data_as(C.POINTER(C.c_int)), out.size, C.byref(n),
+                                  C.byref(pad)), "pmf_chain_schedule")
+    return out.reshape(-1, 6), pad.value

@@ -171,7 +171,8 @@ double orc_chain_energy(const orc_chain *c, const double *r, double lambda, doub
                 double rr = norm3(d);
                 double sij = 0.5 * (c->sigma[i] + c->sigma[j]);
                 double eij = sqrt(c->eps[i] * c->eps[j]);
-                double sr6 = pow(sij / rr, 6.0);
+                double sr2 = (sij / rr) * (sij / rr);
+                double sr6 = sr2 * sr2 * sr2;
                 elj += 4.0 * eij * (sr6 * sr6 - sr6);
                 eq += c->ke * c->q[i] * c->q[j] / rr;
             }
@@ -273,7 +274,8 @@ void orc_chain_forces(const orc_chain *c, const double *r, double lambda, double
                 double rr = norm3(d);
                 double sij = 0.5 * (c->sigma[i] + c->sigma[j]);
                 double eij = sqrt(c->eps[i] * c->eps[j]);
-                double sr6 = pow(sij / rr, 6.0);
+                double sr2 = (sij / rr) * (sij / rr);
+                double sr6 = sr2 * sr2 * sr2;
                 /* dU/dr = -(24 eps (2 sr12 - sr6) + ke qi qj / r) / r */
                 double dudr = -(24.0 * eij * (2.0 * sr6 * sr6 - sr6) + c->ke * c->q[i] * c->q[j] / rr) / rr;
                 for (int a = 0; a < 3; ++a) {

@@ -207,6 +207,30 @@ pmf_status pmf_free_energy_from_samples(const float *x, int x_on_device, const d
                                         const int64_t *samples_per_window, double k, double kT,
                                         pmf_free_energy_result *res);
 
+/* Allocation-free form of pmf_free_energy_from_samples, for callers that
+ * must not allocate GPU memory: for instance a host application whose own
+ * pool has already reserved the device memory, or a latency-critical loop
+ * that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ * The paper has no counterpart; it is a library-interface convenience.
+ *   x       device pointer, FP32 samples [n_windows][replicas][samples_per_window]
+ *   lambda  device pointer, n_windows window centres (strictly monotone)
+ *   out     device pointer, 14 * n_windows doubles: the arrays of
+ *           pmf_free_energy_result in its field order (lambda, dF_JE, dF_fluct,
+ *           dF_G, dF_com, uncertainty, se_JE, se_fluct, var_ZW, W_mean,
+ *           acc_force, mean_x, var_x, gamma2), each n_windows long
+ * Limits: 2 <= n_windows <= 1024, n_windows * replicas <= 65536,
+ * samples_per_window >= 1; larger sizes return PMF_EINVAL.
+ * The call only enqueues kernels on the library stream and returns; the
+ * results are valid once that stream has reached this point.  Its scratch is
+ * a fixed array (about 2.7 MB) that every GPU which loads the library keeps
+ * until the process exits, shared by all calls on that GPU: calls whose work
+ * overlaps on the GPU race and must be serialised by the caller.  The first
+ * call on a device looks up that array's device address (with the device
+ * current); make that first call before any stream capture begins.  No call
+ * allocates or frees memory. */
+pmf_status pmf_free_energy_noalloc(const float *x, const double *lambda, int n_windows, int replicas,
+                                   int64_t samples_per_window, double k, double kT, double *out);
+
 /* Final state of every replica: pos/vel [window][replica][bead][3] (chain) or
  * [window][replica] (1D, vel unused).  Capacity in doubles of each buffer. */
 pmf_status pmf_final_state(const pmf_run *run, double *pos, double *vel, size_t capacity,

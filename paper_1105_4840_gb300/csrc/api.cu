@@ -472,6 +472,22 @@ pmf_status pmf_free_energy_from_samples(const float *x, int x_on_device, const d
     return copy_result(h.data(), n_windows, res);
 }
 
+pmf_status pmf_free_energy_noalloc(const float *x, const double *lambda, int n_windows, int replicas,
+                                   int64_t samples_per_window, double k, double kT, double *out)
+{
+    if (!x || !lambda || !out) return fail(PMF_EINVAL, "pmf_free_energy_noalloc: null pointer");
+    if (n_windows < 2 || n_windows > kNoAllocMaxWindows)
+        return fail(PMF_EINVAL, "pmf_free_energy_noalloc: n_windows must be in [2, 1024]");
+    if (replicas < 1 || (long long)n_windows * replicas > kNoAllocMaxWindowReplicas)
+        return fail(PMF_EINVAL, "pmf_free_energy_noalloc: n_windows * replicas must be in [1, 65536] "
+                                "(fixed scratch size)");
+    if (samples_per_window < 1) return fail(PMF_EINVAL, "pmf_free_energy_noalloc: samples_per_window >= 1");
+    if (!(k > 0) || !(kT > 0)) return fail(PMF_EINVAL, "pmf_free_energy_noalloc: need k > 0, kT > 0");
+    cudaError_t e = reduce_noalloc_launch(x, lambda, n_windows, replicas, samples_per_window, k, kT, out, g_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pmf_free_energy_noalloc");
+    return PMF_OK;
+}
+
 pmf_status pmf_final_state(const pmf_run *run, double *pos, double *vel, size_t capacity, size_t *n_written)
 {
     if (pmf_status s = need_finished(run)) return s;

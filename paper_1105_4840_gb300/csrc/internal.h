@@ -86,6 +86,12 @@ enum ResultField {
 // scratch: device buffer of reduce_scratch_bytes(); out: device [kResFields][n_windows]
 size_t reduce_scratch_bytes(int n_windows, int replicas);
 cudaError_t reduce_launch(const ReduceLayout &L, void *scratch, double *out, cudaStream_t st);
+// Allocation-free reduction: scratch in a fixed device array, equal samples
+// per window, all pointers on the device.
+constexpr int kNoAllocMaxWindows = 1024;
+constexpr long long kNoAllocMaxWindowReplicas = 65536;  // n_windows * replicas
+cudaError_t reduce_noalloc_launch(const float *x, const double *lambda, int n_windows, int replicas,
+                                  long long samples_per_window, double k, double kT, double *out, cudaStream_t st);
 cudaError_t work_samples_launch(const ReduceLayout &L, int mode, long long samples_per_replica, double *out,
                                 cudaStream_t st);
 

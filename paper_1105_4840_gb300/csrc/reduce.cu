@@ -15,6 +15,8 @@
 // samples is the product of the per-window averages.
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -273,6 +275,97 @@ cudaError_t work_samples_launch(const ReduceLayout &L, int mode, long long sampl
         const long long n = (long long)L.replicas * samples_per_replica;
         work_paired_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(L, samples_per_replica, out);
     }
+    return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the reduction (pmf_free_energy_noalloc).
+//
+// Its scratch (replica partials, window results, sample offsets) lives in one
+// file-scope device array of fixed size instead of memory obtained from
+// cudaMalloc.  Every GPU that loads the library holds this array until the
+// process exits, and every call on that GPU reuses it: two calls whose work
+// overlaps on the GPU (different streams, or a second call before the first
+// has finished) write the same scratch and race.  Nothing in it has to start
+// at zero: each call rewrites every entry it later reads.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t kNoAllocPartialBytes = sizeof(Partial) * (size_t)kNoAllocMaxWindowReplicas;
+constexpr size_t kNoAllocWindowBytes = sizeof(WindowOut) * (size_t)kNoAllocMaxWindows;
+constexpr size_t kNoAllocLayoutBytes = 2 * sizeof(long long) * (size_t)kNoAllocMaxWindows;
+constexpr size_t kNoAllocBytes = kNoAllocPartialBytes + kNoAllocWindowBytes + kNoAllocLayoutBytes;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Host side: the array's name is only a host stand-in; its device address is
+// looked up once per device (with that device current) and cached.
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+cudaError_t noalloc_scratch(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (g_noalloc_addr[dev] == nullptr) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+__global__ void noalloc_layout_kernel(long long *off, long long *tw, int n_windows, int replicas, long long T)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_windows) {
+        off[i] = (long long)i * replicas * T;
+        tw[i] = T;
+    }
+}
+
+}  // namespace
+
+cudaError_t reduce_noalloc_launch(const float *x, const double *lambda, int n_windows, int replicas,
+                                  long long samples_per_window, double k, double kT, double *out, cudaStream_t st)
+{
+    void *base = nullptr;
+    cudaError_t e = noalloc_scratch(&base);
+    if (e != cudaSuccess) return e;
+    unsigned char *b = static_cast<unsigned char *>(base);
+    long long *off = reinterpret_cast<long long *>(b + kNoAllocPartialBytes + kNoAllocWindowBytes);
+    long long *tw = off + kNoAllocMaxWindows;
+    noalloc_layout_kernel<<<(n_windows + 127) / 128, 128, 0, st>>>(off, tw, n_windows, replicas, samples_per_window);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    Partial *P = reinterpret_cast<Partial *>(b);
+    WindowOut *wo = reinterpret_cast<WindowOut *>(b + kNoAllocPartialBytes);
+    ReduceLayout L;
+    L.x = x;
+    L.lambda = lambda;
+    L.off_w = off;
+    L.tw = tw;
+    L.n_windows = n_windows;
+    L.replicas = replicas;
+    L.k = k;
+    L.kT = kT;
+    partial_kernel<<<dim3(n_windows, replicas), kPartialThreads, 0, st>>>(L, P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t smem = sizeof(double) * (size_t)replicas;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    window_kernel<<<n_windows, kWindowThreads, smem, st>>>(L, P, wo);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    profile_kernel<<<1, 32, 0, st>>>(L, wo, out);
     return cudaGetLastError();
 }
 

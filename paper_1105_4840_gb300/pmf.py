@@ -88,13 +88,16 @@ def _load():
     L.pmf_chain_schedule.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_size_t,
                                      C.POINTER(C.c_size_t), C.POINTER(C.c_int)]
     L.pmf_run_reduce.argtypes = [P]
+    L.pmf_free_energy_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64,
+                                          C.c_double, C.c_double, C.c_void_p]
     L.pmf_set_stream.argtypes = [C.c_void_p]
     L.pmf_last_error.restype = C.c_char_p
     L.pmf_version.restype = C.c_char_p
     for name in ("pmf_create_system", "pmf_run_windows", "pmf_run_prepare", "pmf_run_launch",
                  "pmf_run_wait", "pmf_get_run_info", "pmf_x_samples", "pmf_work_samples",
                  "pmf_free_energy", "pmf_free_energy_from_samples", "pmf_final_state", "pmf_philox",
-                 "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_set_stream"):
+                 "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_free_energy_noalloc",
+                 "pmf_set_stream"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -314,3 +317,12 @@ def pmf_chain_schedule(N, NW=4):
     _check(lib.pmf_chain_schedule(N, NW, out.ctypes.data_as(C.POINTER(C.c_int)), out.size, C.byref(n),
                                   C.byref(pad)), "pmf_chain_schedule")
     return out.reshape(-1, 6), pad.value
+
+
+def pmf_free_energy_noalloc(x_dev, lambda_dev, n_windows, replicas, samples_per_window, k, kT, out_dev):
+    """Allocation-free reduction; every pointer is an integer device address.
+    out_dev receives 14 * n_windows doubles (RESULT_FIELDS order).  Returns
+    after enqueueing on the library stream."""
+    _check(lib.pmf_free_energy_noalloc(C.c_void_p(int(x_dev)), C.c_void_p(int(lambda_dev)), n_windows,
+                                       replicas, samples_per_window, k, kT, C.c_void_p(int(out_dev))),
+           "pmf_free_energy_noalloc")

@@ -298,21 +298,32 @@ void orc_chain_forces(const orc_chain *c, const double *r, double lambda, double
     }
 }
 
-/* Maxwell-Boltzmann velocities: v = sqrt(kT/m) * n with n from the Philox
- * block (bead, uid, 0, TAG_INITVEL); the fourth normal is unused. */
+/* Standard normals for the 3N degrees of freedom of one replica at one
+ * step: block b of Philox counter (b, uid, step, tag) supplies the normals of
+ * dofs 4b .. 4b+3, dof d = 3 * bead + axis.  xi must hold 4 ceil(3N/4). */
+static void dof_normals(int n, uint64_t seed, uint32_t uid, uint32_t step, uint32_t tag, double *xi)
+{
+    const int nblk = (3 * n + 3) / 4;
+    for (int b = 0; b < nblk; ++b) orc_normals4(seed, (uint32_t)b, uid, step, tag, xi + 4 * b);
+}
+
+/* Maxwell-Boltzmann velocities: v = sqrt(kT/m) * xi with the dof normals of
+ * step 0 and tag TAG_INITVEL. */
 void orc_chain_init_velocities(const orc_chain *c, double kT, uint64_t seed, uint32_t uid, double *v)
 {
+    double *xi = (double *)malloc(sizeof(double) * 4 * (size_t)((3 * c->n + 3) / 4));
+    if (!xi) return;
+    dof_normals(c->n, seed, uid, 0u, ORC_TAG_INITVEL, xi);
     for (int i = 0; i < c->n; ++i) {
-        double nn[4];
-        orc_normals4(seed, (uint32_t)i, uid, 0u, ORC_TAG_INITVEL, nn);
         double s = sqrt(kT / c->mass[i]);
-        for (int a = 0; a < 3; ++a) v[3 * i + a] = s * nn[a];
+        for (int a = 0; a < 3; ++a) v[3 * i + a] = s * xi[3 * i + a];
     }
+    free(xi);
 }
 
 /* BAOAB Langevin integration of one replica in one window.
  *   per step n:  v += dt/2 F/m;  r += dt/2 v;
- *                v = c1 v + c2 sqrt(kT/m) xi_n   (xi from block (bead, uid, n, TAG_OSTEP));
+ *                v = c1 v + c2 sqrt(kT/m) xi_n   (dof normals of step n, TAG_OSTEP);
  *                r += dt/2 v;  F = F(r);  v += dt/2 F/m
  * with c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2).  After step n (1-based
  * count n+1 > n_equil with (n+1-n_equil) % stride == 0) x = |r_{N-1}-r_0| is
@@ -325,23 +336,23 @@ long orc_chain_run(const orc_chain *c, double lambda, double k, double kT, doubl
 {
     const int n = c->n;
     double *f = (double *)malloc(sizeof(double) * 3 * (size_t)n);
-    if (!f) return -1;
+    double *xi = (double *)malloc(sizeof(double) * 4 * (size_t)((3 * n + 3) / 4));
+    if (!f || !xi) { free(f); free(xi); return -1; }
     if (init_v) orc_chain_init_velocities(c, kT, seed, uid, v);
     const double c1 = exp(-gamma * dt);
     const double c2 = sqrt(1.0 - c1 * c1);
     orc_chain_forces(c, r, lambda, k, f);
     long ns = 0;
     for (long step = 0; step < n_steps; ++step) {
+        dof_normals(n, seed, uid, (uint32_t)step, ORC_TAG_OSTEP, xi);
         for (int i = 0; i < n; ++i) {
             double im = 1.0 / c->mass[i];
             double sv = sqrt(kT * im);
-            double xi[4];
-            orc_normals4(seed, (uint32_t)i, uid, (uint32_t)step, ORC_TAG_OSTEP, xi);
             for (int a = 0; a < 3; ++a) {
                 double *vv = v + 3 * i + a, *rr = r + 3 * i + a;
                 *vv += 0.5 * dt * f[3 * i + a] * im;
                 *rr += 0.5 * dt * (*vv);
-                *vv = c1 * (*vv) + c2 * sv * xi[a];
+                *vv = c1 * (*vv) + c2 * sv * xi[3 * i + a];
                 *rr += 0.5 * dt * (*vv);
             }
         }
@@ -352,9 +363,10 @@ long orc_chain_run(const orc_chain *c, double lambda, double k, double kT, doubl
         }
         long done = step + 1;
         if (done > n_equil && (done - n_equil) % stride == 0) samples[ns++] = orc_chain_rc(c, r);
-        if (!isfinite(r[0]) || !isfinite(r[3 * (n - 1)])) { free(f); return -1; }
+        if (!isfinite(r[0]) || !isfinite(r[3 * (n - 1)])) { free(f); free(xi); return -1; }
     }
     free(f);
+    free(xi);
     return ns;
 }
 

@@ -143,3 +143,40 @@ def seed_order(final_x, target):
     order[r mod len]."""
     final_x = np.asarray(final_x, dtype=np.float64)
     return np.argsort(np.abs(final_x - target), kind="stable")
+
+
+def normalise(lam, x, c, h):
+    """lambda' = (lambda - c) / h, x' = (x - c) / h."""
+    return (np.asarray(lam, dtype=np.float64) - c) / h, (np.asarray(x, dtype=np.float64) - c) / h
+
+
+def to_physical(out, c, h):
+    """(mu', s') -> (mu, log sigma^2) = (c + h mu', s' + 2 log h)."""
+    return c + h * out[:, 0], out[:, 1] + 2.0 * math.log(h)
+
+
+def minibatch(philox_bulk, seed, step, batch, total):
+    """Sample indices of one Adam step: Philox4x32-10 block j of counter
+    (j, step, 0, 3) gives index (word1 * 2^32 + word0) mod total."""
+    raw, _ = philox_bulk(seed, 0, step, 0, 3, batch)
+    r = (raw[:, 1].astype(np.uint64) << np.uint64(32)) | raw[:, 0].astype(np.uint64)
+    return (r % np.uint64(total)).astype(np.int64)
+
+
+def train(p, x_store, offsets, lambdas, steps, batch, lr, seed, c, h, philox_bulk, state=None, t0=0):
+    """Adam on mini-batches drawn from a run's sample store (layout
+    [window][replica][sample]; offsets[w] = first sample of window w)."""
+    state = {} if state is None else state
+    offsets = np.asarray(offsets, dtype=np.int64)
+    lam_w = np.asarray(lambdas, dtype=np.float64)
+    x_store = np.asarray(x_store, dtype=np.float64)
+    loss = math.nan
+    for step in range(steps):
+        idx = minibatch(philox_bulk, seed, t0 + step, batch, x_store.size)
+        w = np.searchsorted(offsets, idx, side="right") - 1
+        lam_n, x_n = normalise(lam_w[w], x_store[idx], c, h)
+        cache = forward(p, lam_n)
+        loss = nll(cache["out"], x_n)
+        g = backward(p, cache, x_n)
+        adam_step(p, g, state, lr)
+    return p, state, loss

@@ -99,8 +99,9 @@ void pmf_destroy_system(pmf_system *sys);
  * Chain: BAOAB Langevin with friction gamma (1/ps).  1D: overdamped
  * Euler-Maruyama x += F dt/gamma + sqrt(2 kT dt/gamma) xi.
  * Replica uid of (window w, replica r) = uid_base + w * replicas + r; the
- * Langevin noise of a replica is Philox4x32-10 with key seed and counter
- * (bead, uid, step, 0); initial velocities use counter (bead, uid, 0, 1).
+ * Langevin noise of a replica is Philox4x32-10 with key seed: block b of
+ * counter (b, uid, step, 0) gives the normals of degrees of freedom
+ * 4b..4b+3 (dof = 3 * bead + axis); initial velocities use (b, uid, 0, 1).
  */
 typedef struct {
     double k;                   /* trap stiffness (energy / length^2)            */
@@ -119,7 +120,7 @@ typedef struct {
 } pmf_run_params;
 
 /* PPP of Sec. III (ii): allocate the run, upload lambda[n_windows] (strictly
- * monotone, n_windows >= 2), launch every window x replica simulation from
+ * monotone, 1 <= n_windows <= 1024), launch every window x replica simulation from
  * the system's start state x_o, and wait.  Equivalent to pmf_run_prepare +
  * pmf_run_launch + pmf_run_wait.  *out is library-owned (pmf_destroy_run);
  * it is set even when the run fails with PMF_ENUMERIC / PMF_ETIMEOUT so the
@@ -136,6 +137,14 @@ pmf_status pmf_run_windows(pmf_system *sys, const double *lambda, int n_windows,
 pmf_status pmf_run_prepare(pmf_system *sys, const double *lambda, int n_windows,
                            const pmf_run_params *p, pmf_run **out);
 pmf_status pmf_run_launch(pmf_run *run);
+
+/* As pmf_run_prepare, but every replica starts from its own state instead
+ * of the common x_o: start[(w * replicas + r) * N * 3 + 3 b + axis] (chain)
+ * or start[w * replicas + r] (1D), host, copied.  Used to seed inserted
+ * windows from stored end states (the learned window placement); the
+ * paper's protocol itself starts every window from x_o (Sec. III (ii)). */
+pmf_status pmf_run_prepare_seeded(pmf_system *sys, const double *lambda, int n_windows, const pmf_run_params *p,
+                                  const double *start, pmf_run **out);
 pmf_status pmf_run_wait(pmf_run *run);
 void pmf_destroy_run(pmf_run *run);
 
@@ -236,6 +245,80 @@ pmf_status pmf_free_energy_noalloc(const float *x, const double *lambda, int n_w
 pmf_status pmf_final_state(const pmf_run *run, double *pos, double *vel, size_t capacity,
                            size_t *n_written);
 
+/* ---- learned window placement: surrogate MLP ---------------------------
+ * A small network lambda -> (mu, log sigma^2) of the reaction coordinate,
+ * 1 -> 64 -> 64 -> 2 with SiLU, trained on a run's (lambda_i, x) samples by
+ * the Gaussian negative log-likelihood 0.5 [log sigma^2 + (x - mu)^2 / sigma^2]
+ * with Adam.  It models the Gaussian rho(x_i) of Sec. II (the text before
+ * Eq. (13)) as a smooth function of lambda, so the overlap of adjacent x
+ * distributions (the criterion of Sec. III, Sec. IV B and Sec. V (iii)) can be
+ * predicted between windows.  Inputs and targets are normalised as
+ * lambda' = (lambda - c) / h, x' = (x - c) / h.  The 64 x 64 layer runs on
+ * the tensor cores in BF16 with FP32 accumulation (forward and backward);
+ * FP32 master weights.  Parameters are packed as W1[64], b1[64],
+ * W2[64][64] (row = output), b2[64], W3[2][64], b3[2]. */
+#define PMF_MLP_PARAMS 4418
+typedef struct pmf_mlp pmf_mlp;
+/* params: PMF_MLP_PARAMS initial FP32 weights (host, copied). */
+pmf_status pmf_mlp_create(const float *params, double c, double h, pmf_mlp **out);
+void pmf_mlp_destroy(pmf_mlp *mlp);
+/* Current FP32 weights into params[PMF_MLP_PARAMS] (host). */
+pmf_status pmf_mlp_get_params(const pmf_mlp *mlp, float *params);
+/* mu[n], log_var[n] (host) at lambda[n] (host), physical units. */
+pmf_status pmf_mlp_predict(pmf_mlp *mlp, const double *lambda, int n, double *mu, double *log_var);
+/* Gradient grad[PMF_MLP_PARAMS] (host) of the mean normalised NLL over the
+ * samples (lambda[n], x[n]) (host) and that loss (*loss, may be NULL);
+ * weights unchanged. */
+pmf_status pmf_mlp_gradient(pmf_mlp *mlp, const double *lambda, const float *x, int n, float *grad, double *loss);
+/* Adam training on a finished run: `steps` updates, each on `batch` samples
+ * (rounded up to a multiple of 128) drawn uniformly from the run's sample
+ * store by Philox4x32-10 with key seed, counter (j, step, 0, 3), index =
+ * (word1 << 32 | word0) mod total; the sample's window gives lambda.  lr is
+ * the Adam step size (beta 0.9 / 0.999, eps 1e-8).  *loss (may be NULL)
+ * receives the last batch's mean normalised NLL.  PMF_ETIMEOUT if a tensor
+ * core completion wait ran out (the kernel then stops and frees its tensor
+ * memory). */
+pmf_status pmf_mlp_train(pmf_mlp *mlp, const pmf_run *run, int steps, int batch, double lr, uint64_t seed,
+                         double *loss);
+
+/* ---- adaptive protocol: surrogate-guided window insertion -----------------
+ * Starting from windows lambda0[n0] (a coarse PPP run from x_o), repeat up
+ * to max_rounds times: train the surrogate on the samples of every window
+ * so far, predict N(mu, sigma^2) of x at each window, and insert the midpoint
+ * of every adjacent pair whose predicted overlap coefficient
+ * int min(p_i, p_{i+1}) is below overlap_threshold (the paper's criterion
+ * that adjacent distributions of x overlap comparably to their spread,
+ * Sec. III, Sec. IV B, Sec. V (iii)).  Each inserted window's replicas start
+ * from the stored end states of its two neighbours whose final x is nearest
+ * the predicted mean (replica r takes the candidate of rank r mod count) and
+ * run with the same parameters and fresh replica uids.  The estimators of
+ * pmf_free_energy are then evaluated on the merged non-uniform grid.
+ * gpu_seconds sums the device time of the simulations, the training, the
+ * predictions, the seeding and the reductions (CUDA events on the library
+ * stream). */
+typedef struct {
+    double overlap_threshold;   /* e.g. 0.3                                   */
+    int max_rounds;             /* insertion rounds (>= 0)                    */
+    int max_windows;            /* cap on the total window count (<= 1024)    */
+    int mlp_steps, mlp_batch;   /* Adam updates and batch per round           */
+    double mlp_lr;
+    uint64_t mlp_seed;
+    const float *mlp_init;      /* PMF_MLP_PARAMS initial weights (host)      */
+} pmf_adaptive_params;
+
+typedef struct {
+    int n_windows;              /* final window count                         */
+    int rounds;                 /* rounds that inserted windows               */
+    int inserted;               /* windows inserted in total                  */
+    double gpu_seconds;
+    double mlp_loss;            /* last training batch loss                    */
+    double lambda[1024];        /* final window centres, in path order        */
+} pmf_adaptive_info;
+
+/* res arrays must hold at least max_windows entries (res->capacity). */
+pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, const pmf_run_params *p,
+                            const pmf_adaptive_params *ap, pmf_adaptive_info *info, pmf_free_energy_result *res);
+
 /* ---- kernel-level entry points used by the parity tests ---------------- */
 
 /* The integrator's Philox4x32-10 and Box-Muller on the GPU: blocks with
@@ -251,13 +334,31 @@ pmf_status pmf_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint
 pmf_status pmf_chain_forces(pmf_system *sys, int chain, const double *pos, double lambda,
                             double k, double *forces);
 
-/* Host-side schedule of the nonbonded phase for a chain of N beads and NW
- * warps per CTA (no GPU needed): the ring units each warp executes, as
- * records of 6 ints (warp, I, J, t_begin, t_end, flags) in out[capacity];
- * *n_written receives the record count.  Tiles are 32 beads except a last
- * tile of 8, 16 or 32 (*padded receives the padded bead count).  PMF_EINVAL
- * if capacity < 6 * records. */
-pmf_status pmf_chain_schedule(int N, int NW, int *out, size_t capacity, size_t *n_written, int *padded);
+/* Overlap coefficients ovl[i] = int min(p_i, p_{i+1}) dx, i < n - 1, of the
+ * Gaussians N(mu_i, exp(log_var_i)) (host arrays), computed by the kernel
+ * the adaptive protocol uses. */
+pmf_status pmf_overlap(const double *mu, const double *log_var, int n, double *ovl);
+
+/* Host-side schedule of the nonbonded phase for a chain of N beads, NW
+ * warps per CTA and the integration precision (no GPU needed): the ring
+ * pieces each warp executes, as records of 8 ints (warp, I1, I2 or -1, J,
+ * kind, near1, near2, pair_next) in out[capacity]; *n_written receives the
+ * record count.  pair_next = 1: this width-32 packed piece runs interleaved
+ * with the warp's next record.  A piece pairs the 32-bead i-tile I1 (and I2) with j-tile J over the
+ * ring steps t of `kind`; lane l meets j = J*32 + ((l mod W) + t) mod W:
+ *   scalar (FP64):  0..3  W 32, t = 8k..8k+7        4, 5  W 32 diagonal, t = 1..8, 9..16
+ *                   6, 7  W 16, t = 0..7, 8..15      8     W 16 diagonal, t = 1..8
+ *                   9     W 8,  t = 0..7             10    W 8 diagonal, t = 1..4
+ *   packed (FP32, two steps t and t + D per f32x2 double step, D = 8 for W 32
+ *   and 16, 4 for W 8; kinds 8 and 10 as above):
+ *                   11    W 32, t = 0..7 (+8)        12    W 32, t = 16..23 (+8)
+ *                   13    W 32 diagonal, t = 1..8 (+8)
+ *                   14    W 16, t = 0..7 (+8)        15    W 8, t = 0..3 (+4)
+ * near1/near2 flag i-tiles adjacent to J (exclusions |i - j| <= 2 possible).
+ * Tiles are 32 beads except a last tile of 8, 16 or 32 (*padded receives the
+ * padded bead count).  PMF_EINVAL if capacity < 8 * records. */
+pmf_status pmf_chain_schedule(int N, int NW, int precision, int *out, size_t capacity, size_t *n_written,
+                              int *padded);
 
 /* Library stream: cudaStream_t passed as void* (NULL = legacy default). */
 pmf_status pmf_set_stream(void *stream);

@@ -1,0 +1,99 @@
+// Learned window placement, device side: overlap of adjacent predicted x
+// distributions and seeding of inserted windows.
+//
+// The paper's criterion (Sec. III after Eq. (9), Sec. IV B, Sec. V (iii)):
+// adjacent x distributions must overlap comparably to their spread.  With
+// the surrogate's Gaussian prediction N(mu_i, sigma_i^2) per window the
+// overlap coefficient OVL = int min(p_i, p_{i+1}) has a closed form: the two
+// pdfs cross where their log-densities agree (a quadratic in x), and between
+// the crossings the wider Gaussian is the smaller pdf.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace pmf {
+
+__device__ __forceinline__ double phi_cdf(double z) { return 0.5 * erfc(-z * 0.70710678118654752440); }
+
+__device__ double gaussian_ovl(double m1, double s1, double m2, double s2)
+{
+    if (fabs(s1 - s2) < 1e-12 * fmax(s1, s2)) return 2.0 * phi_cdf(-fabs(m1 - m2) / (2.0 * s1));
+    const double a = 1.0 / (2 * s2 * s2) - 1.0 / (2 * s1 * s1);
+    const double b = m1 / (s1 * s1) - m2 / (s2 * s2);
+    const double c = m2 * m2 / (2 * s2 * s2) - m1 * m1 / (2 * s1 * s1) + log(s2 / s1);
+    const double disc = fmax(b * b - 4 * a * c, 0.0);
+    double r1 = (-b - sqrt(disc)) / (2 * a), r2 = (-b + sqrt(disc)) / (2 * a);
+    if (r1 > r2) { const double t = r1; r1 = r2; r2 = t; }
+    const double mw = s1 > s2 ? m1 : m2, sw = s1 > s2 ? s1 : s2;
+    const double mn = s1 > s2 ? m2 : m1, sn = s1 > s2 ? s2 : s1;
+    const double inside = phi_cdf((r2 - mw) / sw) - phi_cdf((r1 - mw) / sw);
+    const double outside = phi_cdf((r1 - mn) / sn) + (1.0 - phi_cdf((r2 - mn) / sn));
+    return inside + outside;
+}
+
+__global__ void overlap_kernel(const double *mu, const double *log_var, int n, double *ovl)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i + 1 >= n) return;
+    ovl[i] = gaussian_ovl(mu[i], exp(0.5 * log_var[i]), mu[i + 1], exp(0.5 * log_var[i + 1]));
+}
+
+cudaError_t overlap_launch(const double *mu, const double *log_var, int n, double *ovl, cudaStream_t st)
+{
+    if (n < 2) return cudaSuccess;
+    overlap_kernel<<<(n + 127) / 128, 128, 0, st>>>(mu, log_var, n, ovl);
+    return cudaGetLastError();
+}
+
+// Seeding: block q fills the start states of inserted window q.  Its M
+// candidates are stored end states (positions of M replicas of the two
+// neighbouring windows); replica r starts from the candidate of rank r mod M
+// when candidates are ordered by |x_final - target_q| (ties by index).
+template <typename R>
+__global__ void seed_kernel(const SeedJob *jobs, int N, int Np, int replicas, double *start)
+{
+    extern __shared__ double dist[];  // [M]
+    const SeedJob &J = jobs[blockIdx.x];
+    const int M = J.n_cand;
+    for (int c = threadIdx.x; c < M; c += blockDim.x) {
+        double x;
+        if (N > 0) {
+            const R *p = reinterpret_cast<const R *>(J.cand[c]);  // positions, 4 values per bead
+            const double dx = (double)p[4 * (N - 1) + 0] - (double)p[0];
+            const double dy = (double)p[4 * (N - 1) + 1] - (double)p[1];
+            const double dz = (double)p[4 * (N - 1) + 2] - (double)p[2];
+            x = sqrt(dx * dx + dy * dy + dz * dz);
+        } else {
+            x = *reinterpret_cast<const double *>(J.cand[c]);
+        }
+        dist[c] = fabs(x - J.target);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < M; c += blockDim.x) {
+        int rank = 0;
+        for (int d = 0; d < M; ++d) rank += (dist[d] < dist[c]) || (dist[d] == dist[c] && d < c);
+        for (int r = rank; r < replicas; r += M) {
+            double *out = start + ((size_t)blockIdx.x * replicas + r) * (N > 0 ? 3 * (size_t)N : 1);
+            if (N > 0) {
+                const R *p = reinterpret_cast<const R *>(J.cand[c]);
+                for (int b = 0; b < N; ++b)
+                    for (int k = 0; k < 3; ++k) out[3 * b + k] = (double)p[4 * b + k];
+            } else {
+                out[0] = *reinterpret_cast<const double *>(J.cand[c]);
+            }
+        }
+    }
+}
+
+cudaError_t seed_launch(const SeedJob *jobs, int n_jobs, int max_cand, int N, int Np, int replicas, bool fp64,
+                        double *start, cudaStream_t st)
+{
+    if (n_jobs == 0) return cudaSuccess;
+    const size_t smem = sizeof(double) * (size_t)max_cand;
+    if (fp64 || N == 0) seed_kernel<double><<<n_jobs, 128, smem, st>>>(jobs, N, Np, replicas, start);
+    else seed_kernel<float><<<n_jobs, 128, smem, st>>>(jobs, N, Np, replicas, start);
+    return cudaGetLastError();
+}
+
+}  // namespace pmf

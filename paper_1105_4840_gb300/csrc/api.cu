@@ -1,4 +1,5 @@
 // C ABI of libpmf: handles, argument checks, orchestration of the kernels.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -72,6 +73,7 @@ struct pmf_run {
     int *d_err = nullptr;
     void *d_scratch = nullptr;
     double *d_res = nullptr;
+    double *d_start = nullptr;  // per-replica start state of a seeded run
     cudaEvent_t done = nullptr;
     bool launched = false, finished = false, reduced = false;
     size_t state_bytes = 0;
@@ -88,9 +90,17 @@ struct pmf_run {
         cudaFree(d_err);
         cudaFree(d_scratch);
         cudaFree(d_res);
+        cudaFree(d_start);
         if (done) cudaEventDestroy(done);
     }
 };
+
+static pmf_status need_finished(const pmf_run *run)
+{
+    if (!run) return fail(PMF_EINVAL, "null run");
+    if (!run->finished) return fail(PMF_ESTATE, "run has not finished (call pmf_run_wait)");
+    return PMF_OK;
+}
 
 extern "C" {
 
@@ -179,8 +189,8 @@ pmf_status pmf_run_prepare(pmf_system *sys, const double *lambda, int n_windows,
 {
     if (!sys || !lambda || !p || !out) return fail(PMF_EINVAL, "pmf_run_prepare: null argument");
     *out = nullptr;
-    if (n_windows < 2 || n_windows > 1024) return fail(PMF_EINVAL, "n_windows must be in [2, 1024]");
-    const double sgn = lambda[1] > lambda[0] ? 1.0 : -1.0;
+    if (n_windows < 1 || n_windows > 1024) return fail(PMF_EINVAL, "n_windows must be in [1, 1024]");
+    const double sgn = (n_windows > 1 && lambda[1] < lambda[0]) ? -1.0 : 1.0;
     for (int i = 0; i < n_windows; ++i) {
         if (!std::isfinite(lambda[i])) return fail(PMF_EINVAL, "lambda must be finite");
         if (i > 0 && !((lambda[i] - lambda[i - 1]) * sgn > 0)) return fail(PMF_EINVAL, "lambda must be strictly monotone");
@@ -254,6 +264,7 @@ pmf_status pmf_run_launch(pmf_run *run)
     L.off_w = run->d_off;
     L.tw = run->d_tw;
     L.err = run->d_err;
+    L.start = run->d_start;
     L.replicas = run->replicas;
     L.stride = run->stride;
     L.uid_base = run->uid_base;
@@ -302,6 +313,30 @@ pmf_status pmf_run_wait(pmf_run *run)
     return PMF_OK;
 }
 
+pmf_status pmf_run_prepare_seeded(pmf_system *sys, const double *lambda, int n_windows, const pmf_run_params *p,
+                                  const double *start, pmf_run **out)
+{
+    if (!start) return fail(PMF_EINVAL, "pmf_run_prepare_seeded: null start");
+    pmf_status s = pmf_run_prepare(sys, lambda, n_windows, p, out);
+    if (s != PMF_OK) return s;
+    pmf_run *run = *out;
+    const size_t n_rep = (size_t)n_windows * p->replicas;
+    const size_t per = sys->model == PMF_MODEL_CHAIN ? (size_t)sys->chains[p->chain]->n_beads() * 3 : 1;
+    for (size_t i = 0; i < n_rep * per; ++i)
+        if (!std::isfinite(start[i])) {
+            pmf_destroy_run(run);
+            *out = nullptr;
+            return fail(PMF_EINVAL, "pmf_run_prepare_seeded: non-finite start state");
+        }
+    cudaError_t e = upload(&run->d_start, start, n_rep * per);
+    if (e != cudaSuccess) {
+        pmf_destroy_run(run);
+        *out = nullptr;
+        return cuda_fail(e, "upload start states");
+    }
+    return PMF_OK;
+}
+
 pmf_status pmf_run_windows(pmf_system *sys, const double *lambda, int n_windows, const pmf_run_params *p,
                            pmf_run **out)
 {
@@ -327,12 +362,6 @@ pmf_status pmf_get_run_info(const pmf_run *run, pmf_run_info *info)
     return PMF_OK;
 }
 
-static pmf_status need_finished(const pmf_run *run)
-{
-    if (!run) return fail(PMF_EINVAL, "null run");
-    if (!run->finished) return fail(PMF_ESTATE, "run has not finished (call pmf_run_wait)");
-    return PMF_OK;
-}
 
 pmf_status pmf_x_samples(const pmf_run *run, float *out, size_t capacity, size_t *n_written)
 {
@@ -472,6 +501,411 @@ pmf_status pmf_free_energy_from_samples(const float *x, int x_on_device, const d
     return copy_result(h.data(), n_windows, res);
 }
 
+// ---------------------------------------------------------------- surrogate MLP
+
+struct pmf_mlp {
+    float *params = nullptr, *m = nullptr, *v = nullptr;
+    int *err = nullptr;
+    int t = 0;
+    double c = 0, h = 1;
+    ~pmf_mlp()
+    {
+        cudaFree(params);
+        cudaFree(m);
+        cudaFree(v);
+        cudaFree(err);
+    }
+};
+
+pmf_status pmf_mlp_create(const float *params, double c, double h, pmf_mlp **out)
+{
+    if (!params || !out) return fail(PMF_EINVAL, "pmf_mlp_create: null argument");
+    *out = nullptr;
+    if (!std::isfinite(c) || !(h > 0) || !std::isfinite(h)) return fail(PMF_EINVAL, "pmf_mlp_create: need finite c, h > 0");
+    for (int i = 0; i < kMlpParams; ++i)
+        if (!std::isfinite(params[i])) return fail(PMF_EINVAL, "pmf_mlp_create: non-finite weight");
+    if (pmf_status s = need_device()) return s;
+    auto m = std::make_unique<pmf_mlp>();
+    m->c = c;
+    m->h = h;
+    CK(upload(&m->params, params, kMlpParams), "mlp params");
+    CK(cudaMalloc(&m->m, sizeof(float) * kMlpParams), "mlp adam");
+    CK(cudaMalloc(&m->v, sizeof(float) * kMlpParams), "mlp adam");
+    CK(cudaMemset(m->m, 0, sizeof(float) * kMlpParams), "mlp adam");
+    CK(cudaMemset(m->v, 0, sizeof(float) * kMlpParams), "mlp adam");
+    CK(cudaMalloc(&m->err, sizeof(int)), "mlp flag");
+    CK(cudaMemset(m->err, 0, sizeof(int)), "mlp flag");
+    *out = m.release();
+    return PMF_OK;
+}
+
+void pmf_mlp_destroy(pmf_mlp *mlp) { delete mlp; }
+
+pmf_status pmf_mlp_get_params(const pmf_mlp *mlp, float *params)
+{
+    if (!mlp || !params) return fail(PMF_EINVAL, "null argument");
+    CK(cudaMemcpyAsync(params, mlp->params, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, g_stream), "copy");
+    CK(cudaStreamSynchronize(g_stream), "sync");
+    return PMF_OK;
+}
+
+static pmf_status mlp_run(pmf_mlp *mlp, MlpLaunch &L, const char *where)
+{
+    L.params = mlp->params;
+    L.adam_m = mlp->m;
+    L.adam_v = mlp->v;
+    L.c = mlp->c;
+    L.h = mlp->h;
+    L.err = mlp->err;
+    CK(cudaMemsetAsync(mlp->err, 0, sizeof(int), g_stream), where);
+    cudaError_t e = mlp_launch(L, g_stream);
+    if (e != cudaSuccess) return cuda_fail(e, where);
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, mlp->err, sizeof(int), cudaMemcpyDeviceToHost, g_stream), where);
+    CK(cudaStreamSynchronize(g_stream), where);
+    if (err) return fail(PMF_ETIMEOUT, std::string(where) + ": tensor-core completion wait timed out");
+    return PMF_OK;
+}
+
+pmf_status pmf_mlp_predict(pmf_mlp *mlp, const double *lambda, int n, double *mu, double *log_var)
+{
+    if (!mlp || !lambda || !mu || !log_var || n < 0) return fail(PMF_EINVAL, "pmf_mlp_predict: bad argument");
+    if (n == 0) return PMF_OK;
+    struct Tmp {
+        double *lam = nullptr, *mu = nullptr, *lv = nullptr;
+        ~Tmp() { cudaFree(lam); cudaFree(mu); cudaFree(lv); }
+    } t;
+    CK(upload(&t.lam, lambda, n), "upload lambda");
+    CK(cudaMalloc(&t.mu, sizeof(double) * n), "alloc");
+    CK(cudaMalloc(&t.lv, sizeof(double) * n), "alloc");
+    MlpLaunch L;
+    L.mode = 0;
+    L.lam_in = t.lam;
+    L.n = n;
+    L.out_mu = t.mu;
+    L.out_logvar = t.lv;
+    if (pmf_status s = mlp_run(mlp, L, "pmf_mlp_predict")) return s;
+    CK(cudaMemcpy(mu, t.mu, sizeof(double) * n, cudaMemcpyDeviceToHost), "copy");
+    CK(cudaMemcpy(log_var, t.lv, sizeof(double) * n, cudaMemcpyDeviceToHost), "copy");
+    return PMF_OK;
+}
+
+pmf_status pmf_mlp_gradient(pmf_mlp *mlp, const double *lambda, const float *x, int n, float *grad, double *loss)
+{
+    if (!mlp || !lambda || !x || !grad || n < 1) return fail(PMF_EINVAL, "pmf_mlp_gradient: bad argument");
+    struct Tmp {
+        double *lam = nullptr, *loss = nullptr;
+        float *x = nullptr, *g = nullptr;
+        ~Tmp() { cudaFree(lam); cudaFree(loss); cudaFree(x); cudaFree(g); }
+    } t;
+    CK(upload(&t.lam, lambda, n), "upload lambda");
+    CK(upload(&t.x, x, n), "upload x");
+    CK(cudaMalloc(&t.g, sizeof(float) * kMlpParams), "alloc");
+    CK(cudaMalloc(&t.loss, sizeof(double)), "alloc");
+    MlpLaunch L;
+    L.mode = 1;
+    L.lam_in = t.lam;
+    L.x_in = t.x;
+    L.n = n;
+    L.out_grad = t.g;
+    L.out_loss = t.loss;
+    if (pmf_status s = mlp_run(mlp, L, "pmf_mlp_gradient")) return s;
+    CK(cudaMemcpy(grad, t.g, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost), "copy");
+    if (loss) CK(cudaMemcpy(loss, t.loss, sizeof(double), cudaMemcpyDeviceToHost), "copy");
+    return PMF_OK;
+}
+
+pmf_status pmf_mlp_train(pmf_mlp *mlp, const pmf_run *run, int steps, int batch, double lr, uint64_t seed,
+                         double *loss)
+{
+    if (!mlp || !run || steps < 0 || batch < 1 || batch > (1 << 20) || !(lr > 0))
+        return fail(PMF_EINVAL, "pmf_mlp_train: bad argument");
+    if (pmf_status s = need_finished(run)) return s;
+    if (steps == 0) return PMF_OK;
+    double *dloss = nullptr;
+    CK(cudaMalloc(&dloss, sizeof(double)), "alloc");
+    MlpLaunch L;
+    L.mode = 2;
+    L.adam_t = mlp->t;
+    L.lr = lr;
+    L.xs = run->d_x;
+    L.win_lambda = run->d_lambda;
+    L.win_off = run->d_off;
+    L.win_tw = run->d_tw;
+    L.n_windows = run->n_windows;
+    L.replicas = run->replicas;
+    L.total = run->total;
+    L.steps = steps;
+    L.batch = batch;
+    L.seed = seed;
+    L.out_loss = dloss;
+    pmf_status s = mlp_run(mlp, L, "pmf_mlp_train");
+    if (s == PMF_OK) {
+        mlp->t += steps;
+        if (loss) {
+            cudaError_t e = cudaMemcpy(loss, dloss, sizeof(double), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) s = cuda_fail(e, "copy loss");
+        }
+    }
+    cudaFree(dloss);
+    return s;
+}
+
+// ---------------------------------------------------------------- adaptive protocol
+
+namespace {
+
+struct GpuTimer {
+    double ms = 0.0;
+    cudaEvent_t a = nullptr, b = nullptr;
+    GpuTimer()
+    {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+    ~GpuTimer()
+    {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+    void start() { cudaEventRecord(a, g_stream); }
+    cudaError_t stop()
+    {
+        cudaEventRecord(b, g_stream);
+        cudaError_t e = cudaEventSynchronize(b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        ms += t;
+        return e;
+    }
+};
+
+struct Window {
+    double lam;
+    pmf_run *run;
+    int w;  // window index inside run
+};
+
+// Samples of several runs' windows merged in path order (device copies).
+struct Merged {
+    float *x = nullptr;
+    double *lam = nullptr;
+    long long *off = nullptr, *tw = nullptr;
+    long long total = 0;
+    int n = 0;
+    ~Merged() { cudaFree(x); cudaFree(lam); cudaFree(off); cudaFree(tw); }
+};
+
+cudaError_t merge_windows(const std::vector<Window> &win, int replicas, Merged &m)
+{
+    m.n = (int)win.size();
+    std::vector<double> lam(m.n);
+    std::vector<long long> off(m.n), tw(m.n);
+    long long total = 0;
+    for (int i = 0; i < m.n; ++i) {
+        lam[i] = win[i].lam;
+        tw[i] = win[i].run->tw[win[i].w];
+        off[i] = total;
+        total += tw[i] * replicas;
+    }
+    m.total = total;
+    cudaError_t e;
+    if ((e = cudaMalloc(&m.x, sizeof(float) * total)) != cudaSuccess) return e;
+    for (int i = 0; i < m.n; ++i) {
+        const pmf_run *r = win[i].run;
+        e = cudaMemcpyAsync(m.x + off[i], r->d_x + r->off[win[i].w], sizeof(float) * tw[i] * replicas,
+                            cudaMemcpyDeviceToDevice, g_stream);
+        if (e != cudaSuccess) return e;
+    }
+    if ((e = upload(&m.lam, lam.data(), m.n)) != cudaSuccess) return e;
+    if ((e = upload(&m.off, off.data(), m.n)) != cudaSuccess) return e;
+    return upload(&m.tw, tw.data(), m.n);
+}
+
+}  // namespace
+
+pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, const pmf_run_params *p,
+                            const pmf_adaptive_params *ap, pmf_adaptive_info *info, pmf_free_energy_result *res)
+{
+    if (!sys || !lambda0 || !p || !ap || !info || !res || !ap->mlp_init)
+        return fail(PMF_EINVAL, "pmf_run_adaptive: null argument");
+    if (ap->max_windows < n0 || ap->max_windows > 1024 || ap->max_rounds < 0 || !(ap->overlap_threshold >= 0) ||
+        ap->overlap_threshold > 1 || ap->mlp_steps < 0 || ap->mlp_batch < 1 || !(ap->mlp_lr > 0))
+        return fail(PMF_EINVAL, "pmf_run_adaptive: bad adaptive parameters");
+    if (res->capacity < ap->max_windows) return fail(PMF_EINVAL, "pmf_run_adaptive: result capacity < max_windows");
+    std::memset(info, 0, sizeof(*info));
+    GpuTimer timer;
+    std::vector<std::unique_ptr<pmf_run, void (*)(pmf_run *)>> runs;
+    auto own = [&](pmf_run *r) { runs.emplace_back(r, pmf_destroy_run); };
+    pmf_run *r0 = nullptr;
+    pmf_status st = pmf_run_prepare(sys, lambda0, n0, p, &r0);
+    if (st != PMF_OK) return st;
+    own(r0);
+    timer.start();
+    if ((st = pmf_run_launch(r0)) != PMF_OK) return st;
+    if ((st = pmf_run_wait(r0)) != PMF_OK) return st;
+    CK(timer.stop(), "timer");
+    const double dir = lambda0[n0 - 1] > lambda0[0] ? 1.0 : -1.0;
+    std::vector<Window> win;
+    for (int i = 0; i < n0; ++i) win.push_back(Window{lambda0[i], r0, i});
+    uint32_t uid_next = p->uid_base + (uint32_t)(n0 * p->replicas);
+    const int R = p->replicas;
+    double lo = lambda0[0], hi = lambda0[0];
+    for (int i = 0; i < n0; ++i) { lo = std::min(lo, lambda0[i]); hi = std::max(hi, lambda0[i]); }
+    pmf_mlp *mlp_raw = nullptr;
+    if ((st = pmf_mlp_create(ap->mlp_init, 0.5 * (lo + hi), std::max(0.5 * (hi - lo), 1e-6), &mlp_raw)) != PMF_OK)
+        return st;
+    std::unique_ptr<pmf_mlp, void (*)(pmf_mlp *)> mlp(mlp_raw, pmf_mlp_destroy);
+    const bool chain = sys->model == PMF_MODEL_CHAIN;
+    const int N = chain ? sys->chains[p->chain]->n_beads() : 0;
+    const int Np = chain ? sys->chains[p->chain]->n_padded() : 0;
+    const bool fp64 = chain && sys->chains[p->chain]->precision() == PMF_FP64;
+    const size_t state_stride = chain ? sys->chains[p->chain]->state_bytes_per_replica() : sizeof(double);
+    for (int round = 0; round < ap->max_rounds; ++round) {
+        std::sort(win.begin(), win.end(), [&](const Window &a, const Window &b) { return dir * a.lam < dir * b.lam; });
+        Merged m;
+        timer.start();
+        CK(merge_windows(win, R, m), "merge samples");
+        MlpLaunch L;
+        L.mode = 2;
+        L.adam_t = mlp->t;
+        L.lr = ap->mlp_lr;
+        L.xs = m.x;
+        L.win_lambda = m.lam;
+        L.win_off = m.off;
+        L.win_tw = m.tw;
+        L.n_windows = m.n;
+        L.replicas = R;
+        L.total = m.total;
+        L.steps = ap->mlp_steps;
+        L.batch = ap->mlp_batch;
+        L.seed = ap->mlp_seed + (uint64_t)round;
+        double *dloss = nullptr;
+        CK(cudaMalloc(&dloss, sizeof(double)), "alloc");
+        L.out_loss = dloss;
+        if (ap->mlp_steps > 0) {
+            if ((st = mlp_run(mlp.get(), L, "pmf_run_adaptive: training")) != PMF_OK) { cudaFree(dloss); return st; }
+            mlp->t += ap->mlp_steps;
+            cudaMemcpy(&info->mlp_loss, dloss, sizeof(double), cudaMemcpyDeviceToHost);
+        }
+        cudaFree(dloss);
+        // predictions at the windows and at the candidate midpoints
+        std::vector<double> lam(m.n), mids(m.n > 1 ? m.n - 1 : 0);
+        for (int i = 0; i < m.n; ++i) lam[i] = win[i].lam;
+        for (int i = 0; i + 1 < m.n; ++i) mids[i] = 0.5 * (lam[i] + lam[i + 1]);
+        std::vector<double> mu(m.n), lv(m.n), mu_mid(mids.size()), lv_mid(mids.size()), ovl(mids.size());
+        if ((st = pmf_mlp_predict(mlp.get(), lam.data(), m.n, mu.data(), lv.data())) != PMF_OK) return st;
+        if (!mids.empty() && (st = pmf_mlp_predict(mlp.get(), mids.data(), (int)mids.size(), mu_mid.data(), lv_mid.data())) != PMF_OK)
+            return st;
+        {
+            double *d_mu = nullptr, *d_lv = nullptr, *d_ovl = nullptr;
+            cudaError_t e = upload(&d_mu, mu.data(), m.n);
+            if (e == cudaSuccess) e = upload(&d_lv, lv.data(), m.n);
+            if (e == cudaSuccess) e = cudaMalloc(&d_ovl, sizeof(double) * std::max<size_t>(1, mids.size()));
+            if (e == cudaSuccess) e = overlap_launch(d_mu, d_lv, m.n, d_ovl, g_stream);
+            if (e == cudaSuccess && !mids.empty())
+                e = cudaMemcpyAsync(ovl.data(), d_ovl, sizeof(double) * mids.size(), cudaMemcpyDeviceToHost, g_stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+            cudaFree(d_mu);
+            cudaFree(d_lv);
+            cudaFree(d_ovl);
+            if (e != cudaSuccess) return cuda_fail(e, "overlap");
+        }
+        CK(timer.stop(), "timer");
+        std::vector<int> pick;
+        for (size_t i = 0; i < mids.size(); ++i)
+            if (ovl[i] < ap->overlap_threshold && (int)(win.size() + pick.size()) < ap->max_windows) pick.push_back((int)i);
+        if (pick.empty()) break;
+        // seed jobs: candidates = end states of the two neighbours
+        std::vector<SeedJob> jobs(pick.size());
+        std::vector<double> new_lam(pick.size());
+        int max_cand = 0;
+        for (size_t q = 0; q < pick.size(); ++q) {
+            const int i = pick[q];
+            new_lam[q] = mids[i];
+            jobs[q].target = mu_mid[i];
+            int nc = 0;
+            for (int side = 0; side < 2; ++side) {
+                const Window &nb = win[i + side];
+                for (int r = 0; r < R && nc < kMaxSeedCandidates; ++r) {
+                    const size_t rep = (size_t)nb.w * nb.run->replicas + r;
+                    jobs[q].cand[nc++] = static_cast<const char *>(nb.run->d_state) + rep * state_stride;
+                }
+            }
+            jobs[q].n_cand = nc;
+            max_cand = std::max(max_cand, nc);
+        }
+        pmf_run_params p2 = *p;
+        p2.uid_base = uid_next;
+        p2.n_steps_per_window = nullptr;
+        pmf_run *rn = nullptr;
+        if ((st = pmf_run_prepare(sys, new_lam.data(), (int)new_lam.size(), &p2, &rn)) != PMF_OK) return st;
+        own(rn);
+        SeedJob *d_jobs = nullptr;
+        timer.start();
+        CK(upload(&d_jobs, jobs.data(), jobs.size()), "upload seed jobs");
+        const size_t per = chain ? 3 * (size_t)N : 1;
+        cudaError_t e = cudaMalloc(&rn->d_start, sizeof(double) * per * R * new_lam.size());
+        if (e == cudaSuccess) e = seed_launch(d_jobs, (int)jobs.size(), max_cand, N, Np, R, fp64, rn->d_start, g_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+        cudaFree(d_jobs);
+        if (e != cudaSuccess) return cuda_fail(e, "seed");
+        if ((st = pmf_run_launch(rn)) != PMF_OK) return st;
+        if ((st = pmf_run_wait(rn)) != PMF_OK) return st;
+        CK(timer.stop(), "timer");
+        for (size_t q = 0; q < new_lam.size(); ++q) win.push_back(Window{new_lam[q], rn, (int)q});
+        uid_next += (uint32_t)(new_lam.size() * R);
+        info->rounds = round + 1;
+        info->inserted += (int)new_lam.size();
+    }
+    std::sort(win.begin(), win.end(), [&](const Window &a, const Window &b) { return dir * a.lam < dir * b.lam; });
+    Merged m;
+    timer.start();
+    CK(merge_windows(win, R, m), "merge samples");
+    void *scratch = nullptr;
+    double *d_res = nullptr;
+    CK(cudaMalloc(&scratch, reduce_scratch_bytes(m.n, R)), "alloc");
+    cudaError_t e = cudaMalloc(&d_res, sizeof(double) * kResFields * m.n);
+    ReduceLayout RL;
+    RL.x = m.x;
+    RL.lambda = m.lam;
+    RL.off_w = m.off;
+    RL.tw = m.tw;
+    RL.n_windows = m.n;
+    RL.replicas = R;
+    RL.k = p->k;
+    RL.kT = p->kT;
+    if (e == cudaSuccess) e = reduce_launch(RL, scratch, d_res, g_stream);
+    std::vector<double> h((size_t)kResFields * m.n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_res, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g_stream);
+    if (e == cudaSuccess) e = timer.stop();
+    cudaFree(scratch);
+    cudaFree(d_res);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce");
+    info->n_windows = m.n;
+    for (int i = 0; i < m.n; ++i) info->lambda[i] = win[i].lam;
+    info->gpu_seconds = timer.ms / 1000.0;
+    return copy_result(h.data(), m.n, res);
+}
+
+pmf_status pmf_overlap(const double *mu, const double *log_var, int n, double *ovl)
+{
+    if (!mu || !log_var || !ovl || n < 2) return fail(PMF_EINVAL, "pmf_overlap: bad argument");
+    if (pmf_status s = need_device()) return s;
+    double *d_mu = nullptr, *d_lv = nullptr, *d_ovl = nullptr;
+    cudaError_t e = upload(&d_mu, mu, n);
+    if (e == cudaSuccess) e = upload(&d_lv, log_var, n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_ovl, sizeof(double) * (n - 1));
+    if (e == cudaSuccess) e = overlap_launch(d_mu, d_lv, n, d_ovl, g_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ovl, d_ovl, sizeof(double) * (n - 1), cudaMemcpyDeviceToHost, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    cudaFree(d_mu);
+    cudaFree(d_lv);
+    cudaFree(d_ovl);
+    if (e != cudaSuccess) return cuda_fail(e, "pmf_overlap");
+    return PMF_OK;
+}
+
 pmf_status pmf_free_energy_noalloc(const float *x, const double *lambda, int n_windows, int replicas,
                                    int64_t samples_per_window, double k, double kT, double *out)
 {
@@ -538,20 +972,23 @@ pmf_status pmf_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint
     return PMF_OK;
 }
 
-pmf_status pmf_chain_schedule(int N, int NW, int *out, size_t capacity, size_t *n_written, int *padded)
+pmf_status pmf_chain_schedule(int N, int NW, int precision, int *out, size_t capacity, size_t *n_written,
+                              int *padded)
 {
-    if (N < 4 || N > 1024 || (NW != 4 && NW != 8)) return fail(PMF_EINVAL, "pmf_chain_schedule: N in [4,1024], NW 4 or 8");
-    const auto sched = chain_schedule(N, NW, kChainUnitPiece);
+    if (N < 4 || N > 1024 || (NW != 4 && NW != 8) || (precision != PMF_FP32 && precision != PMF_FP64))
+        return fail(PMF_EINVAL, "pmf_chain_schedule: N in [4,1024], NW 4 or 8, precision FP32 or FP64");
+    const auto sched = chain_schedule(N, NW, precision == PMF_FP32);
     size_t n = 0;
     for (const auto &v : sched) n += v.size();
     if (n_written) *n_written = n;
     if (padded) *padded = chain_geometry(N).Np;
-    if (!out || capacity < 6 * n) return fail(PMF_EINVAL, "pmf_chain_schedule: capacity too small");
+    if (!out || capacity < 8 * n) return fail(PMF_EINVAL, "pmf_chain_schedule: capacity too small");
     size_t q = 0;
     for (int w = 0; w < NW; ++w)
         for (const UnitDesc &u : sched[w]) {
-            int *o = out + 6 * q++;
-            o[0] = w; o[1] = u.I; o[2] = u.J; o[3] = u.tb; o[4] = u.te; o[5] = u.flags;
+            int *o = out + 8 * q++;
+            o[0] = w; o[1] = u.I1; o[2] = u.I2; o[3] = u.J; o[4] = u.kind; o[5] = u.near1; o[6] = u.near2;
+            o[7] = u.pair_next;
         }
     return PMF_OK;
 }

@@ -54,6 +54,7 @@ template <typename R> struct ChainArgs {
     const int *unit_count;     // [NW]
     int *err;
     double *force_out;         // optional [N][3]: forces at the final positions
+    const double *start;       // optional [n_rep][N][3]: start positions instead of x_o
     long long step_begin, step_end;
     int N, Np, n_tiles, w_last, replicas, max_units, stride;
     uint32_t uid_base;
@@ -79,6 +80,10 @@ template <typename R> __device__ __forceinline__ V3<R> cross(V3<R> a, V3<R> b)
     return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 
+// FP32 uses the packed f32x2 pair engine; FP64 the scalar ring pieces.
+template <typename R> constexpr bool kPacked = false;
+template <> constexpr bool kPacked<float> = true;
+
 // Shared-memory views of one replica.
 template <typename R> struct Smem {
     Vec4<R> *posd;   // [n_tiles][64]: tile copy then its duplicate
@@ -86,8 +91,18 @@ template <typename R> struct Smem {
     Vec4<R> *vel;    // [Np]
     Vec4<R> *fw;     // [NW][Np]
     Vec4<R> *bslot;  // [4][Np]
+    R *noise;        // [4 * n_blocks] normals of the next O-step, dof d = 3 b + axis
+    // FP32 packed path: entry p of tile T pairs ring positions p and p + D
+    // (D = pair_offset(W)): posp[2(64T + p)] = (x_p, x_{p+D}, y_p, y_{p+D}),
+    // posp[2(64T + p) + 1] = (z_p, z_{p+D}, s_p, s_{p+D}),
+    // eqp[64T + p] = (e_p, e_{p+D}, q_p, q_{p+D}), p < 2W.
+    float4 *posp;
+    float4 *eqp;
     int *flag;
 };
+
+// Offset between the two ring steps a packed FP32 double step evaluates.
+__host__ __device__ constexpr int pair_offset(int W) { return W == 32 ? 8 : W / 2; }
 
 __device__ __forceinline__ int tile_width(int t, int n_tiles, int w_last) { return t == n_tiles - 1 ? w_last : 32; }
 
@@ -106,47 +121,339 @@ __device__ __forceinline__ void store_pos(const Smem<R> &s, int b, V3<R> p, R si
     s.posd[t * 64 + i + W] = v;
 }
 
-// One ring unit: i-tile I against j-tile J for ring steps [tb, te).
-template <typename R>
-__device__ __forceinline__ void pair_unit(const Smem<R> &s, Vec4<R> *fw_mine, int I, int J, int tb, int te, int flags,
-                                          int n_tiles, int w_last, int lane)
+// The packed copy: ring position i of tile t is the first element of
+// entries i and i + W and the second element of entries (i - D) mod W and
+// that + W.
+__device__ __forceinline__ void store_posp(const Smem<float> &s, int b, V3<float> p, int n_tiles, int w_last)
 {
-    const int wI = tile_width(I, n_tiles, w_last);
-    const int W = tile_width(J, n_tiles, w_last);
+    const int t = b >> 5, i = b & 31, W = tile_width(t, n_tiles, w_last), D = pair_offset(W);
+    float *base = reinterpret_cast<float *>(s.posp + 2 * 64 * t);
+    const int q = (i - D) & (W - 1);
+#pragma unroll
+    for (int rep = 0; rep < 2; ++rep) {
+        float *e1 = base + 8 * (i + rep * W);  // first element of entry i (+W)
+        e1[0] = p.x; e1[2] = p.y; e1[4] = p.z;
+        float *e2 = base + 8 * (q + rep * W);  // second element of entry q (+W)
+        e2[1] = p.x; e2[3] = p.y; e2[5] = p.z;
+    }
+}
+
+// Ring pieces.  A piece runs ring steps t = TB .. TB+NST-1 of a j-tile of
+// width W against one i-tile (or two, DUAL, sharing the j loads and the
+// j-force shuffles).  Lane l holds i = I*32 + l and pairs with
+// j = J*32 + ((l mod W) + t) mod W; the j-force accumulator moves to lane
+// l-1 (mod W) after every step.  Masks exist only where they can bite: the
+// exclusions |i - j| <= 2 at t < 3 of neighbouring tiles, and the half step
+// t = W/2 of a diagonal tile (which would count each pair twice).
+struct PieceKind {
+    int W, TB, NST, DIAG;
+};
+__host__ __device__ constexpr PieceKind piece_kind(int k)
+{
+    return k == 0 ? PieceKind{32, 0, 8, 0} : k == 1 ? PieceKind{32, 8, 8, 0} : k == 2 ? PieceKind{32, 16, 8, 0}
+         : k == 3 ? PieceKind{32, 24, 8, 0} : k == 4 ? PieceKind{32, 1, 8, 1} : k == 5 ? PieceKind{32, 9, 8, 1}
+         : k == 6 ? PieceKind{16, 0, 8, 0} : k == 7 ? PieceKind{16, 8, 8, 0} : k == 8 ? PieceKind{16, 1, 8, 1}
+         : k == 9 ? PieceKind{8, 0, 8, 0} : PieceKind{8, 1, 4, 1};
+}
+
+template <typename R>
+__device__ __forceinline__ R pair_fr(const Vec4<R> &pi, const Vec2<R> &qi, const Vec4<R> &pj, const Vec2<R> &qj, R &dx,
+                                     R &dy, R &dz)
+{
+    dx = pj.x - pi.x;
+    dy = pj.y - pi.y;
+    dz = pj.z - pi.z;
+    const R r2 = dx * dx + dy * dy + dz * dz;
+    const R ri = rsqrt_r(r2);
+    const R ri2 = ri * ri;
+    const R sg = pi.w + pj.w;
+    const R x2 = sg * sg * ri2;
+    const R x6 = x2 * x2 * x2;
+    const R lj = (qi.x * qj.x) * x6 * (R(2) * x6 - R(1));  // 24 eps_ij (2 x^12 - x^6)
+    return ((qi.y * qj.y) * ri + lj) * ri2;                 // -dU/dr / r
+}
+
+template <typename R, int KIND, bool DUAL>
+__device__ __forceinline__ void ring_piece(const Smem<R> &s, Vec4<R> *fw, int I1, int I2, int J, bool near1,
+                                           bool near2, int wI, int lane)
+{
+    constexpr PieceKind K = piece_kind(KIND);
+    constexpr int W = K.W, TB = K.TB, NST = K.NST;
+    constexpr bool DIAG = K.DIAG;
     const int lr = lane & (W - 1);
     const bool ion = lane < wI;
-    const bool diag = flags & 1, near = flags & 2;
-    Vec4<R> pi{R(-1e4), R(-1e4), R(-1e4), R(0)};
-    Vec2<R> qi{R(0), R(0)};
+    Vec4<R> pi1{R(-1e4), R(-1e4), R(-1e4), R(0)}, pi2{R(-2e4), R(-1e4), R(-1e4), R(0)};
+    Vec2<R> qi1{R(0), R(0)}, qi2{R(0), R(0)};
+    if (ion) {
+        pi1 = s.posd[I1 * 64 + lane];
+        qi1 = s.eqd[I1 * 64 + lane];
+    }
+    if (DUAL) {
+        pi2 = s.posd[I2 * 64 + lane];
+        qi2 = s.eqd[I2 * 64 + lane];
+    }
+    R f1x = 0, f1y = 0, f1z = 0, f2x = 0, f2y = 0, f2z = 0, fjx = 0, fjy = 0, fjz = 0;
+    const Vec4<R> *pj = s.posd + J * 64 + lr;
+    const Vec2<R> *qj = s.eqd + J * 64 + lr;
+    const int src = (lane & ~(W - 1)) | ((lr + 1) & (W - 1));
+#pragma unroll
+    for (int k = 0; k < NST; ++k) {
+        const int t = TB + k;
+        const Vec4<R> pjv = pj[t];
+        const Vec2<R> qjv = qj[t];
+        R dx, dy, dz;
+        R fr = pair_fr(pi1, qi1, pjv, qjv, dx, dy, dz);
+        if (t < 3 && near1) {
+            const int d = I1 * 32 + lane - (J * 32 + ((lr + t) & (W - 1)));
+            if (d <= 2 && d >= -2) fr = R(0);
+        }
+        if (DIAG && 2 * t == W && lr >= (W >> 1)) fr = R(0);
+        f1x -= fr * dx; f1y -= fr * dy; f1z -= fr * dz;
+        fjx += fr * dx; fjy += fr * dy; fjz += fr * dz;
+        if (DUAL) {
+            R ex, ey, ez;
+            R gr = pair_fr(pi2, qi2, pjv, qjv, ex, ey, ez);
+            if (t < 3 && near2) {
+                const int d = I2 * 32 + lane - (J * 32 + ((lr + t) & (W - 1)));
+                if (d <= 2 && d >= -2) gr = R(0);
+            }
+            f2x -= gr * ex; f2y -= gr * ey; f2z -= gr * ez;
+            fjx += gr * ex; fjy += gr * ey; fjz += gr * ez;
+        }
+        if (k + 1 < NST) {
+            fjx = __shfl_sync(0xffffffffu, fjx, src);
+            fjy = __shfl_sync(0xffffffffu, fjy, src);
+            fjz = __shfl_sync(0xffffffffu, fjz, src);
+        }
+    }
+    if (ion) {
+        Vec4<R> f = fw[I1 * 32 + lane];
+        f.x += f1x; f.y += f1y; f.z += f1z;
+        fw[I1 * 32 + lane] = f;
+    }
+    if (DUAL) {
+        Vec4<R> f = fw[I2 * 32 + lane];
+        f.x += f2x; f.y += f2y; f.z += f2z;
+        fw[I2 * 32 + lane] = f;
+    }
+#pragma unroll
+    for (int o = W; o < 32; o <<= 1) {
+        fjx += __shfl_xor_sync(0xffffffffu, fjx, o);
+        fjy += __shfl_xor_sync(0xffffffffu, fjy, o);
+        fjz += __shfl_xor_sync(0xffffffffu, fjz, o);
+    }
+    if (lane < W) {
+        const int bj = J * 32 + ((lr + TB + NST - 1) & (W - 1));
+        Vec4<R> f = fw[bj];
+        f.x += fjx; f.y += fjy; f.z += fjz;
+        fw[bj] = f;
+    }
+}
+
+// Packed FP32 double steps: lane l evaluates ring steps t and t + D at once
+// with f32x2 arithmetic (one i-bead, two j-beads); the j-force streams of
+// the two steps are the two halves of a packed accumulator and both move one
+// lane per double step.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+template <int W>
+__device__ __forceinline__ void packed_piece(const Smem<float> &s, Vec4<float> *fw, int I, int J, int TB, int NDS,
+                                             bool diag, bool near, int wI, int lane)
+{
+    constexpr int D = pair_offset(W);
+    const int lr = lane & (W - 1);
+    const bool ion = lane < wI;
+    Vec4<float> pi{-1e4f, -1e4f, -1e4f, 0.f};
+    Vec2<float> qi{0.f, 0.f};
     if (ion) {
         pi = s.posd[I * 64 + lane];
         qi = s.eqd[I * 64 + lane];
     }
-    R fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
-    const Vec4<R> *pj_base = s.posd + J * 64 + lr;
-    const Vec2<R> *qj_base = s.eqd + J * 64 + lr;
+    const float2 nx = f2(-pi.x, -pi.x), ny = f2(-pi.y, -pi.y), nz = f2(-pi.z, -pi.z);
+    const float2 si = f2(pi.w, pi.w), ei = f2(qi.x, qi.x), ci = f2(qi.y, qi.y);
+    const float2 two = f2(2.f, 2.f), mone = f2(-1.f, -1.f);
+    float2 fix = f2(0.f, 0.f), fiy = fix, fiz = fix, fjx = fix, fjy = fix, fjz = fix;
+    const float4 *A = s.posp + 2 * (64 * J + lr);
+    const float4 *E = s.eqp + 64 * J + lr;
     const int src = (lane & ~(W - 1)) | ((lr + 1) & (W - 1));
-    const int gi = I * 32 + lane;
-    for (int t = tb; t < te; ++t) {
-        const Vec4<R> pj = pj_base[t];
-        const Vec2<R> qj = qj_base[t];
-        const R dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-        const R r2 = dx * dx + dy * dy + dz * dz;
-        const R ri = rsqrt_r(r2);
-        const R ri2 = ri * ri;
-        const R sg = pi.w + pj.w;
-        const R x2 = sg * sg * ri2;
-        const R x6 = x2 * x2 * x2;
-        const R ee = qi.x * qj.x;
-        const R qq = qi.y * qj.y;
-        const R lj = ee * x6 * (R(2) * x6 - R(1));
-        R fr = (qq * ri + lj) * ri2;  // -dU/dr / r; force on j = fr * (rj - ri)
-        if (t < 3 && near) {
-            const int gj = J * 32 + ((lr + t) & (W - 1));
-            const int d = gi - gj;
-            if (d <= 2 && d >= -2) fr = R(0);
+    const bool mask_a = near && TB < 3;                      // exclusions at t < 3
+    const bool mask_b = diag && lr >= (W >> 1);             // last step of a diagonal: half the lanes
+#pragma unroll 2
+    for (int k = 0; k < NDS; ++k) {
+        const int t = TB + k;
+        const float4 a = A[2 * t], b = A[2 * t + 1], e = E[t];
+        const float2 dx = __fadd2_rn(f2(a.x, a.y), nx);
+        const float2 dy = __fadd2_rn(f2(a.z, a.w), ny);
+        const float2 dz = __fadd2_rn(f2(b.x, b.y), nz);
+        float2 r2 = __fmul2_rn(dx, dx);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
+        const float2 ri = f2(rsqrtf(r2.x), rsqrtf(r2.y));
+        const float2 ri2 = __fmul2_rn(ri, ri);
+        const float2 sg = __fadd2_rn(si, f2(b.z, b.w));
+        const float2 x2 = __fmul2_rn(__fmul2_rn(sg, sg), ri2);
+        const float2 x6 = __fmul2_rn(__fmul2_rn(x2, x2), x2);
+        const float2 ee = __fmul2_rn(ei, f2(e.x, e.y));
+        const float2 qq = __fmul2_rn(ci, f2(e.z, e.w));
+        const float2 lj = __fmul2_rn(__fmul2_rn(ee, x6), __ffma2_rn(x6, two, mone));
+        float2 fr = __fmul2_rn(__ffma2_rn(qq, ri, lj), ri2);  // -dU/dr / r for both pairs
+        if (mask_a && t < 3) {
+            const int d = I * 32 + lane - (J * 32 + ((lr + t) & (W - 1)));
+            if (d <= 2 && d >= -2) fr.x = 0.f;
         }
-        if (diag && 2 * t == W && lr >= (W >> 1)) fr = R(0);
+        if (mask_b && k == NDS - 1) fr.y = 0.f;  // ring step t + D = W/2
+        fix = __ffma2_rn(fr, dx, fix);
+        fiy = __ffma2_rn(fr, dy, fiy);
+        fiz = __ffma2_rn(fr, dz, fiz);
+        fjx = __ffma2_rn(fr, dx, fjx);
+        fjy = __ffma2_rn(fr, dy, fjy);
+        fjz = __ffma2_rn(fr, dz, fjz);
+        if (k + 1 < NDS) {
+            fjx.x = __shfl_sync(0xffffffffu, fjx.x, src);
+            fjx.y = __shfl_sync(0xffffffffu, fjx.y, src);
+            fjy.x = __shfl_sync(0xffffffffu, fjy.x, src);
+            fjy.y = __shfl_sync(0xffffffffu, fjy.y, src);
+            fjz.x = __shfl_sync(0xffffffffu, fjz.x, src);
+            fjz.y = __shfl_sync(0xffffffffu, fjz.y, src);
+        }
+    }
+    if (ion) {
+        Vec4<float> f = fw[I * 32 + lane];
+        f.x -= fix.x + fix.y; f.y -= fiy.x + fiy.y; f.z -= fiz.x + fiz.y;
+        fw[I * 32 + lane] = f;
+    }
+#pragma unroll
+    for (int o = W; o < 32; o <<= 1) {
+        fjx.x += __shfl_xor_sync(0xffffffffu, fjx.x, o); fjx.y += __shfl_xor_sync(0xffffffffu, fjx.y, o);
+        fjy.x += __shfl_xor_sync(0xffffffffu, fjy.x, o); fjy.y += __shfl_xor_sync(0xffffffffu, fjy.y, o);
+        fjz.x += __shfl_xor_sync(0xffffffffu, fjz.x, o); fjz.y += __shfl_xor_sync(0xffffffffu, fjz.y, o);
+    }
+    if (lane < W) {
+        const int ba = J * 32 + ((lr + TB + NDS - 1) & (W - 1));
+        Vec4<float> f = fw[ba];
+        f.x += fjx.x; f.y += fjy.x; f.z += fjz.x;
+        fw[ba] = f;
+        const int bb = J * 32 + ((lr + TB + NDS - 1 + D) & (W - 1));
+        f = fw[bb];
+        f.x += fjx.y; f.y += fjy.y; f.z += fjz.y;
+        fw[bb] = f;
+    }
+}
+
+// Two width-32 packed pieces interleaved in one loop: their dependency
+// chains (shared loads, rsqrt, j-force shuffles) are independent, so the
+// pair hides each other's latency.  Each piece: i-tile I, j-tile J, first
+// step TB, 8 double steps, diagonal / exclusion flags.
+struct PieceRef {
+    int I, J, TB;
+    bool diag, near;
+};
+
+__device__ __forceinline__ void packed_pair32(const Smem<float> &s, Vec4<float> *fw, const PieceRef p0,
+                                              const PieceRef p1, int lane)
+{
+    constexpr int W = 32, D = 8, NDS = 8;
+    const PieceRef P[2] = {p0, p1};
+    float2 nx[2], ny[2], nz[2], si[2], ei[2], ci[2];
+    float2 fix[2], fiy[2], fiz[2], fjx[2], fjy[2], fjz[2];
+    const float4 *A[2], *E[2];
+    bool mask_a[2], mask_b[2];
+    const int lr = lane;
+    const int src = (lane + 1) & 31;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const Vec4<float> pi = s.posd[P[u].I * 64 + lane];
+        const Vec2<float> qi = s.eqd[P[u].I * 64 + lane];
+        nx[u] = f2(-pi.x, -pi.x); ny[u] = f2(-pi.y, -pi.y); nz[u] = f2(-pi.z, -pi.z);
+        si[u] = f2(pi.w, pi.w); ei[u] = f2(qi.x, qi.x); ci[u] = f2(qi.y, qi.y);
+        fix[u] = f2(0.f, 0.f); fiy[u] = fix[u]; fiz[u] = fix[u]; fjx[u] = fix[u]; fjy[u] = fix[u]; fjz[u] = fix[u];
+        A[u] = s.posp + 2 * (64 * P[u].J + lr + P[u].TB);
+        E[u] = s.eqp + 64 * P[u].J + lr + P[u].TB;
+        mask_a[u] = P[u].near && P[u].TB < 3;
+        mask_b[u] = P[u].diag && lr >= (W >> 1);
+    }
+    const float2 two = f2(2.f, 2.f), mone = f2(-1.f, -1.f);
+#pragma unroll 2
+    for (int k = 0; k < NDS; ++k) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int t = P[u].TB + k;
+            const float4 a = A[u][2 * k], b = A[u][2 * k + 1], e = E[u][k];
+            const float2 dx = __fadd2_rn(f2(a.x, a.y), nx[u]);
+            const float2 dy = __fadd2_rn(f2(a.z, a.w), ny[u]);
+            const float2 dz = __fadd2_rn(f2(b.x, b.y), nz[u]);
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            const float2 ri = f2(rsqrtf(r2.x), rsqrtf(r2.y));
+            const float2 ri2 = __fmul2_rn(ri, ri);
+            const float2 sg = __fadd2_rn(si[u], f2(b.z, b.w));
+            const float2 x2 = __fmul2_rn(__fmul2_rn(sg, sg), ri2);
+            const float2 x6 = __fmul2_rn(__fmul2_rn(x2, x2), x2);
+            const float2 ee = __fmul2_rn(ei[u], f2(e.x, e.y));
+            const float2 qq = __fmul2_rn(ci[u], f2(e.z, e.w));
+            const float2 lj = __fmul2_rn(__fmul2_rn(ee, x6), __ffma2_rn(x6, two, mone));
+            float2 fr = __fmul2_rn(__ffma2_rn(qq, ri, lj), ri2);
+            if (mask_a[u] && t < 3) {
+                const int d = P[u].I * 32 + lane - (P[u].J * 32 + ((lr + t) & (W - 1)));
+                if (d <= 2 && d >= -2) fr.x = 0.f;
+            }
+            if (mask_b[u] && k == NDS - 1) fr.y = 0.f;
+            fix[u] = __ffma2_rn(fr, dx, fix[u]);
+            fiy[u] = __ffma2_rn(fr, dy, fiy[u]);
+            fiz[u] = __ffma2_rn(fr, dz, fiz[u]);
+            fjx[u] = __ffma2_rn(fr, dx, fjx[u]);
+            fjy[u] = __ffma2_rn(fr, dy, fjy[u]);
+            fjz[u] = __ffma2_rn(fr, dz, fjz[u]);
+            if (k + 1 < NDS) {
+                fjx[u].x = __shfl_sync(0xffffffffu, fjx[u].x, src);
+                fjx[u].y = __shfl_sync(0xffffffffu, fjx[u].y, src);
+                fjy[u].x = __shfl_sync(0xffffffffu, fjy[u].x, src);
+                fjy[u].y = __shfl_sync(0xffffffffu, fjy[u].y, src);
+                fjz[u].x = __shfl_sync(0xffffffffu, fjz[u].x, src);
+                fjz[u].y = __shfl_sync(0xffffffffu, fjz[u].y, src);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        Vec4<float> f = fw[P[u].I * 32 + lane];
+        f.x -= fix[u].x + fix[u].y; f.y -= fiy[u].x + fiy[u].y; f.z -= fiz[u].x + fiz[u].y;
+        fw[P[u].I * 32 + lane] = f;
+        const int ba = P[u].J * 32 + ((lr + P[u].TB + NDS - 1) & (W - 1));
+        f = fw[ba];
+        f.x += fjx[u].x; f.y += fjy[u].x; f.z += fjz[u].x;
+        fw[ba] = f;
+        const int bb = P[u].J * 32 + ((lr + P[u].TB + NDS - 1 + D) & (W - 1));
+        f = fw[bb];
+        f.x += fjx[u].y; f.y += fjy[u].y; f.z += fjz[u].y;
+        fw[bb] = f;
+    }
+}
+
+// Diagonal of a ragged last tile (width 8 or 16), scalar, ring steps 1..W/2;
+// rare (at most one per chain), so kept compact rather than unrolled.
+__device__ __noinline__ void ragged_diag_piece(const Smem<float> &s, Vec4<float> *fw, int J, int W, int lane)
+{
+    const int lr = lane & (W - 1);
+    const bool ion = lane < W;
+    Vec4<float> pi{-1e4f, -1e4f, -1e4f, 0.f};
+    Vec2<float> qi{0.f, 0.f};
+    if (ion) {
+        pi = s.posd[J * 64 + lane];
+        qi = s.eqd[J * 64 + lane];
+    }
+    float fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
+    const int src = (lane & ~(W - 1)) | ((lr + 1) & (W - 1));
+    const int te = W / 2 + 1;
+    for (int t = 1; t < te; ++t) {
+        const Vec4<float> pj = s.posd[J * 64 + lr + t];
+        const Vec2<float> qj = s.eqd[J * 64 + lr + t];
+        float dx, dy, dz;
+        float fr = pair_fr(pi, qi, pj, qj, dx, dy, dz);
+        // |i - j| = t without wrap (excluded for t <= 2), W - t >= W/2 >= 4 with wrap;
+        // at t = W/2 the upper half of the ring repeats the lower half's pairs
+        if ((t < 3 && lr + t < W) || (2 * t == W && lr >= (W >> 1))) fr = 0.f;
         fix -= fr * dx; fiy -= fr * dy; fiz -= fr * dz;
         fjx += fr * dx; fjy += fr * dy; fjz += fr * dz;
         if (t + 1 < te) {
@@ -156,9 +463,9 @@ __device__ __forceinline__ void pair_unit(const Smem<R> &s, Vec4<R> *fw_mine, in
         }
     }
     if (ion) {
-        Vec4<R> f = fw_mine[I * 32 + lane];
+        Vec4<float> f = fw[J * 32 + lane];
         f.x += fix; f.y += fiy; f.z += fiz;
-        fw_mine[I * 32 + lane] = f;
+        fw[J * 32 + lane] = f;
     }
     for (int o = W; o < 32; o <<= 1) {
         fjx += __shfl_xor_sync(0xffffffffu, fjx, o);
@@ -167,9 +474,51 @@ __device__ __forceinline__ void pair_unit(const Smem<R> &s, Vec4<R> *fw_mine, in
     }
     if (lane < W) {
         const int bj = J * 32 + ((lr + te - 1) & (W - 1));
-        Vec4<R> f = fw_mine[bj];
+        Vec4<float> f = fw[bj];
         f.x += fjx; f.y += fjy; f.z += fjz;
-        fw_mine[bj] = f;
+        fw[bj] = f;
+    }
+}
+
+// Piece kinds of the packed FP32 path:
+//   11: W 32, t 0..7 + 8..15   12: W 32, t 16..23 + 24..31   13: W 32 diagonal, t 1..8 + 9..16
+//   14: W 16, t 0..7 + 8..15   15: W 8,  t 0..3 + 4..7
+//   8, 10: diagonal of a ragged tile of width 16 / 8, scalar
+__device__ __forceinline__ void run_packed_piece(const Smem<float> &s, Vec4<float> *fw, int kind, int I, int J,
+                                                 bool near, int wI, int lane)
+{
+    switch (kind) {
+    case 11: packed_piece<32>(s, fw, I, J, 0, 8, false, near, wI, lane); break;
+    case 12: packed_piece<32>(s, fw, I, J, 16, 8, false, near, wI, lane); break;
+    case 13: packed_piece<32>(s, fw, I, J, 1, 8, true, near, wI, lane); break;
+    case 14: packed_piece<16>(s, fw, I, J, 0, 8, false, near, wI, lane); break;
+    case 15: packed_piece<8>(s, fw, I, J, 0, 4, false, near, wI, lane); break;
+    case 8: ragged_diag_piece(s, fw, J, 16, lane); break;
+    case 10: ragged_diag_piece(s, fw, J, 8, lane); break;
+    default: break;  // the host schedule emits only the kinds above
+    }
+}
+
+template <typename R, bool DUAL>
+__device__ __forceinline__ void run_piece(const Smem<R> &s, Vec4<R> *fw, int kind, int I1, int I2, int J, bool n1,
+                                          bool n2, int wI, int lane)
+{
+    switch (kind) {
+    case 0: ring_piece<R, 0, DUAL>(s, fw, I1, I2, J, n1, n2, wI, lane); break;
+    case 1: ring_piece<R, 1, DUAL>(s, fw, I1, I2, J, n1, n2, wI, lane); break;
+    case 2: ring_piece<R, 2, DUAL>(s, fw, I1, I2, J, n1, n2, wI, lane); break;
+    case 3: ring_piece<R, 3, DUAL>(s, fw, I1, I2, J, n1, n2, wI, lane); break;
+    case 6: ring_piece<R, 6, DUAL>(s, fw, I1, I2, J, n1, n2, wI, lane); break;
+    case 7: ring_piece<R, 7, DUAL>(s, fw, I1, I2, J, n1, n2, wI, lane); break;
+    case 9: ring_piece<R, 9, DUAL>(s, fw, I1, I2, J, n1, n2, wI, lane); break;
+    default:
+        if (!DUAL) {
+            if (kind == 4) ring_piece<R, 4, false>(s, fw, I1, I2, J, n1, n2, wI, lane);
+            else if (kind == 5) ring_piece<R, 5, false>(s, fw, I1, I2, J, n1, n2, wI, lane);
+            else if (kind == 8) ring_piece<R, 8, false>(s, fw, I1, I2, J, n1, n2, wI, lane);
+            else if (kind == 10) ring_piece<R, 10, false>(s, fw, I1, I2, J, n1, n2, wI, lane);
+        }
+        break;
     }
 }
 
@@ -194,14 +543,15 @@ __device__ __forceinline__ R bonded_owner(const ChainArgs<R> &a, const Smem<R> &
             const V3<R> u = sub(pa, pb), w = sub(pc, pb);
             const R lu2 = dot(u, u), lw2 = dot(w, w);
             const R inv = rsqrt_r(lu2 * lw2);
+            const R inv2 = inv * inv;
             R cs = dot(u, w) * inv;
             cs = cs > R(1) ? R(1) : (cs < R(-1) ? R(-1) : cs);
             const R th = acos(cs);
             R sn2 = R(1) - cs * cs;
             sn2 = sn2 > R(1e-12) ? sn2 : R(1e-12);
             const R pref = a.kth * (th - a.th0) * rsqrt_r(sn2);
-            const V3<R> ga = sub(scl(w, inv), scl(u, cs / lu2));
-            const V3<R> gc = sub(scl(u, inv), scl(w, cs / lw2));
+            const V3<R> ga = sub(scl(w, inv), scl(u, cs * inv2 * lw2));  // cs / |u|^2
+            const V3<R> gc = sub(scl(u, inv), scl(w, cs * inv2 * lu2));  // cs / |w|^2
             f0 = add(f0, scl(ga, pref));
             f2 = add(f2, scl(gc, pref));
             f1 = sub(f1, scl(add(ga, gc), pref));
@@ -214,11 +564,12 @@ __device__ __forceinline__ R bonded_owner(const ChainArgs<R> &a, const Smem<R> &
                 const V3<R> n1 = cross(b1, b2), n2 = cross(b2, b3);
                 const R nn1 = dot(n1, n1), nn2 = dot(n2, n2);
                 const R inv = rsqrt_r(nn1 * nn2);
+                const R inv2 = inv * inv;
                 const R c = dot(n1, n2) * inv;
                 // U = sum_n K_n (1 + cos d_n T_n(cos phi)); T_2 = 2c^2 - 1, T_3 = 4c^3 - 3c
                 const R dudc = K.x + R(4) * K.y * c + K.z * (R(12) * c * c - R(3));
-                const V3<R> g1 = sub(scl(n2, inv), scl(n1, c / nn1));
-                const V3<R> g2 = sub(scl(n1, inv), scl(n2, c / nn2));
+                const V3<R> g1 = sub(scl(n2, inv), scl(n1, c * inv2 * nn2));  // c / |n1|^2
+                const V3<R> g2 = sub(scl(n1, inv), scl(n2, c * inv2 * nn1));  // c / |n2|^2
                 const V3<R> db1 = cross(b2, g1);
                 const V3<R> db2 = add(cross(g1, b1), cross(b3, g2));
                 const V3<R> db3 = cross(g2, b2);
@@ -232,8 +583,9 @@ __device__ __forceinline__ R bonded_owner(const ChainArgs<R> &a, const Smem<R> &
     if (t == 0 || t == N - 1) {
         const V3<R> d = sub(pos_of(s, N - 1), pos_of(s, 0));
         const R x2 = dot(d, d);
-        const R x = sqrt(x2);
-        const R g = a.k * (x - lam) / x;
+        const R rx = rsqrt_r(x2);
+        const R x = x2 * rx;
+        const R g = a.k * (x - lam) * rx;
         if (t == 0) f0 = add(f0, scl(d, g));
         else { f0 = scl(d, -g); xrc = x; }
     }
@@ -244,11 +596,25 @@ __device__ __forceinline__ R bonded_owner(const ChainArgs<R> &a, const Smem<R> &
     return xrc;
 }
 
+// Normals of O-step `step`: block b of Philox counter (b, uid, step, 0)
+// gives dofs 4b..4b+3 (dof d = 3 bead + axis).  Generated by the threads at
+// the top of the CTA, which own few bonded terms.
+template <typename R, int NW>
+__device__ __forceinline__ void gen_noise(const ChainArgs<R> &a, const Smem<R> &s, uint32_t uid, uint32_t step)
+{
+    const int nblk = (3 * a.N + 3) >> 2;
+    for (int b = NW * 32 - 1 - (int)threadIdx.x; b < nblk; b += NW * 32) {
+        const Normal4<R> n = philox_normals<R>(a.seed, (uint32_t)b, uid, step, kTagOStep);
+        reinterpret_cast<Vec4<R> *>(s.noise)[b] = Vec4<R>{n.n0, n.n1, n.n2, n.n3};
+    }
+}
+
 template <typename R, int NW>
 __device__ __forceinline__ void force_phase(const ChainArgs<R> &a, const Smem<R> &s, R lam, long long done,
-                                            long long nequil, long long sample_base, bool sample)
+                                            long long nequil, long long sample_base, bool sample, uint32_t uid)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    gen_noise<R, NW>(a, s, uid, (uint32_t)done);
     for (int t = tid; t < a.N; t += NW * 32) {
         const R x = bonded_owner(a, s, t, lam);
         if (t == a.N - 1) {
@@ -262,14 +628,30 @@ __device__ __forceinline__ void force_phase(const ChainArgs<R> &a, const Smem<R>
         const int cnt = a.unit_count[warp];
         const int4 *u = a.units + warp * a.max_units;
         for (int q = 0; q < cnt; ++q) {
-            const int4 e = u[q];
-            pair_unit<R>(s, fw_mine, e.x, e.y, e.z & 0xff, (e.z >> 8) & 0xff, e.z >> 16, a.n_tiles, a.w_last, lane);
+            const int4 e = u[q];  // (I1, I2 or -1, J, kind | near1 << 8 | near2 << 9)
+            const int kind = e.w & 0xff;
+            const bool n1 = (e.w >> 8) & 1, n2 = (e.w >> 9) & 1;
+            const int wI = tile_width(e.x, a.n_tiles, a.w_last);
+            if constexpr (kPacked<R>) {
+                if ((e.w >> 10) & 1) {  // two width-32 pieces run interleaved
+                    const int4 g = u[++q];
+                    const int k2 = g.w & 0xff;
+                    const PieceRef p0{e.x, e.z, kind == 12 ? 16 : (kind == 13 ? 1 : 0), kind == 13, n1};
+                    const PieceRef p1{g.x, g.z, k2 == 12 ? 16 : (k2 == 13 ? 1 : 0), k2 == 13, (bool)((g.w >> 8) & 1)};
+                    packed_pair32(s, fw_mine, p0, p1, lane);
+                } else {
+                    run_packed_piece(s, fw_mine, kind, e.x, e.z, n1, wI, lane);
+                }
+            } else {
+                if (e.y >= 0) run_piece<R, true>(s, fw_mine, kind, e.x, e.y, e.z, n1, n2, wI, lane);
+                else run_piece<R, false>(s, fw_mine, kind, e.x, 0, e.z, n1, false, wI, lane);
+            }
         }
     }
 }
 
 template <typename R, int NW>
-__global__ void __launch_bounds__(NW * 32) chain_kernel(const ChainArgs<R> a)
+__global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? 5 : 1) chain_kernel(const ChainArgs<R> a)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int rep = blockIdx.x;
@@ -289,6 +671,13 @@ __global__ void __launch_bounds__(NW * 32) chain_kernel(const ChainArgs<R> a)
         s.vel = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np;
         s.fw = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * NW;
         s.bslot = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * 4;
+        s.noise = reinterpret_cast<R *>(p); p += sizeof(Vec4<R>) * ((3 * a.N + 3) >> 2);
+        s.posp = nullptr;
+        s.eqp = nullptr;
+        if constexpr (kPacked<R>) {
+            s.posp = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 2 * 64 * a.n_tiles;
+            s.eqp = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 64 * a.n_tiles;
+        }
         s.flag = reinterpret_cast<int *>(p);
     }
     const int tid = threadIdx.x;
@@ -303,10 +692,23 @@ __global__ void __launch_bounds__(NW * 32) chain_kernel(const ChainArgs<R> a)
         Vec4<R> p, v{0, 0, 0, 0};
         if (s0 == 0) {
             p = a.bead_pos0[b];
+            if (a.start != nullptr && b < a.N) {
+                const double *q = a.start + ((size_t)rep * a.N + b) * 3;
+                p.x = (R)q[0];
+                p.y = (R)q[1];
+                p.z = (R)q[2];
+            }
             if (b < a.N) {
-                const Normal4<R> n = philox_normals<R>(a.seed, (uint32_t)b, uid, 0u, kTagInitVel);
+                // dofs 3b..3b+2 from blocks (3b)/4 and (3b+2)/4 of counter (block, uid, 0, 1)
+                const Normal4<R> n0 = philox_normals<R>(a.seed, (uint32_t)(3 * b) >> 2, uid, 0u, kTagInitVel);
+                const Normal4<R> n1 = philox_normals<R>(a.seed, (uint32_t)(3 * b + 2) >> 2, uid, 0u, kTagInitVel);
+                const R q[8] = {n0.n0, n0.n1, n0.n2, n0.n3, n1.n0, n1.n1, n1.n2, n1.n3};
+                const int o = (3 * b) & 3;  // dof 3b + c is q[o + c] (q[4..7] = second block)
+                R xi[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) xi[c] = q[o + c];
                 const R sv = sqrt(a.kT * a.bead_invm[b]);
-                v = Vec4<R>{sv * n.n0, sv * n.n1, sv * n.n2, R(0)};
+                v = Vec4<R>{sv * xi[0], sv * xi[1], sv * xi[2], R(0)};
             }
         } else {
             p = st[b];
@@ -323,9 +725,21 @@ __global__ void __launch_bounds__(NW * 32) chain_kernel(const ChainArgs<R> a)
         if (i < 2 * W) s.eqd[e] = a.bead_eq[t * 32 + (i & (W - 1))];
     }
     __syncthreads();
+    if constexpr (kPacked<R>) {
+        for (int e = tid; e < a.n_tiles * 64; e += NW * 32) {
+            const int t = e >> 6, i = e & 63, W = tile_width(t, a.n_tiles, a.w_last), D = pair_offset(W);
+            if (i >= 2 * W) continue;
+            const Vec4<R> p0 = s.posd[t * 64 + (i & (W - 1))], p1 = s.posd[t * 64 + ((i + D) & (W - 1))];
+            const Vec2<R> q0 = s.eqd[t * 64 + (i & (W - 1))], q1 = s.eqd[t * 64 + ((i + D) & (W - 1))];
+            s.posp[2 * e] = make_float4(p0.x, p1.x, p0.y, p1.y);
+            s.posp[2 * e + 1] = make_float4(p0.z, p1.z, p0.w, p1.w);
+            s.eqp[e] = make_float4(q0.x, q1.x, q0.y, q1.y);
+        }
+        __syncthreads();
+    }
     const long long nequil = a.nequil_w[w];
     const long long sample_base = a.off_w[w] + (long long)r * a.tw[w];
-    force_phase<R, NW>(a, s, lam, 0, nequil, sample_base, false);
+    force_phase<R, NW>(a, s, lam, s0, nequil, sample_base, false, uid);
     __syncthreads();
 
     for (long long step = s0;; ++step) {
@@ -347,13 +761,13 @@ __global__ void __launch_bounds__(NW * 32) chain_kernel(const ChainArgs<R> a)
                 V3<R> p = pos_of(s, b);
                 v.x += hdt * F.x * im; v.y += hdt * F.y * im; v.z += hdt * F.z * im;
                 p.x += hdt * v.x; p.y += hdt * v.y; p.z += hdt * v.z;
-                const Normal4<R> n = philox_normals<R>(a.seed, (uint32_t)b, uid, (uint32_t)step, kTagOStep);
                 const R sv = c2 * sqrt(a.kT * im);
-                v.x = c1 * v.x + sv * n.n0;
-                v.y = c1 * v.y + sv * n.n1;
-                v.z = c1 * v.z + sv * n.n2;
+                v.x = c1 * v.x + sv * s.noise[3 * b + 0];
+                v.y = c1 * v.y + sv * s.noise[3 * b + 1];
+                v.z = c1 * v.z + sv * s.noise[3 * b + 2];
                 p.x += hdt * v.x; p.y += hdt * v.y; p.z += hdt * v.z;
                 store_pos<R>(s, b, p, a.bead_pos0[b].w, a.n_tiles, a.w_last);
+                if constexpr (kPacked<R>) store_posp(s, b, p, a.n_tiles, a.w_last);
             } else if (a.force_out != nullptr) {
                 a.force_out[3 * b + 0] = (double)F.x;
                 a.force_out[3 * b + 1] = (double)F.y;
@@ -363,7 +777,7 @@ __global__ void __launch_bounds__(NW * 32) chain_kernel(const ChainArgs<R> a)
         }
         if (step >= s1) break;
         __syncthreads();
-        force_phase<R, NW>(a, s, lam, step + 1, nequil, sample_base, true);
+        force_phase<R, NW>(a, s, lam, step + 1, nequil, sample_base, true, uid);
         __syncthreads();
         if (*s.flag) {
             if (tid == 0) atomicOr(a.err, kErrNonFinite);
@@ -398,42 +812,109 @@ ChainGeometry chain_geometry(int N)
     return g;
 }
 
-// Ring units covering every pair i < j exactly once, split into pieces of at
-// most `piece` ring steps and spread over NW warps (longest first onto the
-// least loaded warp).  Bonded owners occupy warps 0..ceil(N/32)-1 first.
-std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, int piece)
+// Ring pieces covering every pair i < j exactly once: for each j-tile J, the
+// diagonal pieces of J and the off-diagonal pieces of every i-tile I < J; two
+// off-diagonal i-tiles with the same j-tile and piece kind share one DUAL
+// piece.  Pieces are spread over the NW warps longest-first onto the least
+// loaded warp; the bonded owners and the noise generators load warps
+// 0..ceil(N/32)-1 first.
+std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed)
 {
     const ChainGeometry g = chain_geometry(N);
-    std::vector<UnitDesc> all;
-    for (int I = 0; I < g.n_tiles; ++I)
-        for (int J = I; J < g.n_tiles; ++J) {
-            const int W = J == g.n_tiles - 1 ? g.w_last : 32;
-            const int tb = (I == J) ? 1 : 0;
-            const int te = (I == J) ? W / 2 + 1 : W;
-            const int flags = (I == J ? 1 : 0) | (J - I <= 1 ? 2 : 0);
-            for (int a = tb; a < te; a += piece) all.push_back(UnitDesc{I, J, a, std::min(te, a + piece), flags});
+    struct P {
+        UnitDesc u;
+        double cost;
+    };
+    std::vector<P> all;
+    for (int J = 0; packed && J < g.n_tiles; ++J) {
+        // packed FP32 double steps: W 32 tiles in two pieces of 8 double steps
+        const int W = J == g.n_tiles - 1 ? g.w_last : 32;
+        if (W == 32) all.push_back(P{UnitDesc{J, -1, J, 13, 1, 0}, 8 * 40.0 + 40.0});
+        else if (W == 16) all.push_back(P{UnitDesc{J, -1, J, 8, 1, 0}, 8 * 30.0 + 20.0});
+        else all.push_back(P{UnitDesc{J, -1, J, 10, 1, 0}, 4 * 30.0 + 20.0});
+        for (int I = 0; I < J; ++I) {
+            const int nr = J - I == 1 ? 1 : 0;
+            if (W == 32) {
+                all.push_back(P{UnitDesc{I, -1, J, 11, nr, 0}, 8 * 40.0 + 40.0});
+                all.push_back(P{UnitDesc{I, -1, J, 12, nr, 0}, 8 * 40.0 + 40.0});
+            } else if (W == 16) {
+                all.push_back(P{UnitDesc{I, -1, J, 14, nr, 0}, 8 * 40.0 + 50.0});
+            } else {
+                all.push_back(P{UnitDesc{I, -1, J, 15, nr, 0}, 4 * 40.0 + 60.0});
+            }
         }
-    std::stable_sort(all.begin(), all.end(),
-                     [](const UnitDesc &x, const UnitDesc &y) { return (x.te - x.tb) > (y.te - y.tb); });
+    }
+    for (int J = 0; !packed && J < g.n_tiles; ++J) {
+        const int W = J == g.n_tiles - 1 ? g.w_last : 32;
+        std::vector<int> diag_kinds, off_kinds;
+        if (W == 32) { diag_kinds = {4, 5}; off_kinds = {0, 1, 2, 3}; }
+        else if (W == 16) { diag_kinds = {8}; off_kinds = {6, 7}; }
+        else { diag_kinds = {10}; off_kinds = {9}; }
+        for (int k : diag_kinds) {
+            const PieceKind K = piece_kind(k);
+            all.push_back(P{UnitDesc{J, -1, J, k, 1, 0}, K.NST * 30.0 + 20.0});
+        }
+        for (int k : off_kinds) {
+            const PieceKind K = piece_kind(k);
+            for (int I = 0; I < J; I += 2) {
+                if (I + 1 < J) {
+                    all.push_back(P{UnitDesc{I, I + 1, J, k, J - I == 1 ? 1 : 0, J - I - 1 == 1 ? 1 : 0},
+                                    K.NST * 55.0 + 30.0});
+                } else {
+                    all.push_back(P{UnitDesc{I, -1, J, k, J - I == 1 ? 1 : 0, 0}, K.NST * 30.0 + 20.0});
+                }
+            }
+        }
+    }
+    // jobs: packed width-32 pieces go in interleaved pairs (kinds 11..13)
+    std::vector<std::vector<P>> jobs;
+    {
+        std::vector<P> w32, rest;
+        for (const P &p : all) (packed && p.u.kind >= 11 && p.u.kind <= 13 ? w32 : rest).push_back(p);
+        for (size_t i = 0; i + 1 < w32.size(); i += 2) jobs.push_back({w32[i], w32[i + 1]});
+        if (w32.size() % 2) jobs.push_back({w32.back()});
+        for (const P &p : rest) jobs.push_back({p});
+    }
+    // an interleaved pair costs a little less than its two pieces one after the other
+    auto job_cost = [](const std::vector<P> &j) { return j.size() == 2 ? 0.9 * (j[0].cost + j[1].cost) : j[0].cost; };
+    std::stable_sort(jobs.begin(), jobs.end(),
+                     [&](const std::vector<P> &x, const std::vector<P> &y) { return job_cost(x) > job_cost(y); });
     std::vector<std::vector<UnitDesc>> per(NW);
     std::vector<double> load(NW, 0.0);
-    const int owner_warps = std::min(NW, (N + 31) / 32);
-    const int per_thread_terms = (N + NW * 32 - 1) / (NW * 32);
-    for (int w = 0; w < owner_warps; ++w) load[w] += 10.0 * per_thread_terms;
-    for (const UnitDesc &u : all) {
+    const int nt = NW * 32;
+    for (int w = 0; w < NW; ++w) {
+        // bonded owners are threads 0..N-1, noise blocks run on threads nt-1 downwards
+        const int nblk = (3 * N + 3) / 4;
+        for (int pass = 0; pass * nt < N; ++pass)
+            if (w * 32 < N - pass * nt) load[w] += 400.0;
+        for (int pass = 0; pass * nt < nblk; ++pass) {
+            const int lo = nt - (nblk - pass * nt);  // lowest thread with a block in this pass
+            if ((w + 1) * 32 > lo) load[w] += 250.0;
+        }
+    }
+    for (const auto &j : jobs) {
         int best = 0;
         for (int w = 1; w < NW; ++w)
             if (load[w] < load[best]) best = w;
-        per[best].push_back(u);
-        load[best] += (u.te - u.tb) + 0.4;
+        if (j.size() == 2) {
+            UnitDesc a = j[0].u;
+            a.pair_next = 1;
+            per[best].push_back(a);
+            per[best].push_back(j[1].u);
+        } else {
+            per[best].push_back(j[0].u);
+        }
+        load[best] += job_cost(j);
     }
     return per;
 }
 
 template <typename R> size_t chain_smem_bytes(const ChainGeometry &g, int NW)
 {
-    return sizeof(Vec4<R>) * g.n_tiles * 64 + sizeof(Vec2<R>) * g.n_tiles * 64 + sizeof(Vec4<R>) * g.Np * (1 + NW + 4) +
-           16;
+    size_t b = sizeof(Vec4<R>) * g.n_tiles * 64 + sizeof(Vec2<R>) * g.n_tiles * 64 + sizeof(Vec4<R>) * g.Np * (1 + NW + 4) +
+               sizeof(Vec4<R>) * ((3 * g.N + 3) / 4) + 16;
+    if (kPacked<R>) b += sizeof(float4) * 3 * 64 * g.n_tiles;
+    return b;
 }
 
 // Device copy of one chain in precision R.
@@ -519,7 +1000,7 @@ cudaError_t ChainModel::init(const ChainHost &h, int precision)
     p->NW = 4;
     cudaError_t e = precision == 1 ? upload_chain<double>(h, p->geo, p->dd) : upload_chain<float>(h, p->geo, p->df);
     if (e != cudaSuccess) return e;
-    const auto sched = chain_schedule(h.N, p->NW, kChainUnitPiece);
+    const auto sched = chain_schedule(h.N, p->NW, precision != 1);
     int mx = 1;
     for (const auto &v : sched) mx = std::max<int>(mx, (int)v.size());
     std::vector<int4> flat((size_t)p->NW * mx, int4{0, 0, 0, 0});
@@ -528,7 +1009,8 @@ cudaError_t ChainModel::init(const ChainHost &h, int precision)
         cnt[w] = (int)sched[w].size();
         for (size_t q = 0; q < sched[w].size(); ++q) {
             const UnitDesc &u = sched[w][q];
-            flat[(size_t)w * mx + q] = int4{u.I, u.J, u.tb | (u.te << 8) | (u.flags << 16), 0};
+            flat[(size_t)w * mx + q] =
+                int4{u.I1, u.I2, u.J, u.kind | (u.near1 << 8) | (u.near2 << 9) | (u.pair_next << 10)};
         }
     }
     p->max_units = mx;
@@ -571,6 +1053,7 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     a.unit_count = m->unit_count;
     a.err = L.err;
     a.force_out = L.force_out;
+    a.start = L.start;
     a.step_begin = L.step_begin;
     a.step_end = L.step_end;
     a.N = m->geo.N;

@@ -21,16 +21,18 @@ struct ChainGeometry {
     int N = 0, Np = 0, n_tiles = 0, w_last = 32;
 };
 
-// One ring unit of the nonbonded phase: i-tile I against j-tile J, ring
-// steps [tb, te); flags bit 0 = diagonal tile, bit 1 = neighbouring tiles
-// (exclusions |i - j| <= 2 possible).
+// One ring piece of the nonbonded phase: i-tile I1 (and I2 >= 0 for a dual
+// piece, -1 otherwise) against j-tile J with piece kind `kind` (ring width,
+// first ring step, step count, diagonal; see piece_kind in chain.cu).
+// near1 / near2: that i-tile neighbours J, so exclusions |i - j| <= 2 occur.
 struct UnitDesc {
-    int I, J, tb, te, flags;
+    int I1, I2, J, kind, near1, near2;
+    int pair_next = 0;  // packed width-32 piece run interleaved with the next record
 };
 
-constexpr int kChainUnitPiece = 8;  // ring steps per scheduled unit
 ChainGeometry chain_geometry(int N);
-std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, int piece);
+// packed: the FP32 f32x2 pieces (kinds 8, 10..15); else the scalar pieces (0..10)
+std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed);
 
 // Everything one launch of a simulation kernel needs about the run.
 struct RunLaunch {
@@ -40,6 +42,7 @@ struct RunLaunch {
     const long long *nsteps_w = nullptr, *nequil_w = nullptr, *off_w = nullptr, *tw = nullptr;
     int *err = nullptr;
     double *force_out = nullptr;
+    const double *start = nullptr;  // optional per-replica start state (chain [rep][N][3], 1D [rep])
     long long step_begin = 0, step_end = 0;
     int replicas = 0, stride = 1, n_blocks = 0;
     uint32_t uid_base = 0;
@@ -94,6 +97,40 @@ cudaError_t reduce_noalloc_launch(const float *x, const double *lambda, int n_wi
                                   long long samples_per_window, double k, double kT, double *out, cudaStream_t st);
 cudaError_t work_samples_launch(const ReduceLayout &L, int mode, long long samples_per_replica, double *out,
                                 cudaStream_t st);
+
+// Surrogate MLP (mlp.cu)
+constexpr int kMlpParams = 64 + 64 + 64 * 64 + 64 + 2 * 64 + 2;
+struct MlpLaunch {
+    float *params = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+    int adam_t = 0;
+    double lr = 1e-3, c = 0, h = 1;
+    const double *lam_in = nullptr;
+    const float *x_in = nullptr;
+    int n = 0;
+    const float *xs = nullptr;
+    const double *win_lambda = nullptr;
+    const long long *win_off = nullptr, *win_tw = nullptr;
+    int n_windows = 0, replicas = 0;
+    long long total = 0;
+    int mode = 0, steps = 0, batch = 0;
+    unsigned long long seed = 0;
+    double *out_mu = nullptr, *out_logvar = nullptr;
+    float *out_grad = nullptr;
+    double *out_loss = nullptr;
+    int *err = nullptr;
+};
+cudaError_t mlp_launch(const MlpLaunch &L, cudaStream_t st);
+
+// Learned window placement (adaptive.cu)
+cudaError_t overlap_launch(const double *mu, const double *log_var, int n, double *ovl, cudaStream_t st);
+constexpr int kMaxSeedCandidates = 4096;
+struct SeedJob {
+    double target;                         // predicted mean x at the inserted window
+    int n_cand;                            // candidates (end states of the neighbours)
+    const void *cand[kMaxSeedCandidates];  // positions (chain: 4 values per bead) or x (1D)
+};
+cudaError_t seed_launch(const SeedJob *jobs, int n_jobs, int max_cand, int N, int Np, int replicas, bool fp64,
+                        double *start, cudaStream_t st);
 
 cudaError_t philox_launch(unsigned long long seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int n,
                           uint32_t *raw, float *normals, cudaStream_t st);

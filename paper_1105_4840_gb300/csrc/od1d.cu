@@ -13,6 +13,7 @@ struct Od1dArgs {
     const double *lambda;
     const long long *nsteps_w, *nequil_w, *off_w, *tw;
     double *state;
+    const double *start;
     float *xout;
     int *err;
     long long step_begin, step_end;
@@ -31,7 +32,7 @@ __global__ void od1d_kernel(const Od1dArgs a)
     const long long nsteps = a.nsteps_w[w], nequil = a.nequil_w[w];
     const long long s0 = a.step_begin, s1 = a.step_end < nsteps ? a.step_end : nsteps;
     if (s0 >= s1) return;
-    double x = s0 == 0 ? a.x0 : a.state[rep];
+    double x = s0 == 0 ? (a.start ? a.start[rep] : a.x0) : a.state[rep];
     const double amp = sqrt(2.0 * a.kT * a.dt / a.gamma);
     const long long base = a.off_w[w] + (long long)r * a.tw[w];
     Normal4<double> n = philox_normals<double>(a.seed, 0u, uid, (uint32_t)(s0 >> 2), kTagOStep);
@@ -63,6 +64,7 @@ cudaError_t od1d_launch(const Od1dParams &m, const RunLaunch &L, int n_rep, cuda
     a.off_w = L.off_w;
     a.tw = L.tw;
     a.state = reinterpret_cast<double *>(L.state);
+    a.start = L.start;
     a.xout = L.xout;
     a.err = L.err;
     a.step_begin = L.step_begin;

@@ -61,6 +61,17 @@ class FreeEnergyResult(C.Structure):
     _fields_ = [("capacity", C.c_int)] + [(("lambda_" if f == "lambda" else f), _D) for f in RESULT_FIELDS]
 
 
+class AdaptiveParams(C.Structure):
+    _fields_ = [("overlap_threshold", C.c_double), ("max_rounds", C.c_int), ("max_windows", C.c_int),
+                ("mlp_steps", C.c_int), ("mlp_batch", C.c_int), ("mlp_lr", C.c_double), ("mlp_seed", C.c_uint64),
+                ("mlp_init", _F)]
+
+
+class AdaptiveInfo(C.Structure):
+    _fields_ = [("n_windows", C.c_int), ("rounds", C.c_int), ("inserted", C.c_int), ("gpu_seconds", C.c_double),
+                ("mlp_loss", C.c_double), ("lambda_", C.c_double * 1024)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with paper_1105_4840_gb300.build.build()")
@@ -71,6 +82,7 @@ def _load():
     L.pmf_destroy_system.restype = None
     for name in ("pmf_run_windows", "pmf_run_prepare"):
         getattr(L, name).argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.POINTER(P)]
+    L.pmf_run_prepare_seeded.argtypes = [P, _D, C.c_int, C.POINTER(RunParams), _D, C.POINTER(P)]
     L.pmf_run_launch.argtypes = [P]
     L.pmf_run_wait.argtypes = [P]
     L.pmf_destroy_run.argtypes = [P]
@@ -85,19 +97,30 @@ def _load():
     L.pmf_philox.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int,
                              C.POINTER(C.c_uint32), _F]
     L.pmf_chain_forces.argtypes = [P, C.c_int, _D, C.c_double, C.c_double, _D]
-    L.pmf_chain_schedule.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_size_t,
+    L.pmf_chain_schedule.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_size_t,
                                      C.POINTER(C.c_size_t), C.POINTER(C.c_int)]
     L.pmf_run_reduce.argtypes = [P]
     L.pmf_free_energy_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64,
                                           C.c_double, C.c_double, C.c_void_p]
+    L.pmf_mlp_create.argtypes = [_F, C.c_double, C.c_double, C.POINTER(P)]
+    L.pmf_mlp_destroy.argtypes = [P]
+    L.pmf_mlp_destroy.restype = None
+    L.pmf_mlp_get_params.argtypes = [P, _F]
+    L.pmf_mlp_predict.argtypes = [P, _D, C.c_int, _D, _D]
+    L.pmf_mlp_gradient.argtypes = [P, _D, _F, C.c_int, _F, _D]
+    L.pmf_mlp_train.argtypes = [P, P, C.c_int, C.c_int, C.c_double, C.c_uint64, _D]
+    L.pmf_overlap.argtypes = [_D, _D, C.c_int, _D]
+    L.pmf_run_adaptive.argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.POINTER(AdaptiveParams),
+                                   C.POINTER(AdaptiveInfo), C.POINTER(FreeEnergyResult)]
     L.pmf_set_stream.argtypes = [C.c_void_p]
     L.pmf_last_error.restype = C.c_char_p
     L.pmf_version.restype = C.c_char_p
-    for name in ("pmf_create_system", "pmf_run_windows", "pmf_run_prepare", "pmf_run_launch",
+    for name in ("pmf_create_system", "pmf_run_windows", "pmf_run_prepare", "pmf_run_prepare_seeded", "pmf_run_launch",
                  "pmf_run_wait", "pmf_get_run_info", "pmf_x_samples", "pmf_work_samples",
                  "pmf_free_energy", "pmf_free_energy_from_samples", "pmf_final_state", "pmf_philox",
                  "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_free_energy_noalloc",
-                 "pmf_set_stream"):
+                 "pmf_mlp_create", "pmf_mlp_get_params", "pmf_mlp_predict", "pmf_mlp_gradient", "pmf_mlp_train",
+                 "pmf_overlap", "pmf_run_adaptive", "pmf_set_stream"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -265,6 +288,16 @@ def pmf_run_prepare(system: System, lambdas, params) -> Run:
     return Run(h, lam, keep=(p, keep, system))
 
 
+def pmf_run_prepare_seeded(system: System, lambdas, params, start) -> Run:
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    st = np.ascontiguousarray(start, dtype=np.float64)
+    p, keep = params
+    h = C.c_void_p()
+    _check(lib.pmf_run_prepare_seeded(system.handle, _dp(lam), lam.size, C.byref(p), _dp(st), C.byref(h)),
+           "pmf_run_prepare_seeded")
+    return Run(h, lam, keep=(p, keep, system, st))
+
+
 def pmf_run_windows(system: System, lambdas, params) -> Run:
     lam = np.ascontiguousarray(lambdas, dtype=np.float64)
     p, keep = params
@@ -308,15 +341,15 @@ def pmf_chain_forces(system: System, chain, pos, lam, k):
     return f
 
 
-def pmf_chain_schedule(N, NW=4):
-    """Host schedule: int array [units, 6] (warp, I, J, t_begin, t_end, flags), padded N."""
+def pmf_chain_schedule(N, NW=4, precision=PMF_FP32):
+    """Host schedule: int array [pieces, 8] (warp, I1, I2, J, kind, near1, near2, pair_next), padded N."""
     n = C.c_size_t()
     pad = C.c_int()
-    lib.pmf_chain_schedule(N, NW, None, 0, C.byref(n), C.byref(pad))
-    out = np.zeros(6 * n.value, dtype=np.int32)
-    _check(lib.pmf_chain_schedule(N, NW, out.ctypes.data_as(C.POINTER(C.c_int)), out.size, C.byref(n),
-                                  C.byref(pad)), "pmf_chain_schedule")
-    return out.reshape(-1, 6), pad.value
+    lib.pmf_chain_schedule(N, NW, precision, None, 0, C.byref(n), C.byref(pad))
+    out = np.zeros(8 * n.value, dtype=np.int32)
+    _check(lib.pmf_chain_schedule(N, NW, precision, out.ctypes.data_as(C.POINTER(C.c_int)), out.size,
+                                  C.byref(n), C.byref(pad)), "pmf_chain_schedule")
+    return out.reshape(-1, 8), pad.value
 
 
 def pmf_free_energy_noalloc(x_dev, lambda_dev, n_windows, replicas, samples_per_window, k, kT, out_dev):
@@ -326,3 +359,89 @@ def pmf_free_energy_noalloc(x_dev, lambda_dev, n_windows, replicas, samples_per_
     _check(lib.pmf_free_energy_noalloc(C.c_void_p(int(x_dev)), C.c_void_p(int(lambda_dev)), n_windows,
                                        replicas, samples_per_window, k, kT, C.c_void_p(int(out_dev))),
            "pmf_free_energy_noalloc")
+
+
+PMF_MLP_PARAMS = 4418
+
+
+def pack_mlp_params(p) -> np.ndarray:
+    """FP32 packing W1[64], b1[64], W2[64][64], b2[64], W3[2][64], b3[2]."""
+    return np.concatenate([np.asarray(p[k], dtype=np.float32).ravel()
+                           for k in ("W1", "b1", "W2", "b2", "W3", "b3")]).astype(np.float32)
+
+
+class Mlp:
+    """Owner of a pmf_mlp handle (surrogate lambda -> mean / log-variance of x)."""
+
+    def __init__(self, params, c, h):
+        w = np.ascontiguousarray(params, dtype=np.float32)
+        if w.size != PMF_MLP_PARAMS:
+            raise ValueError("need PMF_MLP_PARAMS weights")
+        self.handle = C.c_void_p()
+        _check(lib.pmf_mlp_create(w.ctypes.data_as(_F), c, h, C.byref(self.handle)), "pmf_mlp_create")
+
+    def close(self):
+        if self.handle:
+            lib.pmf_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = np.zeros(PMF_MLP_PARAMS, dtype=np.float32)
+        _check(lib.pmf_mlp_get_params(self.handle, out.ctypes.data_as(_F)), "pmf_mlp_get_params")
+        return out
+
+    def predict(self, lam):
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        mu = np.zeros_like(lam)
+        lv = np.zeros_like(lam)
+        _check(lib.pmf_mlp_predict(self.handle, _dp(lam), lam.size, _dp(mu), _dp(lv)), "pmf_mlp_predict")
+        return mu, lv
+
+    def gradient(self, lam, x):
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        g = np.zeros(PMF_MLP_PARAMS, dtype=np.float32)
+        loss = C.c_double()
+        _check(lib.pmf_mlp_gradient(self.handle, _dp(lam), x.ctypes.data_as(_F), lam.size, g.ctypes.data_as(_F),
+                                    C.byref(loss)), "pmf_mlp_gradient")
+        return g, loss.value
+
+    def train(self, run, steps, batch, lr, seed):
+        loss = C.c_double()
+        _check(lib.pmf_mlp_train(self.handle, run.handle, steps, batch, lr, seed, C.byref(loss)), "pmf_mlp_train")
+        return loss.value
+
+
+def pmf_overlap(mu, log_var):
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    lv = np.ascontiguousarray(log_var, dtype=np.float64)
+    out = np.zeros(mu.size - 1)
+    _check(lib.pmf_overlap(_dp(mu), _dp(lv), mu.size, _dp(out)), "pmf_overlap")
+    return out
+
+
+def pmf_run_adaptive(system: System, lambda0, params, mlp_init, threshold=0.3, max_rounds=3, max_windows=64,
+                     mlp_steps=300, mlp_batch=512, mlp_lr=3e-3, mlp_seed=1):
+    """Surrogate-guided window insertion; returns (info dict, free-energy dict)."""
+    lam = np.ascontiguousarray(lambda0, dtype=np.float64)
+    w = np.ascontiguousarray(mlp_init, dtype=np.float32)
+    p, keep = params
+    ap = AdaptiveParams(threshold, max_rounds, max_windows, mlp_steps, mlp_batch, mlp_lr, mlp_seed,
+                        w.ctypes.data_as(_F))
+    info = AdaptiveInfo()
+    res_arrays = {f: np.zeros(max_windows) for f in RESULT_FIELDS}
+    res = FreeEnergyResult(capacity=max_windows,
+                           **{("lambda_" if f == "lambda" else f): _dp(a) for f, a in res_arrays.items()})
+    _check(lib.pmf_run_adaptive(system.handle, _dp(lam), lam.size, C.byref(p), C.byref(ap), C.byref(info),
+                                C.byref(res)), "pmf_run_adaptive")
+    n = info.n_windows
+    out = {f: a[:n].copy() for f, a in res_arrays.items()}
+    meta = dict(n_windows=n, rounds=info.rounds, inserted=info.inserted, gpu_seconds=info.gpu_seconds,
+                mlp_loss=info.mlp_loss, lambdas=np.array(info.lambda_[:n]))
+    return meta, out

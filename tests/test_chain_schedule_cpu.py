@@ -17,66 +17,127 @@ def _width(t, n_tiles, w_last):
     return w_last if t == n_tiles - 1 else 32
 
 
+# kind: (ring width W, first step TB, steps NST, diagonal, packed offset D or 0)
+KINDS = {0: (32, 0, 8, 0, 0), 1: (32, 8, 8, 0, 0), 2: (32, 16, 8, 0, 0), 3: (32, 24, 8, 0, 0),
+         4: (32, 1, 8, 1, 0), 5: (32, 9, 8, 1, 0), 6: (16, 0, 8, 0, 0), 7: (16, 8, 8, 0, 0),
+         8: (16, 1, 8, 1, 0), 9: (8, 0, 8, 0, 0), 10: (8, 1, 4, 1, 0),
+         11: (32, 0, 8, 0, 8), 12: (32, 16, 8, 0, 8), 13: (32, 1, 8, 1, 8), 14: (16, 0, 8, 0, 8),
+         15: (8, 0, 4, 0, 4)}
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("NW", [4, 8])
 @pytest.mark.parametrize("N", NS)
-def test_ring_units_cover_pairs_once(N, NW):
+def test_ring_pieces_cover_pairs_once(N, NW, precision):
     from paper_1105_4840_gb300 import pmf
 
-    units, Np = pmf.pmf_chain_schedule(N, NW)
+    units, Np = pmf.pmf_chain_schedule(N, NW, precision)
     n_tiles = (N + 31) // 32
     rem = N % 32
     w_last = 32 if rem == 0 else (8 if rem <= 8 else (16 if rem <= 16 else 32))
     assert Np == (n_tiles - 1) * 32 + w_last
     count = np.zeros((Np, Np), dtype=np.int64)
-    for (w, I, J, tb, te, flags) in units:
-        assert 0 <= w < NW and 0 <= I <= J < n_tiles and 0 <= tb < te
-        W = _width(J, n_tiles, w_last)
-        wI = _width(I, n_tiles, w_last)
-        assert te <= (W // 2 + 1 if I == J else W)
-        diag, near = bool(flags & 1), bool(flags & 2)
-        assert diag == (I == J) and near == (J - I <= 1)
+    for q, (w, I1, I2, J, kind, near1, near2, pair_next) in enumerate(units):
+        assert 0 <= w < NW and 0 <= I1 <= J < n_tiles and kind in KINDS
+        if pair_next:  # interleaved with the next record of the same warp: both width-32 packed
+            assert precision == 0 and 11 <= kind <= 13
+            assert units[q + 1][0] == w and 11 <= units[q + 1][4] <= 13 and units[q + 1][7] == 0
+            assert q == 0 or units[q - 1][7] == 0
+        W, TB, NST, DIAG, DP = KINDS[kind]
+        assert (kind >= 11 or kind in (8, 10)) if precision == 0 else kind <= 10
+        if DP:
+            _packed_piece(count, N, Np, n_tiles, w_last, I1, J, near1, W, TB, NST, DIAG, DP)
+            continue
+        assert W == _width(J, n_tiles, w_last)
+        assert bool(DIAG) == (I1 == J)
+        tiles = [(I1, near1)] + ([(I2, near2)] if I2 >= 0 else [])
+        if I2 >= 0:
+            assert not DIAG and I1 < I2 < J
         lanes = np.arange(32)
         lr = lanes & (W - 1)
         src = (lanes & ~(W - 1)) | ((lr + 1) & (W - 1))
-        acc = (lr + tb) & (W - 1)  # j index whose force each lane carries
-        for t in range(tb, te):
+        acc = (lr + TB) & (W - 1)  # j index whose force each lane carries
+        for k in range(NST):
+            t = TB + k
             assert np.all(acc == ((lr + t) & (W - 1)))
             jidx = lr + t
             assert jidx.max() < 2 * W <= 64  # duplicated tile copy
             j = J * 32 + (jidx & (W - 1))
-            i = I * 32 + lanes
-            ion = lanes < wI
-            masked = np.zeros(32, dtype=bool)
-            if t < 3 and near:
-                masked |= np.abs(i - j) <= 2
-            if diag and 2 * t == W:
-                masked |= lr >= W // 2
-            ok = ion & ~masked & (i < N) & (j < N)
-            assert np.all(i[ok] != j[ok])
-            assert np.all(np.abs(i[ok] - j[ok]) >= 3)
-            for a, b in zip(i[ok], j[ok]):
-                count[min(a, b), max(a, b)] += 1
-            if t + 1 < te:
+            for I, near in tiles:
+                assert bool(near) == (J - I == 1) or (DIAG and near)
+                wI = _width(I, n_tiles, w_last)
+                i = I * 32 + lanes
+                ion = lanes < wI
+                masked = np.zeros(32, dtype=bool)
+                if t < 3 and near:
+                    masked |= np.abs(i - j) <= 2
+                if DIAG and 2 * t == W:
+                    masked |= lr >= W // 2
+                ok = ion & ~masked & (i < N) & (j < N)
+                assert np.all(i[ok] != j[ok])
+                assert np.all(np.abs(i[ok] - j[ok]) >= 3)
+                for a, b in zip(i[ok], j[ok]):
+                    count[min(a, b), max(a, b)] += 1
+                assert I * 32 + wI <= Np
+            if k + 1 < NST:
                 acc = acc[src]
-        # flush: lanes < W write bead J*32 + ((lr + te - 1) & (W - 1)); groups of
-        # W lanes (reduced by xor) must carry the same bead
-        flush = (lr + te - 1) & (W - 1)
+        flush = (lr + TB + NST - 1) & (W - 1)
         assert np.all(acc == flush)
         for g in range(32 // W):
             assert np.all(acc[g * W:(g + 1) * W] == acc[:W])
         assert (J * 32 + flush[:W]).max() < Np
-        assert I * 32 + wI <= Np
     want = np.zeros_like(count)
     for a in range(N):
         want[a, a + 3:N] = 1
     np.testing.assert_array_equal(count, want)
 
 
+def _packed_piece(count, N, Np, n_tiles, w_last, I, J, near, W, TB, NDS, DIAG, D):
+    """Replay of packed_piece: double step k evaluates ring steps t = TB + k
+    (stream a) and t + D (stream b); both j-force streams rotate by one lane."""
+    assert D == (8 if W == 32 else W // 2)
+    lanes = np.arange(32)
+    lr = lanes & (W - 1)
+    src = (lanes & ~(W - 1)) | ((lr + 1) & (W - 1))
+    acc_a = (lr + TB) & (W - 1)
+    acc_b = (lr + TB + D) & (W - 1)
+    wI = _width(I, n_tiles, w_last)
+    i = I * 32 + lanes
+    ion = lanes < wI
+    for k in range(NDS):
+        t = TB + k
+        assert (lr + t).max() < 2 * W  # packed entry index p = lr + t
+        for stream, tt, acc in (("a", t, acc_a), ("b", t + D, acc_b)):
+            assert np.all(acc == ((lr + tt) & (W - 1)))
+            j = J * 32 + ((lr + tt) & (W - 1))
+            masked = np.zeros(32, dtype=bool)
+            if stream == "a" and t < 3 and near:
+                masked |= np.abs(i - j) <= 2
+            if stream == "b" and DIAG and 2 * tt == W:
+                masked |= lr >= W // 2
+            ok = ion & ~masked & (i < N) & (j < N)
+            assert np.all(i[ok] != j[ok])
+            assert np.all(np.abs(i[ok] - j[ok]) >= 3)
+            for a, b in zip(i[ok], j[ok]):
+                count[min(a, b), max(a, b)] += 1
+        if k + 1 < NDS:
+            acc_a, acc_b = acc_a[src], acc_b[src]
+    fa = (lr + TB + NDS - 1) & (W - 1)
+    fb = (lr + TB + NDS - 1 + D) & (W - 1)
+    assert np.all(acc_a == fa) and np.all(acc_b == fb)
+    for g in range(32 // W):
+        assert np.all(acc_a[g * W:(g + 1) * W] == acc_a[:W])
+        assert np.all(acc_b[g * W:(g + 1) * W] == acc_b[:W])
+    assert max((J * 32 + fa[:W]).max(), (J * 32 + fb[:W]).max()) < Np
+    assert I * 32 + wI <= Np
+
+
 def test_schedule_is_balanced():
     from paper_1105_4840_gb300 import pmf
 
-    units, _ = pmf.pmf_chain_schedule(104, 4)
-    load = np.zeros(4)
-    for (w, I, J, tb, te, flags) in units:
-        load[w] += te - tb
-    assert load.max() <= 1.25 * load.mean()
+    for precision in (0, 1):
+        units, _ = pmf.pmf_chain_schedule(104, 4, precision)
+        load = np.zeros(4)
+        for (w, I1, I2, J, kind, n1, n2, pn) in units:
+            load[w] += KINDS[kind][2] * (2 if (I2 >= 0 or KINDS[kind][4]) else 1)
+        assert load.max() <= 1.5 * load.mean()

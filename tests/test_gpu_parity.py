@@ -26,12 +26,17 @@ def test_philox_bitwise_and_normals(pmf):
         raw_g, nor_g = pmf.pmf_philox(seed, c0, c1, c2, c3, n)
         raw_o, nor_o = _clib.philox_bulk(seed, c0, c1, c2, c3, n)
         np.testing.assert_array_equal(raw_g, raw_o)
-        # FP32 Box-Muller: u = (b + 1/2) 2^-32 rounded to FP32 (spacing 2^-24
-        # near u = 1) perturbs r^2 = -2 ln u by <= 1.2e-7 absolute, i.e. r by
-        # <= 1.2e-7 / (2 r); logf / sqrtf / sincospif add a few ulps relative.
+        # FP32 Box-Muller error bound.  u = (b + 1/2) 2^-32 rounded to FP32:
+        # du/u <= 2^-23.  __logf: abs error <= 2^-21.41 on [0.5, 2], else 3 ulp,
+        # so d(r^2) <= 9.6e-7 + 3.6e-7 r^2 with r^2 = -2 ln u, and
+        # dr <= min(d(r^2) / 2r, sqrt(d(r^2))) + 1 ulp.  The angle
+        # 2 pi (u - 1/2) is off by <= 1.2e-6 and __sincosf adds <= 2^-21.19,
+        # so the cos/sin factor is off by <= 1.7e-6.
         u = (raw_o.astype(np.float64) + 0.5) / 2.0 ** 32
         r = np.sqrt(-2.0 * np.log(u[:, [0, 0, 2, 2]]))
-        bound = 4e-6 * r + 1.5e-7 / np.maximum(r, 1e-4) + 1e-6
+        dr2 = 9.6e-7 + 3.6e-7 * r * r
+        dr = np.minimum(dr2 / (2.0 * np.maximum(r, 1e-30)), np.sqrt(dr2)) + 1.2e-7 * r
+        bound = 1.25 * (1.7e-6 * r + dr + 1.2e-7 * np.abs(nor_o))
         assert np.all(np.abs(nor_g - nor_o) <= bound)
 
 

@@ -212,6 +212,8 @@ def main():
     n_rep = s * R
     uid_base = rank * n_rep
     sysh = pmf.pmf_create_system_chain([p], [start])
+    # untimed setup: pick warps per replica from short probes of this run
+    warps, _ = pmf.pmf_chain_autotune(sysh, run.lambdas, pmf.make_params(run, uid_base=uid_base), probe_steps=2000)
     rr = pmf.pmf_run_prepare(sysh, run.lambdas, pmf.make_params(run, uid_base=uid_base))
     replica_steps = n_rep * run.n_steps
     chunks = math.ceil(run.n_steps / 100000)
@@ -265,6 +267,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sys2 = pmf.pmf_create_system_chain([p], [start])
+        pmf.pmf_chain_set_warps(sys2, 0, warps)
         r2 = pmf.pmf_run_windows(sys2, run.lambdas, pmf.make_params(run, uid_base=uid_base))
         out = r2.free_energy()
         e2e_times.append(time.perf_counter() - t0)
@@ -288,7 +291,7 @@ def main():
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops,
             "traffic": (traffic or {}).get("dram_bytes_per_launch"),
-            "kernel": "chain_kernel<float,4>",
+            "kernel": f"chain_kernel<float,{warps}>",
             "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
             "frac_at_sampled_clock": (achieved / (sm_count * 256 * clk["sm_mhz"] * 1e6 / 1e12)
                                       if clk.get("sm_mhz") else None),
@@ -301,6 +304,7 @@ def main():
             "config": {"workload": WORKLOAD, "beads": N_BEADS, "windows": s, "replicas_per_window": R,
                        "md_steps_per_window": run.n_steps, "dt_ps": run.dt, "sample_stride": run.stride,
                        "forces": "fp32", "reductions": "fp64", "parallelism": f"replicas x{world}",
+                       "warps_per_replica": warps,
                        "l2": "256 MB flush between timed steps"},
             "e2e": {"value": e2e_value, "unit": "replica-steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -245,6 +245,18 @@ pmf_status pmf_free_energy_noalloc(const float *x, const double *lambda, int n_w
 pmf_status pmf_final_state(const pmf_run *run, double *pos, double *vel, size_t capacity,
                            size_t *n_written);
 
+/* ---- batching / autotuning ----------------------------------------------
+ * Warps per replica CTA of chain `chain` (4, 6 or 8 for FP32; FP64 uses 4);
+ * the host schedule of the nonbonded phase is rebuilt for the new count.
+ * Results are bit-reproducible for a given count; different counts sum the
+ * forces in different orders. */
+pmf_status pmf_chain_set_warps(pmf_system *sys, int chain, int warps);
+/* Time probe_steps steps of the given run (every window and replica, one
+ * warm-up launch each) for each warp count and keep the fastest; *best_warps
+ * and *best_ms (may be NULL) report the choice and its probe time. */
+pmf_status pmf_chain_autotune(pmf_system *sys, const double *lambda, int n_windows, const pmf_run_params *p,
+                              int probe_steps, int *best_warps, double *best_ms);
+
 /* ---- learned window placement: surrogate MLP ---------------------------
  * A small network lambda -> (mu, log sigma^2) of the reaction coordinate,
  * 1 -> 64 -> 64 -> 2 with SiLU, trained on a run's (lambda_i, x) samples by
@@ -341,22 +353,22 @@ pmf_status pmf_overlap(const double *mu, const double *log_var, int n, double *o
 
 /* Host-side schedule of the nonbonded phase for a chain of N beads, NW
  * warps per CTA and the integration precision (no GPU needed): the ring
- * pieces each warp executes, as records of 8 ints (warp, I1, I2 or -1, J,
- * kind, near1, near2, pair_next) in out[capacity]; *n_written receives the
- * record count.  pair_next = 1: this width-32 packed piece runs interleaved
- * with the warp's next record.  A piece pairs the 32-bead i-tile I1 (and I2) with j-tile J over the
- * ring steps t of `kind`; lane l meets j = J*32 + ((l mod W) + t) mod W:
+ * pieces each warp executes, as records of 7 ints (warp, I1, I2 or -1, J,
+ * kind, near1, near2) in out[capacity]; *n_written receives the record
+ * count.  A piece pairs the 32-bead i-tile I1 (and I2) with j-tile J; at
+ * ring step t lane l meets j = J*32 + ((l mod W) + t) mod W:
  *   scalar (FP64):  0..3  W 32, t = 8k..8k+7        4, 5  W 32 diagonal, t = 1..8, 9..16
  *                   6, 7  W 16, t = 0..7, 8..15      8     W 16 diagonal, t = 1..8
  *                   9     W 8,  t = 0..7             10    W 8 diagonal, t = 1..4
- *   packed (FP32, two steps t and t + D per f32x2 double step, D = 8 for W 32
- *   and 16, 4 for W 8; kinds 8 and 10 as above):
- *                   11    W 32, t = 0..7 (+8)        12    W 32, t = 16..23 (+8)
- *                   13    W 32 diagonal, t = 1..8 (+8)
- *                   14    W 16, t = 0..7 (+8)        15    W 8, t = 0..3 (+4)
+ *   quad (FP32): lane l holds i-beads at ring indices l and l + 1 and meets
+ *   ring positions l + t and l + t + D (D = 8 for W 32 and 16, 4 for W 8),
+ *   t stepping by 2 (kinds 8 and 10 as above):
+ *                   21    W 32, t = 1, 3, 5, 7       22    W 32, t = 17, 19, 21, 23
+ *                   23    W 32 diagonal, t = 2, 4, 6, 8
+ *                   24    W 16, t = 1, 3, 5, 7       25    W 8, t = 1, 3
  * near1/near2 flag i-tiles adjacent to J (exclusions |i - j| <= 2 possible).
  * Tiles are 32 beads except a last tile of 8, 16 or 32 (*padded receives the
- * padded bead count).  PMF_EINVAL if capacity < 8 * records. */
+ * padded bead count).  PMF_EINVAL if capacity < 7 * records. */
 pmf_status pmf_chain_schedule(int N, int NW, int precision, int *out, size_t capacity, size_t *n_written,
                               int *padded);
 

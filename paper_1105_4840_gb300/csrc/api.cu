@@ -888,6 +888,61 @@ pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, cons
     return copy_result(h.data(), m.n, res);
 }
 
+pmf_status pmf_chain_set_warps(pmf_system *sys, int chain, int warps)
+{
+    if (!sys || sys->model != PMF_MODEL_CHAIN || chain < 0 || chain >= (int)sys->chains.size())
+        return fail(PMF_EINVAL, "pmf_chain_set_warps: not a chain system / bad chain index");
+    cudaError_t e = sys->chains[chain]->set_warps(warps);
+    if (e == cudaErrorInvalidValue) return fail(PMF_EINVAL, "pmf_chain_set_warps: warps must be 4, 6 or 8 (FP64: 4)");
+    if (e != cudaSuccess) return cuda_fail(e, "pmf_chain_set_warps");
+    if (sys->chains[chain]->smem_bytes() > 227 * 1024) {
+        sys->chains[chain]->set_warps(4);
+        return fail(PMF_EINVAL, "pmf_chain_set_warps: shared memory would exceed 227 KB");
+    }
+    return PMF_OK;
+}
+
+pmf_status pmf_chain_autotune(pmf_system *sys, const double *lambda, int n_windows, const pmf_run_params *p,
+                              int probe_steps, int *best_warps, double *best_ms)
+{
+    if (!sys || !lambda || !p || probe_steps < 1) return fail(PMF_EINVAL, "pmf_chain_autotune: bad argument");
+    if (sys->model != PMF_MODEL_CHAIN) return fail(PMF_EINVAL, "pmf_chain_autotune: not a chain system");
+    ChainModel &m = *sys->chains[p->chain];
+    const int cand_fp32[3] = {4, 6, 8};
+    const int n_cand = m.precision() == PMF_FP64 ? 1 : 3;
+    pmf_run_params q = *p;
+    q.n_steps = probe_steps + 1;
+    q.n_steps_per_window = nullptr;
+    q.n_equil = probe_steps;
+    q.sample_stride = 1;
+    q.timeout_s = 0;
+    pmf_run *run = nullptr;
+    if (pmf_status s = pmf_run_prepare(sys, lambda, n_windows, &q, &run)) return s;
+    std::unique_ptr<pmf_run, void (*)(pmf_run *)> guard(run, pmf_destroy_run);
+    int best = m.warps();
+    double best_t = 1e300;
+    GpuTimer timer;
+    for (int c = 0; c < n_cand; ++c) {
+        if (pmf_chain_set_warps(sys, p->chain, cand_fp32[c]) != PMF_OK) continue;
+        if (pmf_status s = pmf_run_launch(run)) return s;  // warm-up
+        if (pmf_status s = pmf_run_wait(run)) return s;
+        const double before = timer.ms;
+        timer.start();
+        if (pmf_status s = pmf_run_launch(run)) return s;
+        CK(timer.stop(), "autotune timer");
+        if (pmf_status s = pmf_run_wait(run)) return s;
+        const double t = timer.ms - before;
+        if (t < best_t) {
+            best_t = t;
+            best = cand_fp32[c];
+        }
+    }
+    if (pmf_status s = pmf_chain_set_warps(sys, p->chain, best)) return s;
+    if (best_warps) *best_warps = best;
+    if (best_ms) *best_ms = best_t;
+    return PMF_OK;
+}
+
 pmf_status pmf_overlap(const double *mu, const double *log_var, int n, double *ovl)
 {
     if (!mu || !log_var || !ovl || n < 2) return fail(PMF_EINVAL, "pmf_overlap: bad argument");
@@ -975,20 +1030,19 @@ pmf_status pmf_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint
 pmf_status pmf_chain_schedule(int N, int NW, int precision, int *out, size_t capacity, size_t *n_written,
                               int *padded)
 {
-    if (N < 4 || N > 1024 || (NW != 4 && NW != 8) || (precision != PMF_FP32 && precision != PMF_FP64))
-        return fail(PMF_EINVAL, "pmf_chain_schedule: N in [4,1024], NW 4 or 8, precision FP32 or FP64");
+    if (N < 4 || N > 1024 || (NW != 4 && NW != 6 && NW != 8) || (precision != PMF_FP32 && precision != PMF_FP64))
+        return fail(PMF_EINVAL, "pmf_chain_schedule: N in [4,1024], NW 4, 6 or 8, precision FP32 or FP64");
     const auto sched = chain_schedule(N, NW, precision == PMF_FP32);
     size_t n = 0;
     for (const auto &v : sched) n += v.size();
     if (n_written) *n_written = n;
     if (padded) *padded = chain_geometry(N).Np;
-    if (!out || capacity < 8 * n) return fail(PMF_EINVAL, "pmf_chain_schedule: capacity too small");
+    if (!out || capacity < 7 * n) return fail(PMF_EINVAL, "pmf_chain_schedule: capacity too small");
     size_t q = 0;
     for (int w = 0; w < NW; ++w)
         for (const UnitDesc &u : sched[w]) {
-            int *o = out + 8 * q++;
+            int *o = out + 7 * q++;
             o[0] = w; o[1] = u.I1; o[2] = u.I2; o[3] = u.J; o[4] = u.kind; o[5] = u.near1; o[6] = u.near2;
-            o[7] = u.pair_next;
         }
     return PMF_OK;
 }

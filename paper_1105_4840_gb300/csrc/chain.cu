@@ -250,65 +250,76 @@ __device__ __forceinline__ void ring_piece(const Smem<R> &s, Vec4<R> *fw, int I1
     }
 }
 
-// Packed FP32 double steps: lane l evaluates ring steps t and t + D at once
-// with f32x2 arithmetic (one i-bead, two j-beads); the j-force streams of
-// the two steps are the two halves of a packed accumulator and both move one
-// lane per double step.
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// Quad pieces (FP32): lane l holds two neighbouring i-beads of its ring,
+// i1 at ring index l and i2 at l + 1, and at ring step t meets the j-beads at
+// ring positions l + t (stream a) and l + t + D (stream b).  i1 sees ring
+// offsets t and t + D, i2 sees t - 1 and t + D - 1, so odd steps t cover all
+// offsets of an off-diagonal j-ring (even steps 2..W/2 the half ring of a
+// diagonal tile).  Four pairs per lane and step share one set of j loads and
+// one rotation (by two lanes) of the j-force streams, halving the shared
+// loads and shuffles per pair; the two i-beads form the packed f32x2 operand.
 template <int W>
-__device__ __forceinline__ void packed_piece(const Smem<float> &s, Vec4<float> *fw, int I, int J, int TB, int NDS,
-                                             bool diag, bool near, int wI, int lane)
+__device__ __forceinline__ void quad_piece(const Smem<float> &s, Vec4<float> *fw, int I, int J, int TB, int NST,
+                                           bool diag, bool near, int wI, int lane)
 {
     constexpr int D = pair_offset(W);
     const int lr = lane & (W - 1);
-    const bool ion = lane < wI;
-    Vec4<float> pi{-1e4f, -1e4f, -1e4f, 0.f};
-    Vec2<float> qi{0.f, 0.f};
-    if (ion) {
-        pi = s.posd[I * 64 + lane];
-        qi = s.eqd[I * 64 + lane];
-    }
-    const float2 nx = f2(-pi.x, -pi.x), ny = f2(-pi.y, -pi.y), nz = f2(-pi.z, -pi.z);
-    const float2 si = f2(pi.w, pi.w), ei = f2(qi.x, qi.x), ci = f2(qi.y, qi.y);
+    const int l2 = (lane & ~(W - 1)) | ((lr + 1) & (W - 1));  // lane of i2 within the i-tile
+    const bool on1 = lane < wI, on2 = l2 < wI;
+    Vec4<float> p1{-1e4f, -1e4f, -1e4f, 0.f}, p2{-2e4f, -1e4f, -1e4f, 0.f};
+    Vec2<float> q1{0.f, 0.f}, q2{0.f, 0.f};
+    if (on1) { p1 = s.posd[I * 64 + lane]; q1 = s.eqd[I * 64 + lane]; }
+    if (on2) { p2 = s.posd[I * 64 + l2]; q2 = s.eqd[I * 64 + l2]; }
+    // i-bead data duplicated across the packed halves (streams a, b)
+    const float2 nx1 = f2(-p1.x, -p1.x), ny1 = f2(-p1.y, -p1.y), nz1 = f2(-p1.z, -p1.z);
+    const float2 nx2 = f2(-p2.x, -p2.x), ny2 = f2(-p2.y, -p2.y), nz2 = f2(-p2.z, -p2.z);
+    const float2 s1 = f2(p1.w, p1.w), s2 = f2(p2.w, p2.w);
+    const float2 e1 = f2(q1.x, q1.x), e2 = f2(q2.x, q2.x), c1 = f2(q1.y, q1.y), c2 = f2(q2.y, q2.y);
     const float2 two = f2(2.f, 2.f), mone = f2(-1.f, -1.f);
-    float2 fix = f2(0.f, 0.f), fiy = fix, fiz = fix, fjx = fix, fjy = fix, fjz = fix;
+    float2 f1x = f2(0.f, 0.f), f1y = f1x, f1z = f1x, f2x = f1x, f2y = f1x, f2z = f1x;
+    float2 fjx = f1x, fjy = f1x, fjz = f1x;
     const float4 *A = s.posp + 2 * (64 * J + lr);
     const float4 *E = s.eqp + 64 * J + lr;
-    const int src = (lane & ~(W - 1)) | ((lr + 1) & (W - 1));
-    const bool mask_a = near && TB < 3;                      // exclusions at t < 3
-    const bool mask_b = diag && lr >= (W >> 1);             // last step of a diagonal: half the lanes
+    const int src = (lane & ~(W - 1)) | ((lr + 2) & (W - 1));
+    const int gi1 = I * 32 + lane, gi2 = I * 32 + l2;
+    const bool mask_near = near && TB < 4;
+    const bool mask_half = diag && lr >= (W >> 1);
 #pragma unroll 2
-    for (int k = 0; k < NDS; ++k) {
-        const int t = TB + k;
+    for (int k = 0; k < NST; ++k) {
+        const int t = TB + 2 * k;
         const float4 a = A[2 * t], b = A[2 * t + 1], e = E[t];
-        const float2 dx = __fadd2_rn(f2(a.x, a.y), nx);
-        const float2 dy = __fadd2_rn(f2(a.z, a.w), ny);
-        const float2 dz = __fadd2_rn(f2(b.x, b.y), nz);
-        float2 r2 = __fmul2_rn(dx, dx);
-        r2 = __ffma2_rn(dy, dy, r2);
-        r2 = __ffma2_rn(dz, dz, r2);
-        const float2 ri = f2(rsqrtf(r2.x), rsqrtf(r2.y));
-        const float2 ri2 = __fmul2_rn(ri, ri);
-        const float2 sg = __fadd2_rn(si, f2(b.z, b.w));
-        const float2 x2 = __fmul2_rn(__fmul2_rn(sg, sg), ri2);
-        const float2 x6 = __fmul2_rn(__fmul2_rn(x2, x2), x2);
-        const float2 ee = __fmul2_rn(ei, f2(e.x, e.y));
-        const float2 qq = __fmul2_rn(ci, f2(e.z, e.w));
-        const float2 lj = __fmul2_rn(__fmul2_rn(ee, x6), __ffma2_rn(x6, two, mone));
-        float2 fr = __fmul2_rn(__ffma2_rn(qq, ri, lj), ri2);  // -dU/dr / r for both pairs
-        if (mask_a && t < 3) {
-            const int d = I * 32 + lane - (J * 32 + ((lr + t) & (W - 1)));
-            if (d <= 2 && d >= -2) fr.x = 0.f;
+        const float2 xj = f2(a.x, a.y), yj = f2(a.z, a.w), zj = f2(b.x, b.y), sj = f2(b.z, b.w);
+        const float2 ej = f2(e.x, e.y), cj = f2(e.z, e.w);
+        // pairs of i1 with (j_a, j_b)
+        const float2 dx1 = __fadd2_rn(xj, nx1), dy1 = __fadd2_rn(yj, ny1), dz1 = __fadd2_rn(zj, nz1);
+        // pairs of i2 with (j_a, j_b)
+        const float2 dx2 = __fadd2_rn(xj, nx2), dy2 = __fadd2_rn(yj, ny2), dz2 = __fadd2_rn(zj, nz2);
+        float2 r21 = __fmul2_rn(dx1, dx1), r22 = __fmul2_rn(dx2, dx2);
+        r21 = __ffma2_rn(dy1, dy1, r21); r22 = __ffma2_rn(dy2, dy2, r22);
+        r21 = __ffma2_rn(dz1, dz1, r21); r22 = __ffma2_rn(dz2, dz2, r22);
+        const float2 ri1 = f2(rsqrtf(r21.x), rsqrtf(r21.y)), ri2_ = f2(rsqrtf(r22.x), rsqrtf(r22.y));
+        const float2 iq1 = __fmul2_rn(ri1, ri1), iq2 = __fmul2_rn(ri2_, ri2_);
+        const float2 sg1 = __fadd2_rn(s1, sj), sg2 = __fadd2_rn(s2, sj);
+        const float2 x21 = __fmul2_rn(__fmul2_rn(sg1, sg1), iq1), x22 = __fmul2_rn(__fmul2_rn(sg2, sg2), iq2);
+        const float2 x61 = __fmul2_rn(__fmul2_rn(x21, x21), x21), x62 = __fmul2_rn(__fmul2_rn(x22, x22), x22);
+        const float2 lj1 = __fmul2_rn(__fmul2_rn(__fmul2_rn(e1, ej), x61), __ffma2_rn(x61, two, mone));
+        const float2 lj2 = __fmul2_rn(__fmul2_rn(__fmul2_rn(e2, ej), x62), __ffma2_rn(x62, two, mone));
+        float2 fr1 = __fmul2_rn(__ffma2_rn(__fmul2_rn(c1, cj), ri1, lj1), iq1);
+        float2 fr2 = __fmul2_rn(__ffma2_rn(__fmul2_rn(c2, cj), ri2_, lj2), iq2);
+        if (mask_near && t < 4) {  // exclusions |i - j| <= 2 can only meet stream a at ring offsets <= 2
+            const int gj = J * 32 + ((lr + t) & (W - 1));
+            const int d1 = gi1 - gj, d2 = gi2 - gj;
+            if (d1 <= 2 && d1 >= -2) fr1.x = 0.f;
+            if (d2 <= 2 && d2 >= -2) fr2.x = 0.f;
         }
-        if (mask_b && k == NDS - 1) fr.y = 0.f;  // ring step t + D = W/2
-        fix = __ffma2_rn(fr, dx, fix);
-        fiy = __ffma2_rn(fr, dy, fiy);
-        fiz = __ffma2_rn(fr, dz, fiz);
-        fjx = __ffma2_rn(fr, dx, fjx);
-        fjy = __ffma2_rn(fr, dy, fjy);
-        fjz = __ffma2_rn(fr, dz, fjz);
-        if (k + 1 < NDS) {
+        if (mask_half && k == NST - 1) fr1.y = 0.f;  // offset W/2 of a diagonal: counted from one side only
+        f1x = __ffma2_rn(fr1, dx1, f1x); f1y = __ffma2_rn(fr1, dy1, f1y); f1z = __ffma2_rn(fr1, dz1, f1z);
+        f2x = __ffma2_rn(fr2, dx2, f2x); f2y = __ffma2_rn(fr2, dy2, f2y); f2z = __ffma2_rn(fr2, dz2, f2z);
+        fjx = __ffma2_rn(fr1, dx1, fjx); fjy = __ffma2_rn(fr1, dy1, fjy); fjz = __ffma2_rn(fr1, dz1, fjz);
+        fjx = __ffma2_rn(fr2, dx2, fjx); fjy = __ffma2_rn(fr2, dy2, fjy); fjz = __ffma2_rn(fr2, dz2, fjz);
+        if (k + 1 < NST) {
             fjx.x = __shfl_sync(0xffffffffu, fjx.x, src);
             fjx.y = __shfl_sync(0xffffffffu, fjx.y, src);
             fjy.x = __shfl_sync(0xffffffffu, fjy.x, src);
@@ -317,10 +328,15 @@ __device__ __forceinline__ void packed_piece(const Smem<float> &s, Vec4<float> *
             fjz.y = __shfl_sync(0xffffffffu, fjz.y, src);
         }
     }
-    if (ion) {
+    if (on1) {
         Vec4<float> f = fw[I * 32 + lane];
-        f.x -= fix.x + fix.y; f.y -= fiy.x + fiy.y; f.z -= fiz.x + fiz.y;
+        f.x -= f1x.x + f1x.y; f.y -= f1y.x + f1y.y; f.z -= f1z.x + f1z.y;
         fw[I * 32 + lane] = f;
+    }
+    if (on2) {  // l2 is a permutation of the lanes: distinct beads within this pass
+        Vec4<float> f = fw[I * 32 + l2];
+        f.x -= f2x.x + f2x.y; f.y -= f2y.x + f2y.y; f.z -= f2z.x + f2z.y;
+        fw[I * 32 + l2] = f;
     }
 #pragma unroll
     for (int o = W; o < 32; o <<= 1) {
@@ -329,104 +345,14 @@ __device__ __forceinline__ void packed_piece(const Smem<float> &s, Vec4<float> *
         fjz.x += __shfl_xor_sync(0xffffffffu, fjz.x, o); fjz.y += __shfl_xor_sync(0xffffffffu, fjz.y, o);
     }
     if (lane < W) {
-        const int ba = J * 32 + ((lr + TB + NDS - 1) & (W - 1));
+        const int tl = TB + 2 * (NST - 1);
+        const int ba = J * 32 + ((lr + tl) & (W - 1));
         Vec4<float> f = fw[ba];
         f.x += fjx.x; f.y += fjy.x; f.z += fjz.x;
         fw[ba] = f;
-        const int bb = J * 32 + ((lr + TB + NDS - 1 + D) & (W - 1));
+        const int bb = J * 32 + ((lr + tl + D) & (W - 1));
         f = fw[bb];
         f.x += fjx.y; f.y += fjy.y; f.z += fjz.y;
-        fw[bb] = f;
-    }
-}
-
-// Two width-32 packed pieces interleaved in one loop: their dependency
-// chains (shared loads, rsqrt, j-force shuffles) are independent, so the
-// pair hides each other's latency.  Each piece: i-tile I, j-tile J, first
-// step TB, 8 double steps, diagonal / exclusion flags.
-struct PieceRef {
-    int I, J, TB;
-    bool diag, near;
-};
-
-__device__ __forceinline__ void packed_pair32(const Smem<float> &s, Vec4<float> *fw, const PieceRef p0,
-                                              const PieceRef p1, int lane)
-{
-    constexpr int W = 32, D = 8, NDS = 8;
-    const PieceRef P[2] = {p0, p1};
-    float2 nx[2], ny[2], nz[2], si[2], ei[2], ci[2];
-    float2 fix[2], fiy[2], fiz[2], fjx[2], fjy[2], fjz[2];
-    const float4 *A[2], *E[2];
-    bool mask_a[2], mask_b[2];
-    const int lr = lane;
-    const int src = (lane + 1) & 31;
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const Vec4<float> pi = s.posd[P[u].I * 64 + lane];
-        const Vec2<float> qi = s.eqd[P[u].I * 64 + lane];
-        nx[u] = f2(-pi.x, -pi.x); ny[u] = f2(-pi.y, -pi.y); nz[u] = f2(-pi.z, -pi.z);
-        si[u] = f2(pi.w, pi.w); ei[u] = f2(qi.x, qi.x); ci[u] = f2(qi.y, qi.y);
-        fix[u] = f2(0.f, 0.f); fiy[u] = fix[u]; fiz[u] = fix[u]; fjx[u] = fix[u]; fjy[u] = fix[u]; fjz[u] = fix[u];
-        A[u] = s.posp + 2 * (64 * P[u].J + lr + P[u].TB);
-        E[u] = s.eqp + 64 * P[u].J + lr + P[u].TB;
-        mask_a[u] = P[u].near && P[u].TB < 3;
-        mask_b[u] = P[u].diag && lr >= (W >> 1);
-    }
-    const float2 two = f2(2.f, 2.f), mone = f2(-1.f, -1.f);
-#pragma unroll 2
-    for (int k = 0; k < NDS; ++k) {
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int t = P[u].TB + k;
-            const float4 a = A[u][2 * k], b = A[u][2 * k + 1], e = E[u][k];
-            const float2 dx = __fadd2_rn(f2(a.x, a.y), nx[u]);
-            const float2 dy = __fadd2_rn(f2(a.z, a.w), ny[u]);
-            const float2 dz = __fadd2_rn(f2(b.x, b.y), nz[u]);
-            float2 r2 = __fmul2_rn(dx, dx);
-            r2 = __ffma2_rn(dy, dy, r2);
-            r2 = __ffma2_rn(dz, dz, r2);
-            const float2 ri = f2(rsqrtf(r2.x), rsqrtf(r2.y));
-            const float2 ri2 = __fmul2_rn(ri, ri);
-            const float2 sg = __fadd2_rn(si[u], f2(b.z, b.w));
-            const float2 x2 = __fmul2_rn(__fmul2_rn(sg, sg), ri2);
-            const float2 x6 = __fmul2_rn(__fmul2_rn(x2, x2), x2);
-            const float2 ee = __fmul2_rn(ei[u], f2(e.x, e.y));
-            const float2 qq = __fmul2_rn(ci[u], f2(e.z, e.w));
-            const float2 lj = __fmul2_rn(__fmul2_rn(ee, x6), __ffma2_rn(x6, two, mone));
-            float2 fr = __fmul2_rn(__ffma2_rn(qq, ri, lj), ri2);
-            if (mask_a[u] && t < 3) {
-                const int d = P[u].I * 32 + lane - (P[u].J * 32 + ((lr + t) & (W - 1)));
-                if (d <= 2 && d >= -2) fr.x = 0.f;
-            }
-            if (mask_b[u] && k == NDS - 1) fr.y = 0.f;
-            fix[u] = __ffma2_rn(fr, dx, fix[u]);
-            fiy[u] = __ffma2_rn(fr, dy, fiy[u]);
-            fiz[u] = __ffma2_rn(fr, dz, fiz[u]);
-            fjx[u] = __ffma2_rn(fr, dx, fjx[u]);
-            fjy[u] = __ffma2_rn(fr, dy, fjy[u]);
-            fjz[u] = __ffma2_rn(fr, dz, fjz[u]);
-            if (k + 1 < NDS) {
-                fjx[u].x = __shfl_sync(0xffffffffu, fjx[u].x, src);
-                fjx[u].y = __shfl_sync(0xffffffffu, fjx[u].y, src);
-                fjy[u].x = __shfl_sync(0xffffffffu, fjy[u].x, src);
-                fjy[u].y = __shfl_sync(0xffffffffu, fjy[u].y, src);
-                fjz[u].x = __shfl_sync(0xffffffffu, fjz[u].x, src);
-                fjz[u].y = __shfl_sync(0xffffffffu, fjz[u].y, src);
-            }
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        Vec4<float> f = fw[P[u].I * 32 + lane];
-        f.x -= fix[u].x + fix[u].y; f.y -= fiy[u].x + fiy[u].y; f.z -= fiz[u].x + fiz[u].y;
-        fw[P[u].I * 32 + lane] = f;
-        const int ba = P[u].J * 32 + ((lr + P[u].TB + NDS - 1) & (W - 1));
-        f = fw[ba];
-        f.x += fjx[u].x; f.y += fjy[u].x; f.z += fjz[u].x;
-        fw[ba] = f;
-        const int bb = P[u].J * 32 + ((lr + P[u].TB + NDS - 1 + D) & (W - 1));
-        f = fw[bb];
-        f.x += fjx[u].y; f.y += fjy[u].y; f.z += fjz[u].y;
         fw[bb] = f;
     }
 }
@@ -480,19 +406,20 @@ __device__ __noinline__ void ragged_diag_piece(const Smem<float> &s, Vec4<float>
     }
 }
 
-// Piece kinds of the packed FP32 path:
-//   11: W 32, t 0..7 + 8..15   12: W 32, t 16..23 + 24..31   13: W 32 diagonal, t 1..8 + 9..16
-//   14: W 16, t 0..7 + 8..15   15: W 8,  t 0..3 + 4..7
+// Piece kinds of the packed FP32 path (quad pieces):
+//   21: W 32, t = 1, 3, 5, 7 (+8)      22: W 32, t = 17, 19, 21, 23 (+8)
+//   23: W 32 diagonal, t = 2, 4, 6, 8 (+8)
+//   24: W 16, t = 1, 3, 5, 7 (+8)       25: W 8, t = 1, 3 (+4)
 //   8, 10: diagonal of a ragged tile of width 16 / 8, scalar
 __device__ __forceinline__ void run_packed_piece(const Smem<float> &s, Vec4<float> *fw, int kind, int I, int J,
                                                  bool near, int wI, int lane)
 {
     switch (kind) {
-    case 11: packed_piece<32>(s, fw, I, J, 0, 8, false, near, wI, lane); break;
-    case 12: packed_piece<32>(s, fw, I, J, 16, 8, false, near, wI, lane); break;
-    case 13: packed_piece<32>(s, fw, I, J, 1, 8, true, near, wI, lane); break;
-    case 14: packed_piece<16>(s, fw, I, J, 0, 8, false, near, wI, lane); break;
-    case 15: packed_piece<8>(s, fw, I, J, 0, 4, false, near, wI, lane); break;
+    case 21: quad_piece<32>(s, fw, I, J, 1, 4, false, near, wI, lane); break;
+    case 22: quad_piece<32>(s, fw, I, J, 17, 4, false, near, wI, lane); break;
+    case 23: quad_piece<32>(s, fw, I, J, 2, 4, true, near, wI, lane); break;
+    case 24: quad_piece<16>(s, fw, I, J, 1, 4, false, near, wI, lane); break;
+    case 25: quad_piece<8>(s, fw, I, J, 1, 2, false, near, wI, lane); break;
     case 8: ragged_diag_piece(s, fw, J, 16, lane); break;
     case 10: ragged_diag_piece(s, fw, J, 8, lane); break;
     default: break;  // the host schedule emits only the kinds above
@@ -633,15 +560,7 @@ __device__ __forceinline__ void force_phase(const ChainArgs<R> &a, const Smem<R>
             const bool n1 = (e.w >> 8) & 1, n2 = (e.w >> 9) & 1;
             const int wI = tile_width(e.x, a.n_tiles, a.w_last);
             if constexpr (kPacked<R>) {
-                if ((e.w >> 10) & 1) {  // two width-32 pieces run interleaved
-                    const int4 g = u[++q];
-                    const int k2 = g.w & 0xff;
-                    const PieceRef p0{e.x, e.z, kind == 12 ? 16 : (kind == 13 ? 1 : 0), kind == 13, n1};
-                    const PieceRef p1{g.x, g.z, k2 == 12 ? 16 : (k2 == 13 ? 1 : 0), k2 == 13, (bool)((g.w >> 8) & 1)};
-                    packed_pair32(s, fw_mine, p0, p1, lane);
-                } else {
-                    run_packed_piece(s, fw_mine, kind, e.x, e.z, n1, wI, lane);
-                }
+                run_packed_piece(s, fw_mine, kind, e.x, e.z, n1, wI, lane);
             } else {
                 if (e.y >= 0) run_piece<R, true>(s, fw_mine, kind, e.x, e.y, e.z, n1, n2, wI, lane);
                 else run_piece<R, false>(s, fw_mine, kind, e.x, 0, e.z, n1, false, wI, lane);
@@ -651,7 +570,11 @@ __device__ __forceinline__ void force_phase(const ChainArgs<R> &a, const Smem<R>
 }
 
 template <typename R, int NW>
-__global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? 5 : 1) chain_kernel(const ChainArgs<R> a)
+__global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW == 6 ? 4 : 3)) : 1)
+    chain_kernel(const ChainArgs<R> a)
+// FP32 with 4 warps: five CTAs per SM fit (a 672-replica workload has 4.4 per
+// SM); 6 and 8 warps trade occupancy for registers (workloads with many
+// replicas per SM)
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int rep = blockIdx.x;
@@ -827,20 +750,20 @@ std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed)
     };
     std::vector<P> all;
     for (int J = 0; packed && J < g.n_tiles; ++J) {
-        // packed FP32 double steps: W 32 tiles in two pieces of 8 double steps
+        // packed FP32 quad pieces: 4 steps x 4 pairs per lane for a W 32 ring half
         const int W = J == g.n_tiles - 1 ? g.w_last : 32;
-        if (W == 32) all.push_back(P{UnitDesc{J, -1, J, 13, 1, 0}, 8 * 40.0 + 40.0});
+        if (W == 32) all.push_back(P{UnitDesc{J, -1, J, 23, 1, 0}, 4 * 75.0 + 60.0});
         else if (W == 16) all.push_back(P{UnitDesc{J, -1, J, 8, 1, 0}, 8 * 30.0 + 20.0});
         else all.push_back(P{UnitDesc{J, -1, J, 10, 1, 0}, 4 * 30.0 + 20.0});
         for (int I = 0; I < J; ++I) {
             const int nr = J - I == 1 ? 1 : 0;
             if (W == 32) {
-                all.push_back(P{UnitDesc{I, -1, J, 11, nr, 0}, 8 * 40.0 + 40.0});
-                all.push_back(P{UnitDesc{I, -1, J, 12, nr, 0}, 8 * 40.0 + 40.0});
+                all.push_back(P{UnitDesc{I, -1, J, 21, nr, 0}, 4 * 75.0 + 60.0});
+                all.push_back(P{UnitDesc{I, -1, J, 22, nr, 0}, 4 * 75.0 + 60.0});
             } else if (W == 16) {
-                all.push_back(P{UnitDesc{I, -1, J, 14, nr, 0}, 8 * 40.0 + 50.0});
+                all.push_back(P{UnitDesc{I, -1, J, 24, nr, 0}, 4 * 75.0 + 70.0});
             } else {
-                all.push_back(P{UnitDesc{I, -1, J, 15, nr, 0}, 4 * 40.0 + 60.0});
+                all.push_back(P{UnitDesc{I, -1, J, 25, nr, 0}, 2 * 75.0 + 80.0});
             }
         }
     }
@@ -866,19 +789,7 @@ std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed)
             }
         }
     }
-    // jobs: packed width-32 pieces go in interleaved pairs (kinds 11..13)
-    std::vector<std::vector<P>> jobs;
-    {
-        std::vector<P> w32, rest;
-        for (const P &p : all) (packed && p.u.kind >= 11 && p.u.kind <= 13 ? w32 : rest).push_back(p);
-        for (size_t i = 0; i + 1 < w32.size(); i += 2) jobs.push_back({w32[i], w32[i + 1]});
-        if (w32.size() % 2) jobs.push_back({w32.back()});
-        for (const P &p : rest) jobs.push_back({p});
-    }
-    // an interleaved pair costs a little less than its two pieces one after the other
-    auto job_cost = [](const std::vector<P> &j) { return j.size() == 2 ? 0.9 * (j[0].cost + j[1].cost) : j[0].cost; };
-    std::stable_sort(jobs.begin(), jobs.end(),
-                     [&](const std::vector<P> &x, const std::vector<P> &y) { return job_cost(x) > job_cost(y); });
+    std::stable_sort(all.begin(), all.end(), [](const P &x, const P &y) { return x.cost > y.cost; });
     std::vector<std::vector<UnitDesc>> per(NW);
     std::vector<double> load(NW, 0.0);
     const int nt = NW * 32;
@@ -892,19 +803,12 @@ std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed)
             if ((w + 1) * 32 > lo) load[w] += 250.0;
         }
     }
-    for (const auto &j : jobs) {
+    for (const P &p : all) {
         int best = 0;
         for (int w = 1; w < NW; ++w)
             if (load[w] < load[best]) best = w;
-        if (j.size() == 2) {
-            UnitDesc a = j[0].u;
-            a.pair_next = 1;
-            per[best].push_back(a);
-            per[best].push_back(j[1].u);
-        } else {
-            per[best].push_back(j[0].u);
-        }
-        load[best] += job_cost(j);
+        per[best].push_back(p.u);
+        load[best] += p.cost;
     }
     return per;
 }
@@ -997,10 +901,24 @@ cudaError_t ChainModel::init(const ChainHost &h, int precision)
     p->host = h;
     p->geo = chain_geometry(h.N);
     p->precision = precision;
-    p->NW = 4;
     cudaError_t e = precision == 1 ? upload_chain<double>(h, p->geo, p->dd) : upload_chain<float>(h, p->geo, p->df);
     if (e != cudaSuccess) return e;
-    const auto sched = chain_schedule(h.N, p->NW, precision != 1);
+    return set_warps(4);
+}
+
+int ChainModel::warps() const { return p->NW; }
+
+cudaError_t ChainModel::set_warps(int NW)
+{
+    if (NW != 4 && NW != 6 && NW != 8) return cudaErrorInvalidValue;
+    if (p->precision == 1 && NW != 4) return cudaErrorInvalidValue;
+    p->NW = NW;
+    cudaFree(p->units);
+    cudaFree(p->unit_count);
+    p->units = nullptr;
+    p->unit_count = nullptr;
+    cudaError_t e;
+    const auto sched = chain_schedule(p->host.N, p->NW, p->precision != 1);
     int mx = 1;
     for (const auto &v : sched) mx = std::max<int>(mx, (int)v.size());
     std::vector<int4> flat((size_t)p->NW * mx, int4{0, 0, 0, 0});
@@ -1010,7 +928,7 @@ cudaError_t ChainModel::init(const ChainHost &h, int precision)
         for (size_t q = 0; q < sched[w].size(); ++q) {
             const UnitDesc &u = sched[w][q];
             flat[(size_t)w * mx + q] =
-                int4{u.I1, u.I2, u.J, u.kind | (u.near1 << 8) | (u.near2 << 9) | (u.pair_next << 10)};
+                int4{u.I1, u.I2, u.J, u.kind | (u.near1 << 8) | (u.near2 << 9)};
         }
     }
     p->max_units = mx;
@@ -1090,6 +1008,8 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
 cudaError_t ChainModel::launch(const RunLaunch &L, cudaStream_t st)
 {
     if (p->precision == 1) return launch_typed<double, 4>(p, p->dd, L, st);
+    if (p->NW == 6) return launch_typed<float, 6>(p, p->df, L, st);
+    if (p->NW == 8) return launch_typed<float, 8>(p, p->df, L, st);
     return launch_typed<float, 4>(p, p->df, L, st);
 }
 

@@ -27,11 +27,10 @@ struct ChainGeometry {
 // near1 / near2: that i-tile neighbours J, so exclusions |i - j| <= 2 occur.
 struct UnitDesc {
     int I1, I2, J, kind, near1, near2;
-    int pair_next = 0;  // packed width-32 piece run interleaved with the next record
 };
 
 ChainGeometry chain_geometry(int N);
-// packed: the FP32 f32x2 pieces (kinds 8, 10..15); else the scalar pieces (0..10)
+// packed: the FP32 quad pieces (kinds 8, 10, 21..25); else the scalar pieces (0..10)
 std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed);
 
 // Everything one launch of a simulation kernel needs about the run.
@@ -62,6 +61,8 @@ public:
     int precision() const;
     size_t state_bytes_per_replica() const;
     size_t smem_bytes() const;
+    int warps() const;
+    cudaError_t set_warps(int NW);  // 4, 6 or 8 warps per replica (FP64: 4)
 
 private:
     Impl *p;

@@ -112,6 +112,8 @@ def _load():
     L.pmf_overlap.argtypes = [_D, _D, C.c_int, _D]
     L.pmf_run_adaptive.argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.POINTER(AdaptiveParams),
                                    C.POINTER(AdaptiveInfo), C.POINTER(FreeEnergyResult)]
+    L.pmf_chain_set_warps.argtypes = [P, C.c_int, C.c_int]
+    L.pmf_chain_autotune.argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.c_int, C.POINTER(C.c_int), _D]
     L.pmf_set_stream.argtypes = [C.c_void_p]
     L.pmf_last_error.restype = C.c_char_p
     L.pmf_version.restype = C.c_char_p
@@ -120,7 +122,7 @@ def _load():
                  "pmf_free_energy", "pmf_free_energy_from_samples", "pmf_final_state", "pmf_philox",
                  "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_free_energy_noalloc",
                  "pmf_mlp_create", "pmf_mlp_get_params", "pmf_mlp_predict", "pmf_mlp_gradient", "pmf_mlp_train",
-                 "pmf_overlap", "pmf_run_adaptive", "pmf_set_stream"):
+                 "pmf_overlap", "pmf_run_adaptive", "pmf_chain_set_warps", "pmf_chain_autotune", "pmf_set_stream"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -342,14 +344,14 @@ def pmf_chain_forces(system: System, chain, pos, lam, k):
 
 
 def pmf_chain_schedule(N, NW=4, precision=PMF_FP32):
-    """Host schedule: int array [pieces, 8] (warp, I1, I2, J, kind, near1, near2, pair_next), padded N."""
+    """Host schedule: int array [pieces, 7] (warp, I1, I2, J, kind, near1, near2), padded N."""
     n = C.c_size_t()
     pad = C.c_int()
     lib.pmf_chain_schedule(N, NW, precision, None, 0, C.byref(n), C.byref(pad))
-    out = np.zeros(8 * n.value, dtype=np.int32)
+    out = np.zeros(7 * n.value, dtype=np.int32)
     _check(lib.pmf_chain_schedule(N, NW, precision, out.ctypes.data_as(C.POINTER(C.c_int)), out.size,
                                   C.byref(n), C.byref(pad)), "pmf_chain_schedule")
-    return out.reshape(-1, 8), pad.value
+    return out.reshape(-1, 7), pad.value
 
 
 def pmf_free_energy_noalloc(x_dev, lambda_dev, n_windows, replicas, samples_per_window, k, kT, out_dev):
@@ -445,3 +447,17 @@ def pmf_run_adaptive(system: System, lambda0, params, mlp_init, threshold=0.3, m
     meta = dict(n_windows=n, rounds=info.rounds, inserted=info.inserted, gpu_seconds=info.gpu_seconds,
                 mlp_loss=info.mlp_loss, lambdas=np.array(info.lambda_[:n]))
     return meta, out
+
+
+def pmf_chain_set_warps(system: System, chain, warps):
+    _check(lib.pmf_chain_set_warps(system.handle, chain, warps), "pmf_chain_set_warps")
+
+
+def pmf_chain_autotune(system: System, lambdas, params, probe_steps=400):
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    p, keep = params
+    best = C.c_int()
+    ms = C.c_double()
+    _check(lib.pmf_chain_autotune(system.handle, _dp(lam), lam.size, C.byref(p), probe_steps, C.byref(best),
+                                  C.byref(ms)), "pmf_chain_autotune")
+    return best.value, ms.value

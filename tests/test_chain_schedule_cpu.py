@@ -18,15 +18,17 @@ def _width(t, n_tiles, w_last):
 
 
 # kind: (ring width W, first step TB, steps NST, diagonal, packed offset D or 0)
+# kind: (ring width W, first step TB, steps NST, diagonal, quad offset D or 0)
+# scalar kinds step t by 1; quad kinds step t by 2 with two i-beads per lane
 KINDS = {0: (32, 0, 8, 0, 0), 1: (32, 8, 8, 0, 0), 2: (32, 16, 8, 0, 0), 3: (32, 24, 8, 0, 0),
          4: (32, 1, 8, 1, 0), 5: (32, 9, 8, 1, 0), 6: (16, 0, 8, 0, 0), 7: (16, 8, 8, 0, 0),
          8: (16, 1, 8, 1, 0), 9: (8, 0, 8, 0, 0), 10: (8, 1, 4, 1, 0),
-         11: (32, 0, 8, 0, 8), 12: (32, 16, 8, 0, 8), 13: (32, 1, 8, 1, 8), 14: (16, 0, 8, 0, 8),
-         15: (8, 0, 4, 0, 4)}
+         21: (32, 1, 4, 0, 8), 22: (32, 17, 4, 0, 8), 23: (32, 2, 4, 1, 8), 24: (16, 1, 4, 0, 8),
+         25: (8, 1, 2, 0, 4)}
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("NW", [4, 8])
+@pytest.mark.parametrize("NW", [4, 6, 8])
 @pytest.mark.parametrize("N", NS)
 def test_ring_pieces_cover_pairs_once(N, NW, precision):
     from paper_1105_4840_gb300 import pmf
@@ -37,16 +39,12 @@ def test_ring_pieces_cover_pairs_once(N, NW, precision):
     w_last = 32 if rem == 0 else (8 if rem <= 8 else (16 if rem <= 16 else 32))
     assert Np == (n_tiles - 1) * 32 + w_last
     count = np.zeros((Np, Np), dtype=np.int64)
-    for q, (w, I1, I2, J, kind, near1, near2, pair_next) in enumerate(units):
+    for (w, I1, I2, J, kind, near1, near2) in units:
         assert 0 <= w < NW and 0 <= I1 <= J < n_tiles and kind in KINDS
-        if pair_next:  # interleaved with the next record of the same warp: both width-32 packed
-            assert precision == 0 and 11 <= kind <= 13
-            assert units[q + 1][0] == w and 11 <= units[q + 1][4] <= 13 and units[q + 1][7] == 0
-            assert q == 0 or units[q - 1][7] == 0
         W, TB, NST, DIAG, DP = KINDS[kind]
-        assert (kind >= 11 or kind in (8, 10)) if precision == 0 else kind <= 10
+        assert (kind >= 21 or kind in (8, 10)) if precision == 0 else kind <= 10
         if DP:
-            _packed_piece(count, N, Np, n_tiles, w_last, I1, J, near1, W, TB, NST, DIAG, DP)
+            _quad_piece(count, N, Np, n_tiles, w_last, I1, J, near1, W, TB, NST, DIAG, DP)
             continue
         assert W == _width(J, n_tiles, w_last)
         assert bool(DIAG) == (I1 == J)
@@ -92,38 +90,43 @@ def test_ring_pieces_cover_pairs_once(N, NW, precision):
     np.testing.assert_array_equal(count, want)
 
 
-def _packed_piece(count, N, Np, n_tiles, w_last, I, J, near, W, TB, NDS, DIAG, D):
-    """Replay of packed_piece: double step k evaluates ring steps t = TB + k
-    (stream a) and t + D (stream b); both j-force streams rotate by one lane."""
+def _quad_piece(count, N, Np, n_tiles, w_last, I, J, near, W, TB, NST, DIAG, D):
+    """Replay of quad_piece: lane l holds i1 at ring index l and i2 at l + 1;
+    step k (t = TB + 2k) pairs both with ring positions l + t (stream a) and
+    l + t + D (stream b); both j-force streams rotate by two lanes."""
     assert D == (8 if W == 32 else W // 2)
     lanes = np.arange(32)
     lr = lanes & (W - 1)
-    src = (lanes & ~(W - 1)) | ((lr + 1) & (W - 1))
+    l2 = (lanes & ~(W - 1)) | ((lr + 1) & (W - 1))
+    assert sorted(l2) == list(range(32))  # a permutation: the i2 flush hits distinct beads
+    src = (lanes & ~(W - 1)) | ((lr + 2) & (W - 1))
     acc_a = (lr + TB) & (W - 1)
     acc_b = (lr + TB + D) & (W - 1)
     wI = _width(I, n_tiles, w_last)
-    i = I * 32 + lanes
-    ion = lanes < wI
-    for k in range(NDS):
-        t = TB + k
+    gi1, gi2 = I * 32 + lanes, I * 32 + l2
+    on1, on2 = lanes < wI, l2 < wI
+    for k in range(NST):
+        t = TB + 2 * k
         assert (lr + t).max() < 2 * W  # packed entry index p = lr + t
         for stream, tt, acc in (("a", t, acc_a), ("b", t + D, acc_b)):
             assert np.all(acc == ((lr + tt) & (W - 1)))
             j = J * 32 + ((lr + tt) & (W - 1))
-            masked = np.zeros(32, dtype=bool)
-            if stream == "a" and t < 3 and near:
-                masked |= np.abs(i - j) <= 2
-            if stream == "b" and DIAG and 2 * tt == W:
-                masked |= lr >= W // 2
-            ok = ion & ~masked & (i < N) & (j < N)
-            assert np.all(i[ok] != j[ok])
-            assert np.all(np.abs(i[ok] - j[ok]) >= 3)
-            for a, b in zip(i[ok], j[ok]):
-                count[min(a, b), max(a, b)] += 1
-        if k + 1 < NDS:
+            for gi, on, first in ((gi1, on1, True), (gi2, on2, False)):
+                masked = np.zeros(32, dtype=bool)
+                if stream == "a" and near and TB < 4 and t < 4:
+                    masked |= np.abs(gi - j) <= 2
+                if stream == "b" and first and DIAG and k == NST - 1:
+                    masked |= lr >= W // 2
+                ok = on & ~masked & (gi < N) & (j < N)
+                assert np.all(gi[ok] != j[ok])
+                assert np.all(np.abs(gi[ok] - j[ok]) >= 3)
+                for a, b in zip(gi[ok], j[ok]):
+                    count[min(a, b), max(a, b)] += 1
+        if k + 1 < NST:
             acc_a, acc_b = acc_a[src], acc_b[src]
-    fa = (lr + TB + NDS - 1) & (W - 1)
-    fb = (lr + TB + NDS - 1 + D) & (W - 1)
+    tl = TB + 2 * (NST - 1)
+    fa = (lr + tl) & (W - 1)
+    fb = (lr + tl + D) & (W - 1)
     assert np.all(acc_a == fa) and np.all(acc_b == fb)
     for g in range(32 // W):
         assert np.all(acc_a[g * W:(g + 1) * W] == acc_a[:W])
@@ -138,6 +141,6 @@ def test_schedule_is_balanced():
     for precision in (0, 1):
         units, _ = pmf.pmf_chain_schedule(104, 4, precision)
         load = np.zeros(4)
-        for (w, I1, I2, J, kind, n1, n2, pn) in units:
+        for (w, I1, I2, J, kind, n1, n2) in units:
             load[w] += KINDS[kind][2] * (2 if (I2 >= 0 or KINDS[kind][4]) else 1)
         assert load.max() <= 1.5 * load.mean()

@@ -1,0 +1,94 @@
+"""GPU tests of the learned window placement: the overlap kernel against the
+oracle's closed form, seeded runs against oracle runs from the same starts,
+and the adaptive protocol on the 1D model against quadrature."""
+import numpy as np
+import pytest
+
+from oracle import _clib, quadrature as quad, surrogate as sg
+from paper_1105_4840_gb300 import inputs
+from tests.helpers import f32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pmf():
+    from paper_1105_4840_gb300 import pmf as m
+    return m
+
+
+def test_overlap_kernel_matches_oracle(pmf):
+    rng = np.random.default_rng(3)
+    mu = np.cumsum(rng.uniform(0.0, 0.3, 200))
+    sd = rng.uniform(0.03, 0.2, 200)
+    sd[50] = sd[51]  # equal widths: the closed form's special case
+    got = pmf.pmf_overlap(mu, np.log(sd ** 2))
+    want = np.array([sg.gaussian_overlap(mu[i], sd[i], mu[i + 1], sd[i + 1]) for i in range(199)])
+    np.testing.assert_allclose(got, want, atol=1e-12, rtol=0)
+
+
+def test_seeded_chain_run_matches_oracle(pmf):
+    """Every replica from its own start state: 200 steps vs the oracle."""
+    n = 40
+    p = inputs.chain_params(n, 21)
+    starts = [f32(inputs.chain_start(p, 50 + q)) for q in range(4)]
+    run = inputs.RunSettings(k=500.0, kT=inputs.kT_of(300.0), dt=0.001, gamma=5.0, n_steps=200, n_equil=100,
+                             stride=100, replicas=2, seed=4)
+    lam = np.array([1.1, 1.3])
+    sysh = pmf.pmf_create_system_chain([p], [starts[0]])
+    rr = pmf.pmf_run_prepare_seeded(sysh, lam, pmf.make_params(run), np.stack(starts))
+    rr.launch()
+    rr.wait()
+    pos, _ = rr.final_state()
+    pos = pos.reshape(2, 2, n, 3)
+    ch = _clib.Chain(p)
+    for w in range(2):
+        for r in range(2):
+            _, ro, _ = ch.run(starts[2 * w + r], lam[w], run.k, run.kT, run.dt, run.gamma, 200, 100, 100, 4,
+                              2 * w + r)
+            assert np.abs(pos[w, r] - ro).max() <= 1e-4
+
+
+def test_seeded_1d_run_matches_oracle(pmf):
+    w = inputs.od1d_workload()
+    run = w["run"]
+    run.n_steps, run.n_equil, run.replicas = 4000, 400, 3
+    lam = np.array([-0.5, 0.2])
+    starts = np.array([-1.0, -0.3, 0.4, 0.9, 1.2, -1.3])
+    sysh = pmf.pmf_create_system_1d(w["a"], w["x0"])
+    rr = pmf.pmf_run_prepare_seeded(sysh, lam, pmf.make_params(run), starts)
+    rr.launch()
+    rr.wait()
+    xs = rr.x_samples()
+    for wi in range(2):
+        for r in range(3):
+            x, _ = _clib.od1d_run(w["a"], lam[wi], run.k, run.kT, run.gamma, run.dt, run.n_steps, run.n_equil,
+                                  run.stride, run.seed, 3 * wi + r, starts[3 * wi + r])
+            np.testing.assert_allclose(xs[wi][r], x, atol=2e-6, rtol=0)
+
+
+def test_adaptive_protocol_on_double_well(pmf):
+    """From 6 coarse windows (spacing 0.6, about 3 standard deviations of x;
+    overlaps 0.1 - 0.36) the surrogate inserts windows until neighbours
+    overlap by at least 0.5; the resulting JE profile matches the quadrature
+    at every final window."""
+    w = inputs.od1d_workload()
+    run = w["run"]
+    lam0 = np.linspace(-1.5, 1.5, 6)
+    sysh = pmf.pmf_create_system_1d(w["a"], w["x0"])
+    init = pmf.pack_mlp_params(sg.init_params(2))
+    meta, res = pmf.pmf_run_adaptive(sysh, lam0, pmf.make_params(run), init, threshold=0.5, max_rounds=4,
+                                     max_windows=64, mlp_steps=400, mlp_batch=512, mlp_lr=3e-3, mlp_seed=5)
+    assert meta["inserted"] > 0 and meta["n_windows"] == 6 + meta["inserted"]
+    lam = meta["lambdas"]
+    assert np.all(np.diff(lam) > 0)
+    np.testing.assert_allclose(res["lambda"], lam)
+    exact = np.array([quad.od1d_free_energy(l, run.k) for l in lam])
+    exact -= exact[0]
+    assert np.max(np.abs(res["dF_JE"] - exact)) < 0.1
+    # neighbours now overlap (measured from the samples' own moments)
+    sd = np.sqrt(res["var_x"])
+    ovl = np.array([sg.gaussian_overlap(res["mean_x"][i], sd[i], res["mean_x"][i + 1], sd[i + 1])
+                    for i in range(lam.size - 1)])
+    assert np.median(ovl) > 0.4
+    assert meta["gpu_seconds"] > 0

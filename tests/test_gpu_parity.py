@@ -243,3 +243,33 @@ def test_repeat_launch_is_bit_identical(pmf):
     b = rr.x_samples()
     for u, v in zip(a, b):
         np.testing.assert_array_equal(u, v)
+
+
+@pytest.mark.parametrize("warps", [4, 6, 8])
+@pytest.mark.parametrize("n", [13, 40, 104, 110, 333])
+def test_forces_other_warp_counts(pmf, n, warps):
+    """Same thermal-like states as test_forces_match_oracle (bonds off their
+    rest length by ~0.005 nm): at exact rest lengths the FP32 rounding of a
+    0.15 nm bond vector (~1.5e-8 nm) times k_b = 2.5e5 leaves an absolute
+    floor of ~4e-3 kJ/mol/nm per bond that a norm-wise 1e-5 criterion on
+    near-zero total forces cannot absorb."""
+    p = inputs.chain_params(n, 300 + n)
+    r = f32(inputs.chain_start(p, 17 + n) + np.random.default_rng(n + 1).normal(0, 0.005, (n, 3)))
+    sysh = pmf.pmf_create_system_chain([p], [r])
+    pmf.pmf_chain_set_warps(sysh, 0, warps)
+    fg = pmf.pmf_chain_forces(sysh, 0, r, 2.0, 400.0)
+    fo = _clib.Chain(p).forces(r, 2.0, 400.0)
+    assert np.linalg.norm(fg - fo) / np.linalg.norm(fo) <= 1e-5
+
+
+def test_autotune_picks_a_valid_count_and_runs(pmf):
+    p = inputs.chain_params(104, 1)
+    start = inputs.chain_start(p, 1001, target_x=1.3)
+    run = inputs.RunSettings(k=500.0, kT=inputs.kT_of(300.0), dt=0.001, gamma=5.0, n_steps=600, n_equil=100,
+                             stride=50, replicas=4, seed=0)
+    lam = inputs.lambda_grid(1.3, 1.6, 4)
+    sysh = pmf.pmf_create_system_chain([p], [f32(start)])
+    best, ms = pmf.pmf_chain_autotune(sysh, lam, pmf.make_params(run), probe_steps=200)
+    assert best in (4, 6, 8) and ms > 0
+    rr = pmf.pmf_run_windows(sysh, lam, pmf.make_params(run))
+    assert np.all(np.isfinite(rr.free_energy()["dF_JE"]))

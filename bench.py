@@ -171,6 +171,76 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def bench_batch(args, pmf, torch, stream):
+    """Many uneven paths at once: 64 chains (40-400 beads), 21-61 windows
+    each, 16 replicas, one CUDA graph of concurrent per-chain launches, then
+    the per-chain FP64 reductions.  Single GPU, rank 0 only."""
+    from paper_1105_4840_gb300 import inputs
+
+    bw = inputs.batch_workload(n_steps=args.md_steps)
+    run, params, lams = bw["run"], bw["params"], bw["lambdas"]
+    sysh = pmf.pmf_create_system_chain(params, bw["starts"])
+    rr = pmf.pmf_run_batch_prepare(sysh, list(enumerate(lams)), pmf.make_params(run))
+    R = run.replicas
+    replica_steps = sum(l.size for l in lams) * R * run.n_steps
+    flops = sum(flops_per_replica_step(p.n) * l.size * R * run.n_steps for p, l in zip(params, lams))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def reduce_all():
+        for m, l in enumerate(lams):
+            rr.free_energy_item(m, l.size)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        rr.launch()
+        rr.wait()
+    reduce_all()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.5)
+    sim_ms, red_ms = [], []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        rr.launch()
+        e[1].record(stream)
+        rr.wait()
+        reduce_all()  # synchronous per item: the host loop waits on each copy-out
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        sim_ms.append(e[0].elapsed_time(e[1]))
+        red_ms.append(e[1].elapsed_time(e[2]))
+    clocks.stop()
+    rr.wait()
+    t_step = statistics.mean(a + b for a, b in zip(sim_ms, red_ms))
+    clk = clocks.summary()
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_max = float(_peaks().get("sm_max_mhz", 2070.0))
+    peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
+    sim = statistics.mean(sim_ms)
+    achieved = flops / (sim / 1000.0) / 1e12
+    chunks = sum(math.ceil(run.n_steps / 100000) for _ in lams)
+    n = [p.n for p in params]
+    line = {"metric": "replica-steps/s", "value": replica_steps / (t_step / 1000.0), "unit": "replica-steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batch64_uneven", "chains": len(params), "beads_min": min(n),
+                       "beads_max": max(n), "beads_total": sum(n), "windows_total": sum(l.size for l in lams),
+                       "replicas_per_window": R, "md_steps_per_window": run.n_steps,
+                       "launch": "one CUDA graph, one branch per chain", "l2": "256 MB flush between timed steps"},
+            "gpu_launches": args.steps * (chunks + 3 * len(lams)),
+            "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+                       "reasons": clk.get("reasons")},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "chain_kernel<float,4> (64 launches)",
+                         "launch_ms": sim},
+            "simulation_ms": sim, "reduction_ms": statistics.mean(red_ms)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -179,6 +249,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--md-steps", type=int, default=400000, help="BAOAB steps per window (workload: 4e5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="chain104", choices=["chain104", "batch64"],
+                    help="chain104: the 104-bead PPP (default); batch64: 64 uneven chains in one graph")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -206,6 +278,10 @@ def main():
 
     stream = torch.cuda.current_stream()
     pmf.pmf_set_stream(stream.cuda_stream)
+    if args.workload == "batch64":
+        if world == 1:
+            bench_batch(args, pmf, torch, stream)
+        return
     w = _workload(args.md_steps)
     p, start, run = w["params"], w["start"], w["run"]
     s, R = run.lambdas.size, run.replicas

@@ -148,14 +148,36 @@ pmf_status pmf_run_prepare_seeded(pmf_system *sys, const double *lambda, int n_w
 pmf_status pmf_run_wait(pmf_run *run);
 void pmf_destroy_run(pmf_run *run);
 
+/* Batched runs.  One pmf_batch_item is one independent PPP path (Sec. III
+ * (ii)): windows lambda[n_windows] (strictly monotone) on chain `chain` of
+ * the system (ignored for the 1D model).  pmf_run_batch_prepare lays the
+ * items' windows end to end (item m's windows follow item m-1's; at most
+ * PMF_MAX_RUN_WINDOWS in all) and shares p (p->chain is ignored; per-window
+ * step counts, if given, cover the concatenated windows).  Replica uids
+ * continue across items (uid_base + global window * replicas + r), so each
+ * replica of the batch draws its own noise stream.  pmf_run_launch then
+ * enqueues the whole batch: the launch sequence (one chain-kernel launch per
+ * item per 1e5-step chunk) is captured once into a CUDA graph and replayed
+ * by every later launch.  Samples and final states follow the concatenated
+ * window order.  The paper runs one path at a time; batching many paths is
+ * this library's addition.  Free energies per item: pmf_free_energy_item. */
+typedef struct {
+    int chain;                  /* chain index of the system                     */
+    int n_windows;              /* >= 1                                          */
+    const double *lambda;       /* host, [n_windows], copied                     */
+} pmf_batch_item;
+#define PMF_MAX_RUN_WINDOWS 4096
+pmf_status pmf_run_batch_prepare(pmf_system *sys, const pmf_batch_item *items, int n_items,
+                                 const pmf_run_params *p, pmf_run **out);
+
 /* Shape of a run's sample store: x[w][r][t], t fastest; window w holds
  * replicas * samples_per_window[w] floats starting at sample_offset[w]. */
 typedef struct {
     int n_windows;
     int replicas;
     int64_t total_samples;
-    int64_t samples_per_window[1024];
-    int64_t sample_offset[1024];
+    int64_t samples_per_window[PMF_MAX_RUN_WINDOWS];
+    int64_t sample_offset[PMF_MAX_RUN_WINDOWS];
 } pmf_run_info;
 pmf_status pmf_get_run_info(const pmf_run *run, pmf_run_info *info);
 
@@ -201,6 +223,11 @@ typedef struct {
 } pmf_free_energy_result;
 
 pmf_status pmf_free_energy(const pmf_run *run, pmf_free_energy_result *res);
+
+/* The estimates above for item `item` of a batched run (its own windows
+ * only, profile value 0 at its first window); res->capacity >= the item's
+ * n_windows >= 2.  Works on single-item runs too (item 0).  Synchronous. */
+pmf_status pmf_free_energy_item(const pmf_run *run, int item, pmf_free_energy_result *res);
 
 /* Enqueue the FP64 reductions behind pmf_free_energy on the library stream
  * and return at once; the results stay in device memory until the next

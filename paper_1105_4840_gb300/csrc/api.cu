@@ -57,8 +57,21 @@ struct pmf_system {
     Od1dParams od;
 };
 
+// One chain path of a run: windows [w0, w0 + nw) of the run use chain
+// `chain`; their replica states start at byte state_off of d_state.
+struct RunItem {
+    int chain = 0, w0 = 0, nw = 0;
+    size_t state_off = 0, state_stride = 0;
+};
+
 struct pmf_run {
     pmf_system *sys = nullptr;
+    std::vector<RunItem> items;
+    cudaStream_t cap = nullptr;        // private stream for graph capture
+    std::vector<cudaStream_t> branch;  // capture-time fork streams (batch runs)
+    std::vector<cudaEvent_t> fork_ev;  // [0]: fork point, [1 + b]: join of branch b
+    cudaGraphExec_t graph = nullptr;   // captured launch sequence
+    std::vector<unsigned> graph_gen;   // schedule generation per item at capture time
     int chain = 0, n_windows = 0, replicas = 0, stride = 1;
     double k = 0, kT = 1, dt = 0, gamma = 1, timeout_s = 0;
     unsigned long long seed = 0;
@@ -92,6 +105,10 @@ struct pmf_run {
         cudaFree(d_res);
         cudaFree(d_start);
         if (done) cudaEventDestroy(done);
+        if (graph) cudaGraphExecDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+        for (cudaStream_t b : branch) cudaStreamDestroy(b);
+        for (cudaEvent_t e : fork_ev) cudaEventDestroy(e);
     }
 };
 
@@ -184,28 +201,36 @@ pmf_status pmf_create_system(const pmf_system_desc *d, pmf_system **out)
 
 void pmf_destroy_system(pmf_system *sys) { delete sys; }
 
-pmf_status pmf_run_prepare(pmf_system *sys, const double *lambda, int n_windows, const pmf_run_params *p,
-                           pmf_run **out)
+static pmf_status prepare_items(pmf_system *sys, const pmf_batch_item *items, int n_items, const pmf_run_params *p,
+                                pmf_run **out)
 {
-    if (!sys || !lambda || !p || !out) return fail(PMF_EINVAL, "pmf_run_prepare: null argument");
+    if (!sys || !items || !p || !out || n_items < 1) return fail(PMF_EINVAL, "pmf_run_prepare: null argument");
     *out = nullptr;
-    if (n_windows < 1 || n_windows > 1024) return fail(PMF_EINVAL, "n_windows must be in [1, 1024]");
-    const double sgn = (n_windows > 1 && lambda[1] < lambda[0]) ? -1.0 : 1.0;
-    for (int i = 0; i < n_windows; ++i) {
-        if (!std::isfinite(lambda[i])) return fail(PMF_EINVAL, "lambda must be finite");
-        if (i > 0 && !((lambda[i] - lambda[i - 1]) * sgn > 0)) return fail(PMF_EINVAL, "lambda must be strictly monotone");
+    long long total_w = 0;
+    for (int it = 0; it < n_items; ++it) {
+        const pmf_batch_item &I = items[it];
+        if (!I.lambda || I.n_windows < 1) return fail(PMF_EINVAL, "each item needs lambda and n_windows >= 1");
+        if (sys->model == PMF_MODEL_CHAIN && (I.chain < 0 || I.chain >= (int)sys->chains.size()))
+            return fail(PMF_EINVAL, "chain index out of range");
+        const double sgn = (I.n_windows > 1 && I.lambda[1] < I.lambda[0]) ? -1.0 : 1.0;
+        for (int i = 0; i < I.n_windows; ++i) {
+            if (!std::isfinite(I.lambda[i])) return fail(PMF_EINVAL, "lambda must be finite");
+            if (i > 0 && !((I.lambda[i] - I.lambda[i - 1]) * sgn > 0))
+                return fail(PMF_EINVAL, "lambda must be strictly monotone");
+        }
+        total_w += I.n_windows;
     }
+    if (total_w > kMaxRunWindows) return fail(PMF_EINVAL, "a run holds at most 4096 windows");
+    const int n_windows = (int)total_w;
     if (!(p->k > 0) || !(p->kT > 0) || !(p->dt > 0) || !(p->gamma >= 0) || !std::isfinite(p->k))
         return fail(PMF_EINVAL, "need k > 0, kT > 0, dt > 0, gamma >= 0");
     if (sys->model == PMF_MODEL_1D_DOUBLEWELL && !(p->gamma > 0)) return fail(PMF_EINVAL, "1D model needs gamma > 0");
     if (p->replicas < 1 || p->sample_stride < 1) return fail(PMF_EINVAL, "replicas >= 1 and sample_stride >= 1");
     if (p->replicas > 65535 || (long long)n_windows * p->replicas > (1LL << 31) - 1)
         return fail(PMF_EINVAL, "too many replicas (at most 65535 per window)");
-    if (sys->model == PMF_MODEL_CHAIN && (p->chain < 0 || p->chain >= (int)sys->chains.size()))
-        return fail(PMF_EINVAL, "chain index out of range");
     auto run = std::make_unique<pmf_run>();
     run->sys = sys;
-    run->chain = p->chain;
+    run->chain = items[0].chain;
     run->n_windows = n_windows;
     run->replicas = p->replicas;
     run->stride = p->sample_stride;
@@ -216,7 +241,20 @@ pmf_status pmf_run_prepare(pmf_system *sys, const double *lambda, int n_windows,
     run->timeout_s = p->timeout_s;
     run->seed = p->seed;
     run->uid_base = p->uid_base;
-    run->lambda.assign(lambda, lambda + n_windows);
+    size_t state_off = 0;
+    int w0 = 0;
+    for (int it = 0; it < n_items; ++it) {
+        RunItem ri;
+        ri.chain = sys->model == PMF_MODEL_CHAIN ? items[it].chain : 0;
+        ri.w0 = w0;
+        ri.nw = items[it].n_windows;
+        ri.state_stride = sys->model == PMF_MODEL_CHAIN ? sys->chains[ri.chain]->state_bytes_per_replica() : sizeof(double);
+        ri.state_off = state_off;
+        state_off += ri.state_stride * (size_t)ri.nw * p->replicas;
+        run->items.push_back(ri);
+        run->lambda.insert(run->lambda.end(), items[it].lambda, items[it].lambda + items[it].n_windows);
+        w0 += ri.nw;
+    }
     long long off = 0;
     for (int i = 0; i < n_windows; ++i) {
         const long long ns = p->n_steps_per_window ? p->n_steps_per_window[i] : p->n_steps;
@@ -233,9 +271,9 @@ pmf_status pmf_run_prepare(pmf_system *sys, const double *lambda, int n_windows,
         run->max_steps = std::max(run->max_steps, ns);
     }
     run->total = off;
-    const int n_rep = n_windows * p->replicas;
-    if (sys->model == PMF_MODEL_CHAIN) run->state_bytes = sys->chains[p->chain]->state_bytes_per_replica() * n_rep;
-    else run->state_bytes = sizeof(double) * n_rep;
+    run->state_bytes = state_off;
+    int max_nw = 0;
+    for (const RunItem &ri : run->items) max_nw = std::max(max_nw, ri.nw);
     CK(upload(&run->d_lambda, run->lambda.data(), n_windows), "upload lambda");
     CK(upload(&run->d_nsteps, run->nsteps.data(), n_windows), "upload steps");
     CK(upload(&run->d_nequil, run->nequil.data(), n_windows), "upload equil");
@@ -244,47 +282,149 @@ pmf_status pmf_run_prepare(pmf_system *sys, const double *lambda, int n_windows,
     CK(cudaMalloc(&run->d_x, sizeof(float) * run->total), "alloc samples");
     CK(cudaMalloc(&run->d_state, run->state_bytes), "alloc state");
     CK(cudaMalloc(&run->d_err, sizeof(int)), "alloc flag");
-    CK(cudaMalloc(&run->d_scratch, reduce_scratch_bytes(n_windows, p->replicas)), "alloc scratch");
-    CK(cudaMalloc(&run->d_res, sizeof(double) * kResFields * n_windows), "alloc results");
+    CK(cudaMalloc(&run->d_scratch, reduce_scratch_bytes(max_nw, p->replicas)), "alloc scratch");
+    CK(cudaMalloc(&run->d_res, sizeof(double) * kResFields * max_nw), "alloc results");
     CK(cudaEventCreateWithFlags(&run->done, cudaEventDisableTiming), "event");
+    CK(cudaStreamCreateWithFlags(&run->cap, cudaStreamNonBlocking), "capture stream");
+    const int n_branch = std::min(n_items, kMaxBranches);
+    if (n_branch > 1) {
+        run->fork_ev.assign(1 + n_branch, nullptr);
+        run->branch.assign(n_branch, nullptr);
+        for (auto &e : run->fork_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "fork event");
+        for (auto &b : run->branch) CK(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking), "branch stream");
+    }
     *out = run.release();
     return PMF_OK;
 }
 
-pmf_status pmf_run_launch(pmf_run *run)
+pmf_status pmf_run_prepare(pmf_system *sys, const double *lambda, int n_windows, const pmf_run_params *p,
+                           pmf_run **out)
 {
-    if (!run) return fail(PMF_EINVAL, "pmf_run_launch: null run");
-    CK(cudaMemsetAsync(run->d_err, 0, sizeof(int), g_stream), "clear flag");
+    if (!p) return fail(PMF_EINVAL, "pmf_run_prepare: null params");
+    if (n_windows < 1 || n_windows > 1024) return fail(PMF_EINVAL, "n_windows must be in [1, 1024]");
+    pmf_batch_item it{p->chain, n_windows, lambda};
+    return prepare_items(sys, &it, 1, p, out);
+}
+
+pmf_status pmf_run_batch_prepare(pmf_system *sys, const pmf_batch_item *items, int n_items, const pmf_run_params *p,
+                                 pmf_run **out)
+{
+    return prepare_items(sys, items, n_items, p, out);
+}
+
+// Modelled cost of one replica of an item: pair interactions x steps.
+static double item_cost(const pmf_run *run, const RunItem &ri)
+{
+    const double N = run->sys->model == PMF_MODEL_CHAIN ? run->sys->chains[ri.chain]->n_beads() : 1.0;
+    long long steps = 0;
+    for (int w = ri.w0; w < ri.w0 + ri.nw; ++w) steps = std::max(steps, run->nsteps[w]);
+    return (N * N * 0.5 + 40.0 * N) * (double)steps;
+}
+
+// Enqueue every launch of one item on stream st: one launch per 1e5-step
+// chunk (chain model) over the item's nw x replicas CTAs; state carries over
+// between chunks in device memory.
+static cudaError_t enqueue_item(pmf_run *run, const RunItem &ri, cudaStream_t st)
+{
     RunLaunch L;
-    L.state = run->d_state;
+    L.state = static_cast<char *>(run->d_state) + ri.state_off;
     L.xout = run->d_x;
-    L.lambda = run->d_lambda;
-    L.nsteps_w = run->d_nsteps;
-    L.nequil_w = run->d_nequil;
-    L.off_w = run->d_off;
-    L.tw = run->d_tw;
+    L.lambda = run->d_lambda + ri.w0;
+    L.nsteps_w = run->d_nsteps + ri.w0;
+    L.nequil_w = run->d_nequil + ri.w0;
+    L.off_w = run->d_off + ri.w0;
+    L.tw = run->d_tw + ri.w0;
     L.err = run->d_err;
     L.start = run->d_start;
     L.replicas = run->replicas;
     L.stride = run->stride;
-    L.uid_base = run->uid_base;
+    L.uid_base = run->uid_base + (uint32_t)(ri.w0 * run->replicas);
     L.seed = run->seed;
     L.k = run->k;
     L.kT = run->kT;
     L.dt = run->dt;
     L.gamma = run->gamma;
-    const int n_rep = run->n_windows * run->replicas;
+    const int n_rep = ri.nw * run->replicas;
     L.n_blocks = n_rep;
-    // chunks keep each launch bounded; state carries over in device memory
+    long long max_steps = 0;
+    for (int w = ri.w0; w < ri.w0 + ri.nw; ++w) max_steps = std::max(max_steps, run->nsteps[w]);
     const long long chunk = run->sys->model == PMF_MODEL_CHAIN ? 100000 : (1LL << 40);
-    for (long long s0 = 0; s0 < run->max_steps; s0 += chunk) {
+    for (long long s0 = 0; s0 < max_steps; s0 += chunk) {
         L.step_begin = s0;
-        L.step_end = std::min(run->max_steps, s0 + chunk);
-        cudaError_t e = run->sys->model == PMF_MODEL_CHAIN
-                            ? run->sys->chains[run->chain]->launch(L, g_stream)
-                            : od1d_launch(run->sys->od, L, n_rep, g_stream);
-        if (e != cudaSuccess) return cuda_fail(e, "launch simulation");
+        L.step_end = std::min(max_steps, s0 + chunk);
+        cudaError_t e = run->sys->model == PMF_MODEL_CHAIN ? run->sys->chains[ri.chain]->launch(L, st)
+                                                          : od1d_launch(run->sys->od, L, n_rep, st);
+        if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
+}
+
+// Enqueue the run's whole launch sequence on stream st (the capture stream).
+// A batch forks into independent branches, one chain of launches per item,
+// so that the items' kernels run concurrently and the block scheduler fills
+// the SMs; items are issued costliest first (longest CTAs start first) and
+// dealt to branches by least accumulated cost.
+static cudaError_t enqueue_run(pmf_run *run, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(run->d_err, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    if (run->branch.empty()) {
+        for (const RunItem &ri : run->items)
+            if ((e = enqueue_item(run, ri, st)) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
+    const int nb = (int)run->branch.size();
+    if ((e = cudaEventRecord(run->fork_ev[0], st)) != cudaSuccess) return e;
+    for (int b = 0; b < nb; ++b)
+        if ((e = cudaStreamWaitEvent(run->branch[b], run->fork_ev[0], 0)) != cudaSuccess) return e;
+    std::vector<int> order(run->items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::vector<double> cost(order.size());
+    for (size_t i = 0; i < order.size(); ++i) cost[i] = item_cost(run, run->items[i]);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<double> load(nb, 0.0);
+    for (int i : order) {
+        const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[b] += cost[i] * run->items[i].nw;
+        if ((e = enqueue_item(run, run->items[i], run->branch[b])) != cudaSuccess) return e;
+    }
+    for (int b = 0; b < nb; ++b) {
+        if ((e = cudaEventRecord(run->fork_ev[1 + b], run->branch[b])) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st, run->fork_ev[1 + b], 0)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+pmf_status pmf_run_launch(pmf_run *run)
+{
+    if (!run) return fail(PMF_EINVAL, "pmf_run_launch: null run");
+    if (run->d_start && run->items.size() > 1) return fail(PMF_EINVAL, "seeded starts need a single-item run");
+    // the whole launch sequence is captured once into a CUDA graph and
+    // replayed; it is re-captured when a chain's work schedule was rebuilt
+    // (pmf_chain_set_warps / pmf_chain_autotune) since the capture
+    std::vector<unsigned> gen;
+    for (const RunItem &ri : run->items)
+        gen.push_back(run->sys->model == PMF_MODEL_CHAIN ? run->sys->chains[ri.chain]->generation() : 0u);
+    if (!run->graph || gen != run->graph_gen) {
+        if (run->graph) {
+            cudaGraphExecDestroy(run->graph);
+            run->graph = nullptr;
+        }
+        CK(cudaStreamBeginCapture(run->cap, cudaStreamCaptureModeRelaxed), "begin capture");
+        cudaError_t e = enqueue_run(run, run->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(run->cap, &g);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(e, "capture run");
+        }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+        e = cudaGraphInstantiate(&run->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "instantiate graph");
+        run->graph_gen = gen;
+    }
+    CK(cudaGraphLaunch(run->graph, g_stream), "graph launch");
     CK(cudaEventRecord(run->done, g_stream), "record");
     run->launched = true;
     run->finished = false;
@@ -390,6 +530,7 @@ static ReduceLayout layout_of(const pmf_run *run)
 pmf_status pmf_work_samples(const pmf_run *run, int mode, double *out, size_t capacity, size_t *n_written)
 {
     if (pmf_status s = need_finished(run)) return s;
+    if (run->items.size() != 1) return fail(PMF_EINVAL, "pmf_work_samples: single-item runs only");
     long long need = 0;
     if (mode == PMF_WORK_PER_WINDOW_INCREMENT) {
         need = run->off[run->n_windows - 1];
@@ -423,10 +564,38 @@ static pmf_status copy_result(const double *host, int s, pmf_free_energy_result 
     return PMF_OK;
 }
 
+static ReduceLayout item_layout(const pmf_run *run, int item)
+{
+    ReduceLayout L = layout_of(run);
+    const RunItem &ri = run->items[item];
+    L.lambda = run->d_lambda + ri.w0;
+    L.off_w = run->d_off + ri.w0;
+    L.tw = run->d_tw + ri.w0;
+    L.n_windows = ri.nw;
+    return L;
+}
+
+pmf_status pmf_free_energy_item(const pmf_run *run, int item, pmf_free_energy_result *res)
+{
+    if (pmf_status s = need_finished(run)) return s;
+    if (!res || item < 0 || item >= (int)run->items.size()) return fail(PMF_EINVAL, "pmf_free_energy_item: bad item");
+    const int nw = run->items[item].nw;
+    if (nw < 2) return fail(PMF_EINVAL, "pmf_free_energy_item: the item needs two windows");
+    if (res->capacity < nw) return fail(PMF_EINVAL, "result capacity smaller than the item's windows");
+    cudaError_t e = reduce_launch(item_layout(run, item), run->d_scratch, run->d_res, g_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce");
+    const_cast<pmf_run *>(run)->reduced = false;  // d_res now holds this item
+    std::vector<double> h((size_t)kResFields * nw);
+    CK(cudaMemcpyAsync(h.data(), run->d_res, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g_stream), "copy");
+    CK(cudaStreamSynchronize(g_stream), "sync");
+    return copy_result(h.data(), nw, res);
+}
+
 pmf_status pmf_run_reduce(pmf_run *run)
 {
     if (!run) return fail(PMF_EINVAL, "null run");
     if (!run->launched) return fail(PMF_ESTATE, "pmf_run_reduce: run not launched");
+    if (run->items.size() != 1) return fail(PMF_EINVAL, "pmf_run_reduce: use pmf_free_energy_item on batch runs");
     cudaError_t e = reduce_launch(layout_of(run), run->d_scratch, run->d_res, g_stream);
     if (e != cudaSuccess) return cuda_fail(e, "reduce");
     run->reduced = true;
@@ -437,6 +606,7 @@ pmf_status pmf_free_energy(const pmf_run *run, pmf_free_energy_result *res)
 {
     if (pmf_status s = need_finished(run)) return s;
     if (!res) return fail(PMF_EINVAL, "null result");
+    if (run->items.size() != 1) return fail(PMF_EINVAL, "pmf_free_energy: use pmf_free_energy_item on batch runs");
     if (res->capacity < run->n_windows) return fail(PMF_EINVAL, "result capacity smaller than n_windows");
     if (!run->reduced) {
         cudaError_t e = reduce_launch(layout_of(run), run->d_scratch, run->d_res, g_stream);
@@ -987,23 +1157,29 @@ pmf_status pmf_final_state(const pmf_run *run, double *pos, double *vel, size_t 
         CK(cudaMemcpy(pos, run->d_state, sizeof(double) * n_rep, cudaMemcpyDeviceToHost), "copy state");
         return PMF_OK;
     }
-    const ChainModel &m = *run->sys->chains[run->chain];
-    const int N = m.n_beads(), Np = m.n_padded();
-    const size_t need = (size_t)n_rep * N * 3;
+    size_t need = 0;
+    for (const RunItem &ri : run->items)
+        need += (size_t)ri.nw * run->replicas * run->sys->chains[ri.chain]->n_beads() * 3;
     if (n_written) *n_written = need;
     if ((!pos && !vel) || capacity < need) return fail(PMF_EINVAL, "pmf_final_state: capacity too small");
     std::vector<unsigned char> raw(run->state_bytes);
     CK(cudaMemcpy(raw.data(), run->d_state, run->state_bytes, cudaMemcpyDeviceToHost), "copy state");
-    const bool dbl = m.precision() == PMF_FP64;
-    for (int q = 0; q < n_rep; ++q)
-        for (int b = 0; b < N; ++b)
-            for (int a = 0; a < 3; ++a) {
-                const size_t ip = ((size_t)q * 2 * Np + b) * 4 + a, iv = ((size_t)q * 2 * Np + Np + b) * 4 + a;
-                const double pv = dbl ? reinterpret_cast<double *>(raw.data())[ip] : reinterpret_cast<float *>(raw.data())[ip];
-                const double vv = dbl ? reinterpret_cast<double *>(raw.data())[iv] : reinterpret_cast<float *>(raw.data())[iv];
-                if (pos) pos[((size_t)q * N + b) * 3 + a] = pv;
-                if (vel) vel[((size_t)q * N + b) * 3 + a] = vv;
-            }
+    size_t o = 0;
+    for (const RunItem &ri : run->items) {
+        const ChainModel &m = *run->sys->chains[ri.chain];
+        const int N = m.n_beads(), Np = m.n_padded();
+        const bool dbl = m.precision() == PMF_FP64;
+        const unsigned char *base = raw.data() + ri.state_off;
+        for (int q = 0; q < ri.nw * run->replicas; ++q)
+            for (int b = 0; b < N; ++b, o += 3)
+                for (int a = 0; a < 3; ++a) {
+                    const size_t ip = ((size_t)q * 2 * Np + b) * 4 + a, iv = ((size_t)q * 2 * Np + Np + b) * 4 + a;
+                    const double pv = dbl ? reinterpret_cast<const double *>(base)[ip] : reinterpret_cast<const float *>(base)[ip];
+                    const double vv = dbl ? reinterpret_cast<const double *>(base)[iv] : reinterpret_cast<const float *>(base)[iv];
+                    if (pos) pos[o + a] = pv;
+                    if (vel) vel[o + a] = vv;
+                }
+    }
     return PMF_OK;
 }
 

@@ -884,6 +884,7 @@ struct ChainModel::Impl {
     int4 *units = nullptr;
     int *unit_count = nullptr;
     int max_units = 0;
+    unsigned generation = 0;
 };
 
 ChainModel::ChainModel() : p(new Impl) {}
@@ -907,12 +908,14 @@ cudaError_t ChainModel::init(const ChainHost &h, int precision)
 }
 
 int ChainModel::warps() const { return p->NW; }
+unsigned ChainModel::generation() const { return p->generation; }
 
 cudaError_t ChainModel::set_warps(int NW)
 {
     if (NW != 4 && NW != 6 && NW != 8) return cudaErrorInvalidValue;
     if (p->precision == 1 && NW != 4) return cudaErrorInvalidValue;
     p->NW = NW;
+    ++p->generation;
     cudaFree(p->units);
     cudaFree(p->unit_count);
     p->units = nullptr;
@@ -999,7 +1002,16 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     a.has_dih = any_dih;
     a.nonbonded = h.nonbonded;
     const size_t smem = chain_smem_bytes<R>(m->geo, NW);
-    cudaError_t e = cudaFuncSetAttribute(chain_kernel<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // The attribute is the kernel's upper limit, shared by every chain that
+    // launches it: raise it to the device's opt-in maximum rather than to this
+    // chain's size, so launches captured earlier in a graph (other chains,
+    // larger footprints) stay valid.  Each CTA still gets only `smem`.
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (smem > (size_t)optin) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(chain_kernel<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
     chain_kernel<R, NW><<<L.n_blocks, NW * 32, smem, st>>>(a);
     return cudaGetLastError();

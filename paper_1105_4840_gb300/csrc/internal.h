@@ -16,6 +16,9 @@ struct ChainHost {
     int nonbonded = 1;
 };
 
+constexpr int kMaxRunWindows = 4096;
+constexpr int kMaxBranches = 64;  // concurrent item branches of a batched run's graph
+
 // Tiling of N beads into 32-bead tiles; the last tile has width 8, 16 or 32.
 struct ChainGeometry {
     int N = 0, Np = 0, n_tiles = 0, w_last = 32;
@@ -63,6 +66,9 @@ public:
     size_t smem_bytes() const;
     int warps() const;
     cudaError_t set_warps(int NW);  // 4, 6 or 8 warps per replica (FP64: 4)
+    // Incremented by every set_warps (which reallocates the work schedule a
+    // captured launch points at): a captured graph older than this is stale.
+    unsigned generation() const;
 
 private:
     Impl *p;

@@ -184,6 +184,34 @@ def chain_workload(n_beads: int = 104, replicas: int = 32, n_steps: int = 400_00
     return {"params": p, "start": start, "run": run}
 
 
+def batch_workload(n_chains: int = 64, n_min: int = 40, n_max: int = 400, w_min: int = 21, w_max: int = 61,
+                   replicas: int = 16, n_steps: int = 100_000, seed: int = 0, lengths_seed: int = 7,
+                   start_tries: int = 2) -> dict:
+    """Many independent pulls at once: n_chains synthetic chains (the
+    parameter distributions of chain_params, param seed 100 + m) with
+    lengths uniform in [n_min, n_max] beads and window counts uniform in
+    [w_min, w_max]; chain m is pulled from lo_m to hi_m = (1.3, 3.3) nm x
+    sqrt(N_m / 104) (a random coil's size grows about as sqrt(N)), 16
+    replicas per window, 0.1 ns per window, the 104-bead workload's
+    temperature, trap and integrator settings.  Returns params, starts and
+    the per-chain lambda grids."""
+    g = np.random.Generator(np.random.PCG64(lengths_seed))
+    lengths = g.integers(n_min, n_max + 1, n_chains)
+    windows = g.integers(w_min, w_max + 1, n_chains)
+    params, starts, lams = [], [], []
+    for m in range(n_chains):
+        n = int(lengths[m])
+        p = chain_params(n, 100 + m)
+        scale = math.sqrt(n / 104.0)
+        lo, hi = 1.3 * scale, 3.3 * scale
+        params.append(p)
+        starts.append(chain_start(p, 2000 + m, target_x=lo, tries=start_tries))
+        lams.append(lambda_grid(lo, hi, int(windows[m])))
+    run = RunSettings(k=500.0, kT=kT_of(300.0), dt=0.001, gamma=5.0, n_steps=n_steps,
+                      n_equil=n_steps // 10, stride=100, replicas=replicas, seed=seed)
+    return {"params": params, "starts": starts, "lambdas": lams, "run": run}
+
+
 def gaussian_x_samples(lambdas, k, kT, replicas, samples, seed, *, shift=0.3, gamma2=1.2):
     """Synthetic FP32 reaction-coordinate samples [s][R][T]: Gaussian around
     lambda_i - shift * (i % 3) / 3 with variance gamma2 * kT / k.  Used to feed

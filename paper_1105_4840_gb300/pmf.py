@@ -48,9 +48,17 @@ class RunParams(C.Structure):
                 ("uid_base", C.c_uint32), ("chain", C.c_int), ("timeout_s", C.c_double)]
 
 
+MAX_RUN_WINDOWS = 4096  # PMF_MAX_RUN_WINDOWS
+
+
+class BatchItem(C.Structure):
+    _fields_ = [("chain", C.c_int), ("n_windows", C.c_int), ("lambda_", _D)]
+
+
 class RunInfo(C.Structure):
     _fields_ = [("n_windows", C.c_int), ("replicas", C.c_int), ("total_samples", C.c_int64),
-                ("samples_per_window", C.c_int64 * 1024), ("sample_offset", C.c_int64 * 1024)]
+                ("samples_per_window", C.c_int64 * MAX_RUN_WINDOWS),
+                ("sample_offset", C.c_int64 * MAX_RUN_WINDOWS)]
 
 
 RESULT_FIELDS = ("lambda", "dF_JE", "dF_fluct", "dF_G", "dF_com", "uncertainty", "se_JE",
@@ -83,6 +91,8 @@ def _load():
     for name in ("pmf_run_windows", "pmf_run_prepare"):
         getattr(L, name).argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.POINTER(P)]
     L.pmf_run_prepare_seeded.argtypes = [P, _D, C.c_int, C.POINTER(RunParams), _D, C.POINTER(P)]
+    L.pmf_run_batch_prepare.argtypes = [P, C.POINTER(BatchItem), C.c_int, C.POINTER(RunParams), C.POINTER(P)]
+    L.pmf_free_energy_item.argtypes = [P, C.c_int, C.POINTER(FreeEnergyResult)]
     L.pmf_run_launch.argtypes = [P]
     L.pmf_run_wait.argtypes = [P]
     L.pmf_destroy_run.argtypes = [P]
@@ -117,7 +127,8 @@ def _load():
     L.pmf_set_stream.argtypes = [C.c_void_p]
     L.pmf_last_error.restype = C.c_char_p
     L.pmf_version.restype = C.c_char_p
-    for name in ("pmf_create_system", "pmf_run_windows", "pmf_run_prepare", "pmf_run_prepare_seeded", "pmf_run_launch",
+    for name in ("pmf_create_system", "pmf_run_windows", "pmf_run_prepare", "pmf_run_prepare_seeded", "pmf_run_batch_prepare",
+                 "pmf_free_energy_item", "pmf_run_launch",
                  "pmf_run_wait", "pmf_get_run_info", "pmf_x_samples", "pmf_work_samples",
                  "pmf_free_energy", "pmf_free_energy_from_samples", "pmf_final_state", "pmf_philox",
                  "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_free_energy_noalloc",
@@ -266,6 +277,10 @@ class Run:
         return _fe_call(lambda res: lib.pmf_free_energy(self.handle, C.byref(res)), self.lambdas.size,
                         "pmf_free_energy")
 
+    def free_energy_item(self, item, n_windows):
+        return _fe_call(lambda res: lib.pmf_free_energy_item(self.handle, item, C.byref(res)), n_windows,
+                        "pmf_free_energy_item")
+
     def final_state(self):
         n = C.c_size_t()
         lib.pmf_final_state(self.handle, None, None, 0, C.byref(n))
@@ -298,6 +313,21 @@ def pmf_run_prepare_seeded(system: System, lambdas, params, start) -> Run:
     _check(lib.pmf_run_prepare_seeded(system.handle, _dp(lam), lam.size, C.byref(p), _dp(st), C.byref(h)),
            "pmf_run_prepare_seeded")
     return Run(h, lam, keep=(p, keep, system, st))
+
+
+def pmf_run_batch_prepare(system: System, items, params) -> Run:
+    """items: sequence of (chain index, lambda array); windows are laid end to
+    end in item order.  The returned Run's lambdas are the concatenation and
+    `item_windows` the per-item window counts."""
+    lams = [np.ascontiguousarray(l, dtype=np.float64) for _, l in items]
+    arr = (BatchItem * len(lams))(*[BatchItem(chain=int(c), n_windows=l.size, lambda_=_dp(l))
+                                    for (c, _), l in zip(items, lams)])
+    p, keep = params
+    h = C.c_void_p()
+    _check(lib.pmf_run_batch_prepare(system.handle, arr, len(lams), C.byref(p), C.byref(h)), "pmf_run_batch_prepare")
+    run = Run(h, np.concatenate(lams), keep=(p, keep, system, lams, arr))
+    run.item_windows = [l.size for l in lams]
+    return run
 
 
 def pmf_run_windows(system: System, lambdas, params) -> Run:

@@ -290,6 +290,7 @@ def main():
     sysh = pmf.pmf_create_system_chain([p], [start])
     # untimed setup: pick warps per replica from short probes of this run
     warps, _ = pmf.pmf_chain_autotune(sysh, run.lambdas, pmf.make_params(run, uid_base=uid_base), probe_steps=2000)
+    _, grid_ctas, seg_steps = pmf.pmf_chain_get_launch(sysh, 0)
     rr = pmf.pmf_run_prepare(sysh, run.lambdas, pmf.make_params(run, uid_base=uid_base))
     replica_steps = n_rep * run.n_steps
     chunks = math.ceil(run.n_steps / 100000)
@@ -344,6 +345,7 @@ def main():
         t0 = time.perf_counter()
         sys2 = pmf.pmf_create_system_chain([p], [start])
         pmf.pmf_chain_set_warps(sys2, 0, warps)
+        pmf.pmf_chain_set_grid(sys2, 0, grid_ctas, seg_steps)
         r2 = pmf.pmf_run_windows(sys2, run.lambdas, pmf.make_params(run, uid_base=uid_base))
         out = r2.free_energy()
         e2e_times.append(time.perf_counter() - t0)
@@ -381,6 +383,8 @@ def main():
                        "md_steps_per_window": run.n_steps, "dt_ps": run.dt, "sample_stride": run.stride,
                        "forces": "fp32", "reductions": "fp64", "parallelism": f"replicas x{world}",
                        "warps_per_replica": warps,
+                       "launch": (f"persistent, {'auto' if grid_ctas == 0 else grid_ctas} CTAs, "
+                                  f"{seg_steps}-step segments"),
                        "l2": "256 MB flush between timed steps"},
             "e2e": {"value": e2e_value, "unit": "replica-steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -278,9 +278,28 @@ pmf_status pmf_final_state(const pmf_run *run, double *pos, double *vel, size_t 
  * Results are bit-reproducible for a given count; different counts sum the
  * forces in different orders. */
 pmf_status pmf_chain_set_warps(pmf_system *sys, int chain, int warps);
+/* Launch shape of chain `chain` in single-item runs.  ctas < 0: one CTA per
+ * replica, every replica's steps in one launch per 1e5-step chunk.
+ * ctas >= 0: persistent launch of min(ctas, replicas) CTAs (ctas = 0: every
+ * CTA slot the GPU holds at once) that take work items of seg_steps steps
+ * (0: 1000) of one replica from a device queue, in segment-major order
+ * (ctas = 0 picks: every slot if the replicas fill them, else a whole number
+ * of CTAs per SM when that is at least 3, else one CTA per replica); a
+ * replica's next segment waits (at most 60 s, then PMF_ETIMEOUT) until its
+ * previous one has stored the state.  Replicas thus migrate between CTAs and
+ * no SM idles when the replica count is not a multiple of the SM count.
+ * Trajectories are bit-identical for every shape (the state record holds
+ * the whole integrator state between segments).  Default: ctas = 0,
+ * seg_steps = 1000.  Batched runs always use one CTA per replica. */
+pmf_status pmf_chain_set_grid(pmf_system *sys, int chain, int ctas, int seg_steps);
+/* The current warps per replica, ctas and seg_steps of chain `chain` (as set
+ * by the calls above or chosen by pmf_chain_autotune); NULL outputs skipped. */
+pmf_status pmf_chain_get_launch(const pmf_system *sys, int chain, int *warps, int *ctas, int *seg_steps);
 /* Time probe_steps steps of the given run (every window and replica, one
- * warm-up launch each) for each warp count and keep the fastest; *best_warps
- * and *best_ms (may be NULL) report the choice and its probe time. */
+ * warm-up launch each) for each warp count and each of two persistent
+ * launch shapes (ctas = 0 and ctas = one per replica, see
+ * pmf_chain_set_grid) and keep the fastest; *best_warps and *best_ms (may
+ * be NULL) report the warp count chosen and its probe time. */
 pmf_status pmf_chain_autotune(pmf_system *sys, const double *lambda, int n_windows, const pmf_run_params *p,
                               int probe_steps, int *best_warps, double *best_ms);
 

@@ -87,6 +87,8 @@ struct pmf_run {
     void *d_scratch = nullptr;
     double *d_res = nullptr;
     double *d_start = nullptr;  // per-replica start state of a seeded run
+    unsigned long long *d_queue = nullptr;  // persistent launch: work counter
+    int *d_done = nullptr;                  // persistent launch: per-replica segments done
     cudaEvent_t done = nullptr;
     bool launched = false, finished = false, reduced = false;
     size_t state_bytes = 0;
@@ -104,6 +106,8 @@ struct pmf_run {
         cudaFree(d_scratch);
         cudaFree(d_res);
         cudaFree(d_start);
+        cudaFree(d_queue);
+        cudaFree(d_done);
         if (done) cudaEventDestroy(done);
         if (graph) cudaGraphExecDestroy(graph);
         if (cap) cudaStreamDestroy(cap);
@@ -192,7 +196,7 @@ pmf_status pmf_create_system(const pmf_system_desc *d, pmf_system **out)
         auto m = std::make_unique<ChainModel>();
         cudaError_t e = m->init(h, d->precision);
         if (e != cudaSuccess) return cuda_fail(e, "pmf_create_system");
-        if (m->smem_bytes() > 227 * 1024) return fail(PMF_EINVAL, "chain too long for this precision (shared memory)");
+        if (m->smem_bytes() > 227 * 1024 - 256) return fail(PMF_EINVAL, "chain too long for this precision (shared memory)");
         sys->chains.push_back(std::move(m));
     }
     *out = sys.release();
@@ -286,6 +290,10 @@ static pmf_status prepare_items(pmf_system *sys, const pmf_batch_item *items, in
     CK(cudaMalloc(&run->d_res, sizeof(double) * kResFields * max_nw), "alloc results");
     CK(cudaEventCreateWithFlags(&run->done, cudaEventDisableTiming), "event");
     CK(cudaStreamCreateWithFlags(&run->cap, cudaStreamNonBlocking), "capture stream");
+    if (n_items == 1 && sys->model == PMF_MODEL_CHAIN) {
+        CK(cudaMalloc(&run->d_queue, sizeof(unsigned long long)), "alloc queue");
+        CK(cudaMalloc(&run->d_done, sizeof(int) * (size_t)n_windows * p->replicas), "alloc segment counters");
+    }
     const int n_branch = std::min(n_items, kMaxBranches);
     if (n_branch > 1) {
         run->fork_ev.assign(1 + n_branch, nullptr);
@@ -336,6 +344,8 @@ static cudaError_t enqueue_item(pmf_run *run, const RunItem &ri, cudaStream_t st
     L.tw = run->d_tw + ri.w0;
     L.err = run->d_err;
     L.start = run->d_start;
+    L.queue = run->d_queue;  // set for single-item chain runs only
+    L.done = run->d_done;
     L.replicas = run->replicas;
     L.stride = run->stride;
     L.uid_base = run->uid_base + (uint32_t)(ri.w0 * run->replicas);
@@ -1065,10 +1075,31 @@ pmf_status pmf_chain_set_warps(pmf_system *sys, int chain, int warps)
     cudaError_t e = sys->chains[chain]->set_warps(warps);
     if (e == cudaErrorInvalidValue) return fail(PMF_EINVAL, "pmf_chain_set_warps: warps must be 4, 6 or 8 (FP64: 4)");
     if (e != cudaSuccess) return cuda_fail(e, "pmf_chain_set_warps");
-    if (sys->chains[chain]->smem_bytes() > 227 * 1024) {
+    if (sys->chains[chain]->smem_bytes() > 227 * 1024 - 256) {
         sys->chains[chain]->set_warps(4);
         return fail(PMF_EINVAL, "pmf_chain_set_warps: shared memory would exceed 227 KB");
     }
+    return PMF_OK;
+}
+
+pmf_status pmf_chain_set_grid(pmf_system *sys, int chain, int ctas, int seg_steps)
+{
+    if (!sys || sys->model != PMF_MODEL_CHAIN || chain < 0 || chain >= (int)sys->chains.size())
+        return fail(PMF_EINVAL, "pmf_chain_set_grid: not a chain system / bad chain index");
+    if (seg_steps < 0) return fail(PMF_EINVAL, "pmf_chain_set_grid: seg_steps must be >= 0");
+    cudaError_t e = sys->chains[chain]->set_grid(ctas, seg_steps);
+    if (e != cudaSuccess) return cuda_fail(e, "pmf_chain_set_grid");
+    return PMF_OK;
+}
+
+pmf_status pmf_chain_get_launch(const pmf_system *sys, int chain, int *warps, int *ctas, int *seg_steps)
+{
+    if (!sys || sys->model != PMF_MODEL_CHAIN || chain < 0 || chain >= (int)sys->chains.size())
+        return fail(PMF_EINVAL, "pmf_chain_get_launch: not a chain system / bad chain index");
+    const ChainModel &m = *sys->chains[chain];
+    if (warps) *warps = m.warps();
+    if (ctas) *ctas = m.grid_ctas();
+    if (seg_steps) *seg_steps = m.seg_steps();
     return PMF_OK;
 }
 
@@ -1089,25 +1120,35 @@ pmf_status pmf_chain_autotune(pmf_system *sys, const double *lambda, int n_windo
     pmf_run *run = nullptr;
     if (pmf_status s = pmf_run_prepare(sys, lambda, n_windows, &q, &run)) return s;
     std::unique_ptr<pmf_run, void (*)(pmf_run *)> guard(run, pmf_destroy_run);
-    int best = m.warps();
+    int best = m.warps(), best_grid = m.grid_ctas();
+    const int seg = m.seg_steps();
     double best_t = 1e300;
     GpuTimer timer;
+    // launch shapes: the automatic persistent grid, and one persistent CTA
+    // per replica (equal to auto when the replicas fill every CTA slot)
+    const int n_rep = n_windows * p->replicas;
+    const int grids[2] = {0, n_rep};
     for (int c = 0; c < n_cand; ++c) {
         if (pmf_chain_set_warps(sys, p->chain, cand_fp32[c]) != PMF_OK) continue;
-        if (pmf_status s = pmf_run_launch(run)) return s;  // warm-up
-        if (pmf_status s = pmf_run_wait(run)) return s;
-        const double before = timer.ms;
-        timer.start();
-        if (pmf_status s = pmf_run_launch(run)) return s;
-        CK(timer.stop(), "autotune timer");
-        if (pmf_status s = pmf_run_wait(run)) return s;
-        const double t = timer.ms - before;
-        if (t < best_t) {
-            best_t = t;
-            best = cand_fp32[c];
+        for (int gsel = 0; gsel < 2; ++gsel) {
+            if (m.set_grid(grids[gsel], seg) != cudaSuccess) continue;
+            if (pmf_status s = pmf_run_launch(run)) return s;  // warm-up
+            if (pmf_status s = pmf_run_wait(run)) return s;
+            const double before = timer.ms;
+            timer.start();
+            if (pmf_status s = pmf_run_launch(run)) return s;
+            CK(timer.stop(), "autotune timer");
+            if (pmf_status s = pmf_run_wait(run)) return s;
+            const double t = timer.ms - before;
+            if (t < best_t) {
+                best_t = t;
+                best = cand_fp32[c];
+                best_grid = grids[gsel];
+            }
         }
     }
     if (pmf_status s = pmf_chain_set_warps(sys, p->chain, best)) return s;
+    if (m.set_grid(best_grid, seg) != cudaSuccess) return fail(PMF_EINVAL, "pmf_chain_autotune: grid");
     if (best_warps) *best_warps = best;
     if (best_ms) *best_ms = best_t;
     return PMF_OK;

@@ -55,6 +55,10 @@ template <typename R> struct ChainArgs {
     int *err;
     double *force_out;         // optional [N][3]: forces at the final positions
     const double *start;       // optional [n_rep][N][3]: start positions instead of x_o
+    unsigned long long *queue; // persistent mode: next work item (zeroed before the launch)
+    int *done;                 // persistent mode: [n_rep] segments finished (zeroed)
+    long long n_items;         // persistent mode: n_rep x segments
+    int n_rep, seg_steps, persistent;
     long long step_begin, step_end;
     int N, Np, n_tiles, w_last, replicas, max_units, stride;
     uint32_t uid_base;
@@ -569,40 +573,32 @@ __device__ __forceinline__ void force_phase(const ChainArgs<R> &a, const Smem<R>
     }
 }
 
-template <typename R, int NW>
-__global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW == 6 ? 4 : 3)) : 1)
-    chain_kernel(const ChainArgs<R> a)
-// FP32 with 4 warps: five CTAs per SM fit (a 672-replica workload has 4.4 per
-// SM); 6 and 8 warps trade occupancy for registers (workloads with many
-// replicas per SM)
+// Loads that bypass L1: a replica's state may have been written by a CTA on
+// another SM (persistent mode), after this SM cached an older copy.
+template <typename R> __device__ __forceinline__ Vec4<R> load_cg(const Vec4<R> *p);
+template <> __device__ __forceinline__ Vec4<float> load_cg<float>(const Vec4<float> *p)
 {
-    extern __shared__ __align__(32) unsigned char smem_raw[];
-    const int rep = blockIdx.x;
+    const float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
+    return Vec4<float>{v.x, v.y, v.z, v.w};
+}
+template <> __device__ __forceinline__ Vec4<double> load_cg<double>(const Vec4<double> *p)
+{
+    const double2 u = __ldcg(reinterpret_cast<const double2 *>(p));
+    const double2 v = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    return Vec4<double>{u.x, u.y, v.x, v.y};
+}
+
+// Steps [s0, s1) of replica `rep` (s1 clipped to the window's step count).
+// State comes from x_o / the seeded start (s0 == 0) or from the replica's
+// state record, and goes back to it at the end, so a replica's trajectory
+// does not depend on how its steps are cut into launches or segments.
+// Returns false when the run was aborted (non-finite state).
+template <typename R, int NW>
+__device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s, int rep, long long s0,
+                                         long long s1)
+{
     const int w = rep / a.replicas, r = rep % a.replicas;
     const uint32_t uid = a.uid_base + (uint32_t)rep;
-    const long long nsteps = a.nsteps_w[w];
-    const long long s0 = a.step_begin;
-    const long long s1 = a.step_end < nsteps ? a.step_end : nsteps;
-    if (s0 >= s1 && a.force_out == nullptr) return;
-    if (*((volatile int *)a.err) != 0) return;
-
-    Smem<R> s;
-    {
-        unsigned char *p = smem_raw;
-        s.posd = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.n_tiles * 64;
-        s.eqd = reinterpret_cast<Vec2<R> *>(p); p += sizeof(Vec2<R>) * a.n_tiles * 64;
-        s.vel = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np;
-        s.fw = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * NW;
-        s.bslot = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * 4;
-        s.noise = reinterpret_cast<R *>(p); p += sizeof(Vec4<R>) * ((3 * a.N + 3) >> 2);
-        s.posp = nullptr;
-        s.eqp = nullptr;
-        if constexpr (kPacked<R>) {
-            s.posp = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 2 * 64 * a.n_tiles;
-            s.eqp = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 64 * a.n_tiles;
-        }
-        s.flag = reinterpret_cast<int *>(p);
-    }
     const int tid = threadIdx.x;
     const R lam = (R)a.lambda[w];
     const R hdt = R(0.5) * a.dt;
@@ -634,9 +630,9 @@ __global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW =
                 v = Vec4<R>{sv * xi[0], sv * xi[1], sv * xi[2], R(0)};
             }
         } else {
-            p = st[b];
+            p = load_cg(st + b);
             p.w = a.bead_pos0[b].w;
-            v = st[a.Np + b];
+            v = load_cg(st + a.Np + b);
         }
         store_pos<R>(s, b, V3<R>{p.x, p.y, p.z}, p.w, a.n_tiles, a.w_last);
         s.vel[b] = v;
@@ -704,7 +700,7 @@ __global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW =
         __syncthreads();
         if (*s.flag) {
             if (tid == 0) atomicOr(a.err, kErrNonFinite);
-            return;
+            return false;
         }
     }
     __syncthreads();
@@ -712,6 +708,116 @@ __global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW =
         const V3<R> p = pos_of(s, b);
         st[b] = Vec4<R>{p.x, p.y, p.z, R(0)};
         st[a.Np + b] = s.vel[b];
+    }
+    return true;
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Longest wait for a replica's previous segment before the kernel gives up
+// (flags kErrTimeout and returns); a segment normally takes milliseconds.
+constexpr unsigned long long kSegmentWaitNs = 60ull * 1000000000ull;
+
+// Persistent mode, thread 0: the next work item (segment-major: item =
+// segment x n_rep + replica) once the replica's previous segment is done;
+// -1 when the queue is empty or the run was aborted.
+template <typename R>
+__device__ long long next_item(const ChainArgs<R> &a)
+{
+    if (*((volatile int *)a.err) != 0) return -1;
+    const unsigned long long it = atomicAdd(a.queue, 1ull);
+    if (it >= (unsigned long long)a.n_items) return -1;
+    const int rep = (int)(it % (unsigned long long)a.n_rep);
+    const int seg = (int)(it / (unsigned long long)a.n_rep);
+    if (seg > 0 && ld_acquire(a.done + rep) < seg) {
+        const unsigned long long t0 = global_ns();
+        while (ld_acquire(a.done + rep) < seg) {
+            if (*((volatile int *)a.err) != 0) return -1;
+            if (global_ns() - t0 > kSegmentWaitNs) {
+                atomicOr(a.err, kErrTimeout);
+                return -1;
+            }
+            __nanosleep(500);
+        }
+    }
+    return (long long)it;
+}
+
+template <typename R, int NW>
+__global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW == 6 ? 4 : 3)) : 1)
+    chain_kernel(const ChainArgs<R> a)
+// FP32 with 4 warps: five CTAs per SM fit; 6 and 8 warps trade occupancy for
+// registers.  Two modes:
+//  * one CTA per replica (blockIdx.x), steps [step_begin, step_end);
+//  * persistent: gridDim.x CTAs take (segment, replica) items of seg_steps
+//    steps from a global queue, so replicas migrate between CTAs and every SM
+//    stays busy until the queue drains (a replica count that is not a
+//    multiple of the SM count no longer leaves SMs idle).  A replica's
+//    segments run in order: the CTA that takes segment q waits (bounded)
+//    until segment q - 1 has released its state.  Trajectories are
+//    identical in both modes.
+{
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    __shared__ long long s_item;
+    Smem<R> s;
+    {
+        unsigned char *p = smem_raw;
+        s.posd = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.n_tiles * 64;
+        s.eqd = reinterpret_cast<Vec2<R> *>(p); p += sizeof(Vec2<R>) * a.n_tiles * 64;
+        s.vel = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np;
+        s.fw = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * NW;
+        s.bslot = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * 4;
+        s.noise = reinterpret_cast<R *>(p); p += sizeof(Vec4<R>) * ((3 * a.N + 3) >> 2);
+        s.posp = nullptr;
+        s.eqp = nullptr;
+        if constexpr (kPacked<R>) {
+            s.posp = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 2 * 64 * a.n_tiles;
+            s.eqp = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 64 * a.n_tiles;
+        }
+        s.flag = reinterpret_cast<int *>(p);
+    }
+    // one call site of simulate() for both modes keeps the kernel compact;
+    // the item survives the segment in shared memory, not in registers
+    for (long long iter = 0;; ++iter) {
+        if (threadIdx.x == 0) s_item = a.persistent ? next_item(a) : (iter == 0 ? (long long)blockIdx.x : -1);
+        __syncthreads();
+        const long long it = s_item;
+        __syncthreads();  // every thread has read s_item before it is overwritten
+        if (it < 0) return;
+        const int rep = (int)(it % a.n_rep);
+        const long long seg = it / a.n_rep;
+        const long long nsteps = a.nsteps_w[rep / a.replicas];
+        long long s0 = a.step_begin, s1 = a.step_end;
+        if (a.persistent) {
+            s0 += seg * a.seg_steps;
+            s1 = s0 + a.seg_steps < a.step_end ? s0 + a.seg_steps : a.step_end;
+        } else if (*((volatile int *)a.err) != 0) {
+            return;
+        }
+        s1 = s1 < nsteps ? s1 : nsteps;
+        if ((s0 < s1 || a.force_out != nullptr) && !simulate<R, NW>(a, s, rep, s0, s1)) return;
+        if (a.persistent) {
+            __syncthreads();  // the replica's state record is written
+            if (threadIdx.x == 0) {
+                const long long done_item = s_item;
+                __threadfence();
+                st_release(a.done + (int)(done_item % a.n_rep), (int)(done_item / a.n_rep) + 1);
+            }
+        }
     }
 }
 
@@ -885,6 +991,8 @@ struct ChainModel::Impl {
     int *unit_count = nullptr;
     int max_units = 0;
     unsigned generation = 0;
+    int grid_ctas = 0;       // persistent CTAs: 0 = auto, < 0 = one CTA per replica
+    int seg_steps = 1000;    // steps per persistent work item
 };
 
 ChainModel::ChainModel() : p(new Impl) {}
@@ -908,6 +1016,17 @@ cudaError_t ChainModel::init(const ChainHost &h, int precision)
 }
 
 int ChainModel::warps() const { return p->NW; }
+
+cudaError_t ChainModel::set_grid(int ctas, int seg_steps)
+{
+    if (seg_steps < 0) return cudaErrorInvalidValue;
+    p->grid_ctas = ctas;
+    p->seg_steps = seg_steps > 0 ? seg_steps : 1000;
+    ++p->generation;
+    return cudaSuccess;
+}
+int ChainModel::grid_ctas() const { return p->grid_ctas; }
+int ChainModel::seg_steps() const { return p->seg_steps; }
 unsigned ChainModel::generation() const { return p->generation; }
 
 cudaError_t ChainModel::set_warps(int NW)
@@ -1001,6 +1120,12 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
         for (int q = 0; q < 3; ++q) any_dih = any_dih || h.dih_k[3 * b + q] != 0.0;
     a.has_dih = any_dih;
     a.nonbonded = h.nonbonded;
+    a.queue = L.queue;
+    a.done = L.done;
+    a.n_rep = L.n_blocks;
+    a.seg_steps = m->seg_steps;
+    a.persistent = 0;
+    a.n_items = 0;
     const size_t smem = chain_smem_bytes<R>(m->geo, NW);
     // The attribute is the kernel's upper limit, shared by every chain that
     // launches it: raise it to the device's opt-in maximum rather than to this
@@ -1010,10 +1135,40 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(chain_kernel<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    cudaFuncAttributes fa{};
+    if ((e = cudaFuncGetAttributes(&fa, chain_kernel<R, NW>)) != cudaSuccess) return e;
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;  // static + dynamic <= opt-in limit
+    if (smem > (size_t)dyn_max) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(chain_kernel<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
     if (e != cudaSuccess) return e;
-    chain_kernel<R, NW><<<L.n_blocks, NW * 32, smem, st>>>(a);
+    int grid = L.n_blocks;
+    if (L.queue != nullptr && L.done != nullptr && m->grid_ctas >= 0 && L.force_out == nullptr &&
+        L.step_end > L.step_begin) {
+        // persistent: as many CTAs as fit at once (or as requested), never
+        // more than there are replicas
+        int occ = 0, sms = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chain_kernel<R, NW>, NW * 32, smem)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        const long long slots = (long long)std::max(occ, 1) * sms;
+        long long want = m->grid_ctas;
+        if (want == 0) {
+            // auto: fill every slot when there are enough replicas; otherwise a
+            // whole number of CTAs per SM (replicas in excess of it keep the
+            // queue ahead of the running segments, so no CTA waits), unless
+            // that number is below 3, where more CTAs per SM still pay
+            const long long per_sm = L.n_blocks / sms;
+            want = L.n_blocks >= slots ? slots : (per_sm >= 3 ? per_sm * sms : L.n_blocks);
+        }
+        grid = (int)std::min<long long>(want, L.n_blocks);
+        const long long nseg = (L.step_end - L.step_begin + a.seg_steps - 1) / a.seg_steps;
+        a.persistent = 1;
+        a.n_items = nseg * L.n_blocks;
+        if ((e = cudaMemsetAsync(L.queue, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(L.done, 0, sizeof(int) * (size_t)L.n_blocks, st)) != cudaSuccess) return e;
+    }
+    chain_kernel<R, NW><<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 

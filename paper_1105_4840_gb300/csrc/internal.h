@@ -45,6 +45,10 @@ struct RunLaunch {
     int *err = nullptr;
     double *force_out = nullptr;
     const double *start = nullptr;  // optional per-replica start state (chain [rep][N][3], 1D [rep])
+    // persistent chain launches (single-item runs): work queue counter and
+    // per-replica segment counters, both zeroed by the launch itself
+    unsigned long long *queue = nullptr;
+    int *done = nullptr;
     long long step_begin = 0, step_end = 0;
     int replicas = 0, stride = 1, n_blocks = 0;
     uint32_t uid_base = 0;
@@ -69,6 +73,12 @@ public:
     // Incremented by every set_warps (which reallocates the work schedule a
     // captured launch points at): a captured graph older than this is stale.
     unsigned generation() const;
+    // Launch shape: ctas > 0 persistent with that many CTAs, 0 persistent
+    // with every CTA slot of the GPU, < 0 one CTA per replica; seg_steps =
+    // steps per persistent work item (0: 1000).  Bumps the generation.
+    cudaError_t set_grid(int ctas, int seg_steps);
+    int grid_ctas() const;
+    int seg_steps() const;
 
 private:
     Impl *p;

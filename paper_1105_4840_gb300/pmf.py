@@ -123,6 +123,8 @@ def _load():
     L.pmf_run_adaptive.argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.POINTER(AdaptiveParams),
                                    C.POINTER(AdaptiveInfo), C.POINTER(FreeEnergyResult)]
     L.pmf_chain_set_warps.argtypes = [P, C.c_int, C.c_int]
+    L.pmf_chain_set_grid.argtypes = [P, C.c_int, C.c_int, C.c_int]
+    L.pmf_chain_get_launch.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.pmf_chain_autotune.argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.c_int, C.POINTER(C.c_int), _D]
     L.pmf_set_stream.argtypes = [C.c_void_p]
     L.pmf_last_error.restype = C.c_char_p
@@ -133,7 +135,8 @@ def _load():
                  "pmf_free_energy", "pmf_free_energy_from_samples", "pmf_final_state", "pmf_philox",
                  "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_free_energy_noalloc",
                  "pmf_mlp_create", "pmf_mlp_get_params", "pmf_mlp_predict", "pmf_mlp_gradient", "pmf_mlp_train",
-                 "pmf_overlap", "pmf_run_adaptive", "pmf_chain_set_warps", "pmf_chain_autotune", "pmf_set_stream"):
+                 "pmf_overlap", "pmf_run_adaptive", "pmf_chain_set_warps", "pmf_chain_set_grid", "pmf_chain_get_launch",
+                 "pmf_chain_autotune", "pmf_set_stream"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -481,6 +484,17 @@ def pmf_run_adaptive(system: System, lambda0, params, mlp_init, threshold=0.3, m
 
 def pmf_chain_set_warps(system: System, chain, warps):
     _check(lib.pmf_chain_set_warps(system.handle, chain, warps), "pmf_chain_set_warps")
+
+
+def pmf_chain_set_grid(system: System, chain, ctas, seg_steps=0):
+    _check(lib.pmf_chain_set_grid(system.handle, chain, ctas, seg_steps), "pmf_chain_set_grid")
+
+
+def pmf_chain_get_launch(system: System, chain=0):
+    """(warps, ctas, seg_steps) of a chain's launch shape."""
+    w, c, g = C.c_int(), C.c_int(), C.c_int()
+    _check(lib.pmf_chain_get_launch(system.handle, chain, C.byref(w), C.byref(c), C.byref(g)), "pmf_chain_get_launch")
+    return w.value, c.value, g.value
 
 
 def pmf_chain_autotune(system: System, lambdas, params, probe_steps=400):

@@ -273,3 +273,25 @@ def test_autotune_picks_a_valid_count_and_runs(pmf):
     assert best in (4, 6, 8) and ms > 0
     rr = pmf.pmf_run_windows(sysh, lam, pmf.make_params(run))
     assert np.all(np.isfinite(rr.free_energy()["dF_JE"]))
+
+
+@pytest.mark.parametrize("prec,per_window", [(0, False), (1, False), (0, True)])
+def test_persistent_grid_is_bit_identical(pmf, prec, per_window):
+    """Persistent launches (replicas migrating between CTAs in segments of a
+    few steps, fewer CTAs than replicas) reproduce the one-CTA-per-replica
+    trajectories and samples bit for bit, for FP32 and FP64 integration."""
+    p = inputs.chain_params(70, 3)
+    start = f32(inputs.chain_start(p, 1003, target_x=1.2))
+    run = inputs.RunSettings(k=500.0, kT=inputs.kT_of(300.0), dt=0.001, gamma=5.0, n_steps=330, n_equil=30,
+                             stride=20, replicas=5, seed=11)
+    lam = np.array([1.2, 1.5, 1.8, 2.1])
+    sysh = pmf.pmf_create_system_chain([p], [start], precision=prec)
+    out = []
+    for ctas, seg in ((-1, 0), (7, 45), (0, 1000), (3, 1)):
+        pmf.pmf_chain_set_grid(sysh, 0, ctas, seg)
+        spw = [330, 200, 330, 60] if per_window else None
+        rr = pmf.pmf_run_windows(sysh, lam, pmf.make_params(run, n_steps_per_window=spw))
+        out.append((np.concatenate([a.ravel() for a in rr.x_samples()]), rr.final_state()[0]))
+    for x, pos in out[1:]:
+        assert np.array_equal(x, out[0][0])
+        assert np.array_equal(pos, out[0][1])

@@ -110,13 +110,21 @@ def _peaks():
         return {}
 
 
-def _ncu_traffic():
-    """DRAM bytes per chain-kernel launch from the committed ncu summary, if current."""
+def _ncu_traffic(warps):
+    """DRAM bytes per chain-kernel launch from the committed ncu summary, only
+    if it was taken on the current kernel source and the same warp count."""
+    import hashlib
+
     try:
         with open(os.path.join(ROOT, "profiles", "chain_kernel_traffic.json")) as fh:
-            return json.load(fh)
+            t = json.load(fh)
+        with open(os.path.join(ROOT, "paper_1105_4840_gb300", "csrc", "chain.cu"), "rb") as fh:
+            h = hashlib.sha256(fh.read()).hexdigest()
     except OSError:
         return None
+    if t.get("chain_cu_sha256") != h or f"<float, {warps}>" not in t.get("kernel", ""):
+        return None
+    return t
 
 
 def cpu_baseline(budget_s=12.0, n_steps=200):
@@ -365,7 +373,7 @@ def main():
     chain_launch_ms = sum(sim_ms) / (len(sim_ms) * chunks)
     flops_launch = n_rep * min(run.n_steps, 100000) * flops_per_replica_step(N_BEADS)
     achieved = flops_launch / (chain_launch_ms / 1000.0) / 1e12
-    traffic = _ncu_traffic()
+    traffic = _ncu_traffic(warps)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops,
             "traffic": (traffic or {}).get("dram_bytes_per_launch"),

@@ -294,7 +294,9 @@ def main():
     p, start, run = w["params"], w["start"], w["run"]
     s, R = run.lambdas.size, run.replicas
     n_rep = s * R
-    uid_base = rank * n_rep
+    from paper_1105_4840_gb300.shard import shard_uid_base
+
+    uid_base = shard_uid_base(rank, s, R)
     sysh = pmf.pmf_create_system_chain([p], [start])
     # untimed setup: pick warps per replica from short probes of this run
     warps, _ = pmf.pmf_chain_autotune(sysh, run.lambdas, pmf.make_params(run, uid_base=uid_base), probe_steps=2000)
@@ -304,13 +306,21 @@ def main():
     chunks = math.ceil(run.n_steps / 100000)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    from paper_1105_4840_gb300 import shard
+
     def one_step(ev=None):
         if ev is not None:
             ev[0].record(stream)
         rr.launch()
         if ev is not None:
             ev[1].record(stream)
-        rr.reduce()
+        if dist is None:
+            rr.reduce()
+        else:
+            # the exchange step: every rank's per-replica partials, merged
+            rr.wait()
+            merged = shard.gather_partials(rr.partials(), device=torch.device("cuda", local))
+            pmf.pmf_free_energy_from_partials(merged, run.lambdas, run.k, run.kT)
         if ev is not None:
             ev[2].record(stream)
 

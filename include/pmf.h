@@ -235,6 +235,23 @@ pmf_status pmf_free_energy_item(const pmf_run *run, int item, pmf_free_energy_re
  * run (PMF_ESTATE otherwise). */
 pmf_status pmf_run_reduce(pmf_run *run);
 
+/* The exchange step of a run sharded over processes or GPUs (each shard
+ * runs every window with its own replicas, disjoint uids).  pmf_run_partials
+ * computes the run's per-replica partial sums on the GPU and copies them to
+ * out[capacity] (host), FP64, [window][replica][5] =
+ *   {m = min_t w_i, S = sum_t exp(-(w_i - m)/kT), n, sum_t (x - lambda_i),
+ *    sum_t (x - lambda_i)^2}
+ * with w_i of Eq. (9) (w = 0 in the last window).  Single-item runs; capacity
+ * handling as for pmf_x_samples.  Shards' partials are merged by
+ * concatenating them along the replica axis of every window (the max-shifted
+ * sums S are rescaled to a common shift inside the combination), and
+ * pmf_free_energy_from_partials turns partials[n_windows][replicas][5]
+ * (host) into every estimate of pmf_free_energy, identical to a single run
+ * over the union of the replicas up to the order of the sums. */
+pmf_status pmf_run_partials(const pmf_run *run, double *out, size_t capacity, size_t *n_written);
+pmf_status pmf_free_energy_from_partials(const double *partials, const double *lambda, int n_windows,
+                                         int replicas, double k, double kT, pmf_free_energy_result *res);
+
 /* The same reduction on caller-supplied samples x (layout of pmf_run_info
  * with `replicas` and samples_per_window[n_windows]); x is a host pointer
  * (x_on_device = 0) or a device pointer (x_on_device = 1). */

@@ -167,3 +167,86 @@ def je_all_tuples(samples_1d, lambdas, k, kT) -> float:
         terms.append(W)
     W = np.asarray(terms)
     return je_increment(W, kT)
+
+
+def window_partials(samples, lambdas, k: float, kT: float):
+    """Per-replica partial sums of every window, the quantities a shard of
+    replicas contributes to the estimators above: [s][R][5] =
+    {m = min_t w_i, S = sum_t exp(-(w_i - m)/kT), n, sum_t (x - lambda_i),
+    sum_t (x - lambda_i)^2} with w_i of Eq. (9) (0 in the last window)."""
+    lam = np.asarray(lambdas, dtype=np.float64)
+    s = lam.size
+    out = []
+    for i in range(s):
+        x = np.asarray(samples[i], dtype=np.float64)
+        if x.ndim == 1:
+            x = x[None, :]
+        ln = lam[i + 1] if i + 1 < s else lam[i]
+        rows = []
+        for r in range(x.shape[0]):
+            w = work_increment(x[r], lam[i], ln, k)
+            m = float(w.min())
+            d = x[r] - lam[i]
+            rows.append([m, math.fsum(np.exp(-(w - m) / kT).tolist()), float(x.shape[1]),
+                         math.fsum(d.tolist()), math.fsum((d * d).tolist())])
+        out.append(rows)
+    return np.asarray(out)
+
+
+def free_energy_from_partials(P, lambdas, k: float, kT: float) -> dict:
+    """The estimators of free_energy_profile from per-replica partials
+    (window_partials), e.g. the union of several shards' partials
+    concatenated along the replica axis.  Exponential sums of different
+    replicas are brought to the window's common shift m = min_r m_r before
+    they are added (log-sum-exp merge); the jackknife leaves out one
+    replica's partials."""
+    P = np.asarray(P, dtype=np.float64)
+    lam = np.asarray(lambdas, dtype=np.float64)
+    s, R = P.shape[0], P.shape[1]
+    names = ("dF_JE", "dF_fluct", "dF_G", "W_mean", "se_JE", "se_fluct", "var_ZW", "acc_force")
+    out = {n: np.zeros(s) for n in names}
+    mean_x, var_x = np.zeros(s), np.zeros(s)
+    inc = {n: np.zeros(max(s - 1, 0)) for n in ("je", "fl", "g", "w", "jje", "jfl", "vw", "n")}
+    for i in range(s):
+        m_r, S_r, n_r, a_r, b_r = (P[i, :, c] for c in range(5))
+        n = math.fsum(n_r.tolist())
+        a = math.fsum(a_r.tolist())
+        b = math.fsum(b_r.tolist())
+        mean_x[i] = lam[i] + a / n
+        var_x[i] = b / n - (a / n) ** 2
+        if i == s - 1:
+            break
+        d = lam[i + 1] - lam[i]
+        m = float(m_r.min())
+        E = S_r * np.exp(-(m_r - m) / kT)
+        inc["je"][i] = m - kT * math.log(math.fsum(E.tolist()) / n)
+        inc["fl"][i] = -k * d * a / n
+        inc["g"][i] = k * d * d / 2.0 * (1.0 - k * var_x[i] / kT) + inc["fl"][i]
+        inc["w"][i] = 0.5 * k * d * (lam[i + 1] + lam[i] - 2.0 * mean_x[i])
+        inc["vw"][i] = k * k * d * d * var_x[i]
+        inc["n"][i] = n
+        if R >= 2:
+            loo_je = [m - kT * math.log(math.fsum(np.delete(E, r).tolist()) / (n - n_r[r])) for r in range(R)]
+            loo_fl = [-k * d * (a - a_r[r]) / (n - n_r[r]) for r in range(R)]
+            inc["jje"][i] = _jackknife_var(loo_je)
+            inc["jfl"][i] = _jackknife_var(loo_fl)
+        else:
+            inc["jje"][i] = inc["jfl"][i] = math.nan
+    for j in range(1, s):
+        out["dF_JE"][j] = math.fsum(inc["je"][:j].tolist())
+        out["dF_fluct"][j] = math.fsum(inc["fl"][:j].tolist())
+        out["dF_G"][j] = math.fsum(inc["g"][:j].tolist())
+        out["W_mean"][j] = math.fsum(inc["w"][:j].tolist())
+        out["se_JE"][j] = math.sqrt(math.fsum(inc["jje"][:j].tolist()))
+        out["se_fluct"][j] = math.sqrt(math.fsum(inc["jfl"][:j].tolist()))
+        sw2 = math.fsum(inc["vw"][:j].tolist())
+        Q = float(inc["n"][:j].min())
+        out["var_ZW"][j] = zw_variance(math.sqrt(sw2), Q, kT) if Q > 1 else math.nan
+        out["acc_force"][j] = out["dF_fluct"][j] / (lam[j] - lam[0])
+    out["dF_com"] = 0.5 * (out["dF_JE"] + out["dF_fluct"])
+    out["uncertainty"] = 0.5 * (out["dF_JE"] - out["dF_fluct"])
+    out["mean_x"] = mean_x
+    out["var_x"] = var_x
+    out["gamma2"] = k * var_x / kT
+    out["lambda"] = lam.copy()
+    return out

@@ -629,6 +629,57 @@ pmf_status pmf_free_energy(const pmf_run *run, pmf_free_energy_result *res)
     return copy_result(h.data(), run->n_windows, res);
 }
 
+pmf_status pmf_run_partials(const pmf_run *run, double *out, size_t capacity, size_t *n_written)
+{
+    if (pmf_status s = need_finished(run)) return s;
+    if (run->items.size() != 1) return fail(PMF_EINVAL, "pmf_run_partials: single-item runs only");
+    const size_t need = (size_t)kPartialDoubles * run->n_windows * run->replicas;
+    if (n_written) *n_written = need;
+    if (!out || capacity < need) return fail(PMF_EINVAL, "pmf_run_partials: capacity too small");
+    const_cast<pmf_run *>(run)->reduced = false;  // the partials share the reduction scratch
+    cudaError_t e = partials_launch(layout_of(run), run->d_scratch, g_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "partials");
+    CK(cudaMemcpyAsync(out, run->d_scratch, sizeof(double) * need, cudaMemcpyDeviceToHost, g_stream), "copy");
+    CK(cudaStreamSynchronize(g_stream), "sync");
+    return PMF_OK;
+}
+
+pmf_status pmf_free_energy_from_partials(const double *partials, const double *lambda, int n_windows, int replicas,
+                                         double k, double kT, pmf_free_energy_result *res)
+{
+    if (!partials || !lambda || !res) return fail(PMF_EINVAL, "null argument");
+    if (pmf_status s = need_device()) return s;
+    if (n_windows < 2 || n_windows > kMaxRunWindows || replicas < 1 || replicas > (1 << 24))
+        return fail(PMF_EINVAL, "bad window / replica count");
+    if (res->capacity < n_windows) return fail(PMF_EINVAL, "result capacity smaller than n_windows");
+    if (!(k > 0) || !(kT > 0)) return fail(PMF_EINVAL, "need k > 0, kT > 0");
+    const size_t np = (size_t)kPartialDoubles * n_windows * replicas;
+    for (size_t i = 0; i < np; i += kPartialDoubles)
+        if (!(partials[i + 2] >= 0)) return fail(PMF_EINVAL, "partial sample counts must be >= 0");
+    struct Tmp {
+        double *lam = nullptr, *P = nullptr, *res = nullptr;
+        void *wo = nullptr;
+        ~Tmp() { cudaFree(lam); cudaFree(P); cudaFree(res); cudaFree(wo); }
+    } t;
+    CK(upload(&t.lam, lambda, n_windows), "upload lambda");
+    CK(upload(&t.P, partials, np), "upload partials");
+    CK(cudaMalloc(&t.wo, reduce_scratch_bytes(n_windows, replicas) - partial_bytes(n_windows, replicas)),
+       "alloc scratch");
+    CK(cudaMalloc(&t.res, sizeof(double) * kResFields * n_windows), "alloc results");
+    ReduceLayout L;
+    L.lambda = t.lam;
+    L.n_windows = n_windows;
+    L.replicas = replicas;
+    L.k = k;
+    L.kT = kT;
+    cudaError_t e = combine_launch(L, t.P, t.wo, t.res, g_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "combine");
+    std::vector<double> h((size_t)kResFields * n_windows);
+    CK(cudaMemcpyAsync(h.data(), t.res, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g_stream), "copy");
+    CK(cudaStreamSynchronize(g_stream), "sync");
+    return copy_result(h.data(), n_windows, res);
+}
+
 pmf_status pmf_free_energy_from_samples(const float *x, int x_on_device, const double *lambda, int n_windows,
                                         int replicas, const int64_t *samples_per_window, double k, double kT,
                                         pmf_free_energy_result *res)

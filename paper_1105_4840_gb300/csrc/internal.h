@@ -106,6 +106,15 @@ enum ResultField {
 // scratch: device buffer of reduce_scratch_bytes(); out: device [kResFields][n_windows]
 size_t reduce_scratch_bytes(int n_windows, int replicas);
 cudaError_t reduce_launch(const ReduceLayout &L, void *scratch, double *out, cudaStream_t st);
+// The two halves of reduce_launch.  Per-replica partials, 5 doubles each,
+// [window][replica]: {min w, sum exp(-(w - min)/kT), n, sum (x - lambda_i),
+// sum (x - lambda_i)^2}; combine turns them into the results (window_scratch:
+// >= reduce_scratch_bytes - partial_bytes).
+constexpr int kPartialDoubles = 5;
+size_t partial_bytes(int n_windows, int replicas);
+cudaError_t partials_launch(const ReduceLayout &L, void *partials, cudaStream_t st);
+cudaError_t combine_launch(const ReduceLayout &L, const void *partials, void *window_scratch, double *out,
+                           cudaStream_t st);
 // Allocation-free reduction: scratch in a fixed device array, equal samples
 // per window, all pointers on the device.
 constexpr int kNoAllocMaxWindows = 1024;

@@ -25,6 +25,7 @@ namespace pmf {
 struct Partial {
     double m, S, n, sdx, sdx2;
 };
+static_assert(sizeof(Partial) == kPartialDoubles * sizeof(double), "partials are exported as 5 doubles");
 struct WindowOut {
     double je, fl, g, wmean, varw, n, jk_je, jk_fl, mean, var;
 };
@@ -102,9 +103,14 @@ __global__ void __launch_bounds__(kPartialThreads) partial_kernel(const ReduceLa
 
 constexpr int kWindowThreads = 256;
 
+// Replica counts up to this keep the per-replica exponential sums E[r] in
+// shared memory; larger ones recompute them in the jackknife loops.
+constexpr int kWindowSmemReplicas = 16384;
+
+template <bool SMEM>
 __global__ void __launch_bounds__(kWindowThreads) window_kernel(const ReduceLayout L, const Partial *P, WindowOut *wo)
 {
-    extern __shared__ double E[];  // [replicas]
+    extern __shared__ double E[];  // [replicas] when SMEM
     __shared__ double red[kWindowThreads / 32 + 1];
     const int w = blockIdx.x, R = L.replicas;
     const Partial *p = P + (size_t)w * R;
@@ -118,7 +124,7 @@ __global__ void __launch_bounds__(kWindowThreads) window_kernel(const ReduceLayo
     double se = 0, ce = 0, sn = 0, s1 = 0, c1 = 0, s2 = 0, c2 = 0;
     for (int r = threadIdx.x; r < R; r += kWindowThreads) {
         const double e = p[r].n > 0 ? p[r].S * exp(-(p[r].m - m) / L.kT) : 0.0;
-        E[r] = e;
+        if (SMEM) E[r] = e;
         neumaier(se, ce, e);
         sn += p[r].n;
         neumaier(s1, c1, p[r].sdx);
@@ -141,7 +147,7 @@ __global__ void __launch_bounds__(kWindowThreads) window_kernel(const ReduceLayo
         for (int r = threadIdx.x; r < R; r += kWindowThreads) {
             double sm = 0, cm = 0;
             for (int q = 0; q < R; ++q)
-                if (q != r) neumaier(sm, cm, E[q]);
+                if (q != r) neumaier(sm, cm, SMEM ? E[q] : (p[q].n > 0 ? p[q].S * exp(-(p[q].m - m) / L.kT) : 0.0));
             const double nm = n - p[r].n;
             vje += m - L.kT * log((sm + cm) / nm);
             vfl += -L.k * d * (sdx - p[r].sdx) / nm;
@@ -154,7 +160,7 @@ __global__ void __launch_bounds__(kWindowThreads) window_kernel(const ReduceLayo
         for (int r = threadIdx.x; r < R; r += kWindowThreads) {
             double sm = 0, cm = 0;
             for (int q = 0; q < R; ++q)
-                if (q != r) neumaier(sm, cm, E[q]);
+                if (q != r) neumaier(sm, cm, SMEM ? E[q] : (p[q].n > 0 ? p[q].S * exp(-(p[q].m - m) / L.kT) : 0.0));
             const double nm = n - p[r].n;
             const double a = m - L.kT * log((sm + cm) / nm) - mje;
             const double b = -L.k * d * (sdx - p[r].sdx) / nm - mfl;
@@ -222,23 +228,41 @@ size_t reduce_scratch_bytes(int n_windows, int replicas)
     return sizeof(Partial) * (size_t)n_windows * replicas + sizeof(WindowOut) * (size_t)n_windows + 256;
 }
 
-cudaError_t reduce_launch(const ReduceLayout &L, void *scratch, double *out, cudaStream_t st)
+cudaError_t partials_launch(const ReduceLayout &L, void *P, cudaStream_t st)
 {
-    Partial *P = reinterpret_cast<Partial *>(scratch);
-    WindowOut *wo = reinterpret_cast<WindowOut *>(reinterpret_cast<char *>(scratch) +
-                                                  sizeof(Partial) * (size_t)L.n_windows * L.replicas);
-    partial_kernel<<<dim3(L.n_windows, L.replicas), kPartialThreads, 0, st>>>(L, P);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(double) * (size_t)L.replicas;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+    partial_kernel<<<dim3(L.n_windows, L.replicas), kPartialThreads, 0, st>>>(L, static_cast<Partial *>(P));
+    return cudaGetLastError();
+}
+
+cudaError_t combine_launch(const ReduceLayout &L, const void *P, void *window_scratch, double *out, cudaStream_t st)
+{
+    const Partial *pp = static_cast<const Partial *>(P);
+    WindowOut *wo = static_cast<WindowOut *>(window_scratch);
+    cudaError_t e;
+    if (L.replicas <= kWindowSmemReplicas) {
+        const size_t smem = sizeof(double) * (size_t)L.replicas;
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(window_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        window_kernel<true><<<L.n_windows, kWindowThreads, smem, st>>>(L, pp, wo);
+    } else {
+        window_kernel<false><<<L.n_windows, kWindowThreads, 0, st>>>(L, pp, wo);
     }
-    window_kernel<<<L.n_windows, kWindowThreads, smem, st>>>(L, P, wo);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     profile_kernel<<<1, 32, 0, st>>>(L, wo, out);
     return cudaGetLastError();
+}
+
+size_t partial_bytes(int n_windows, int replicas) { return sizeof(Partial) * (size_t)n_windows * replicas; }
+
+cudaError_t reduce_launch(const ReduceLayout &L, void *scratch, double *out, cudaStream_t st)
+{
+    void *P = scratch;
+    void *wo = static_cast<char *>(scratch) + partial_bytes(L.n_windows, L.replicas);
+    cudaError_t e = partials_launch(L, P, st);
+    if (e != cudaSuccess) return e;
+    return combine_launch(L, P, wo, out, st);
 }
 
 __global__ void work_increment_kernel(const ReduceLayout L, double *out)
@@ -356,17 +380,8 @@ cudaError_t reduce_noalloc_launch(const float *x, const double *lambda, int n_wi
     L.replicas = replicas;
     L.k = k;
     L.kT = kT;
-    partial_kernel<<<dim3(n_windows, replicas), kPartialThreads, 0, st>>>(L, P);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t smem = sizeof(double) * (size_t)replicas;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    window_kernel<<<n_windows, kWindowThreads, smem, st>>>(L, P, wo);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    profile_kernel<<<1, 32, 0, st>>>(L, wo, out);
-    return cudaGetLastError();
+    if ((e = partials_launch(L, P, st)) != cudaSuccess) return e;
+    return combine_launch(L, P, wo, out, st);
 }
 
 }  // namespace pmf

@@ -103,6 +103,9 @@ def _load():
     L.pmf_free_energy.argtypes = [P, C.POINTER(FreeEnergyResult)]
     L.pmf_free_energy_from_samples.argtypes = [C.c_void_p, C.c_int, _D, C.c_int, C.c_int, _I64,
                                                C.c_double, C.c_double, C.POINTER(FreeEnergyResult)]
+    L.pmf_run_partials.argtypes = [P, _D, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.pmf_free_energy_from_partials.argtypes = [_D, _D, C.c_int, C.c_int, C.c_double, C.c_double,
+                                                C.POINTER(FreeEnergyResult)]
     L.pmf_final_state.argtypes = [P, _D, _D, C.c_size_t, C.POINTER(C.c_size_t)]
     L.pmf_philox.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int,
                              C.POINTER(C.c_uint32), _F]
@@ -132,7 +135,8 @@ def _load():
     for name in ("pmf_create_system", "pmf_run_windows", "pmf_run_prepare", "pmf_run_prepare_seeded", "pmf_run_batch_prepare",
                  "pmf_free_energy_item", "pmf_run_launch",
                  "pmf_run_wait", "pmf_get_run_info", "pmf_x_samples", "pmf_work_samples",
-                 "pmf_free_energy", "pmf_free_energy_from_samples", "pmf_final_state", "pmf_philox",
+                 "pmf_free_energy", "pmf_free_energy_from_samples", "pmf_final_state",
+                 "pmf_run_partials", "pmf_free_energy_from_partials", "pmf_philox",
                  "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_free_energy_noalloc",
                  "pmf_mlp_create", "pmf_mlp_get_params", "pmf_mlp_predict", "pmf_mlp_gradient", "pmf_mlp_train",
                  "pmf_overlap", "pmf_run_adaptive", "pmf_chain_set_warps", "pmf_chain_set_grid", "pmf_chain_get_launch",
@@ -284,6 +288,14 @@ class Run:
         return _fe_call(lambda res: lib.pmf_free_energy_item(self.handle, item, C.byref(res)), n_windows,
                         "pmf_free_energy_item")
 
+    def partials(self):
+        """Per-replica partial sums [n_windows, replicas, 5] (pmf_run_partials)."""
+        n = C.c_size_t()
+        lib.pmf_run_partials(self.handle, None, 0, C.byref(n))
+        out = np.zeros(n.value)
+        _check(lib.pmf_run_partials(self.handle, _dp(out), out.size, C.byref(n)), "pmf_run_partials")
+        return out.reshape(self.lambdas.size, -1, 5)
+
     def final_state(self):
         n = C.c_size_t()
         lib.pmf_final_state(self.handle, None, None, 0, C.byref(n))
@@ -344,6 +356,15 @@ def pmf_run_windows(system: System, lambdas, params) -> Run:
         err.run = run
         raise err
     return run
+
+
+def pmf_free_energy_from_partials(partials, lambdas, k, kT):
+    """partials: [n_windows, replicas, 5] (shards concatenated on axis 1)."""
+    P = np.ascontiguousarray(partials, dtype=np.float64)
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    return _fe_call(lambda res: lib.pmf_free_energy_from_partials(_dp(P), _dp(lam), lam.size, P.shape[1], k, kT,
+                                                                  C.byref(res)), lam.size,
+                    "pmf_free_energy_from_partials")
 
 
 def pmf_free_energy_from_samples(x, lambdas, replicas, samples_per_window, k, kT, x_on_device=False):

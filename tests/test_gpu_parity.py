@@ -295,3 +295,39 @@ def test_persistent_grid_is_bit_identical(pmf, prec, per_window):
     for x, pos in out[1:]:
         assert np.array_equal(x, out[0][0])
         assert np.array_equal(pos, out[0][1])
+
+
+def test_partials_export_and_shard_merge(pmf):
+    """pmf_run_partials against the oracle's partials of the same samples;
+    combining a run's own partials reproduces pmf_free_energy bit for bit;
+    two shards (disjoint uid blocks) merged by replica concatenation equal the
+    reduction of their pooled samples."""
+    from paper_1105_4840_gb300 import shard
+
+    w = inputs.od1d_workload()
+    run = w["run"]
+    run.n_steps, run.n_equil, run.replicas = 4000, 400, 4
+    lam = np.linspace(-1.5, 1.5, 9)
+    sysh = pmf.pmf_create_system_1d(w["a"], w["x0"])
+    shards, xs = [], []
+    for rank in range(2):
+        base = shard.shard_uid_base(rank, lam.size, run.replicas)
+        rr = pmf.pmf_run_windows(sysh, lam, pmf.make_params(run, uid_base=base))
+        P = rr.partials()
+        x = rr.x_samples()
+        Po = est.window_partials([a.astype(np.float64) for a in x], lam, run.k, run.kT)
+        np.testing.assert_array_equal(P[:, :, 2], Po[:, :, 2])
+        np.testing.assert_allclose(P, Po, rtol=1e-12, atol=1e-12)
+        a = pmf.pmf_free_energy_from_partials(P, lam, run.k, run.kT)
+        b = rr.free_energy()
+        for key in a:
+            np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+        shards.append(P)
+        xs.append(x)
+    merged = shard.merge_partials(shards)
+    got = pmf.pmf_free_energy_from_partials(merged, lam, run.k, run.kT)
+    pooled = np.concatenate([np.concatenate([xs[0][i], xs[1][i]], axis=0).ravel() for i in range(lam.size)])
+    T = xs[0][0].shape[1]
+    want = pmf.pmf_free_energy_from_samples(pooled.astype(np.float32), lam, 2 * run.replicas, [T] * lam.size,
+                                            run.k, run.kT)
+    _compare_profiles(got, want, run.kT, rel=1e-11)

@@ -146,3 +146,26 @@ def test_je_increment_is_shift_invariant_and_exact():
     direct = -kT * math.log(np.mean(np.exp(-w / kT)))
     assert est.je_increment(w, kT) == pytest.approx(direct, rel=1e-12)
     assert est.je_increment(w + 1000.0, kT) == pytest.approx(direct + 1000.0, rel=1e-12)
+
+
+def test_partials_merge_equals_direct_profile():
+    """Shards' per-replica partials, concatenated along the replica axis and
+    combined with the log-sum-exp merge, reproduce every estimator computed
+    from the union of the samples (a second, independent route through the
+    same definitions: one replica dominating exp(-w/kT) included)."""
+    rng = np.random.default_rng(12)
+    lam = np.array([0.0, 0.4, 0.7, 1.3, 1.5])
+    k, kT = 30.0, 0.8
+    samples = [lam[i] - 0.05 + 0.2 * rng.standard_normal((6, 40)) for i in range(lam.size)]
+    samples[1][2, 5] = 3.0  # a far-out sample: its replica dominates the exponential sum
+    direct = est.free_energy_profile(samples, lam, k, kT)
+    shard_a = est.window_partials([x[:4] for x in samples], lam, k, kT)
+    shard_b = est.window_partials([x[4:] for x in samples], lam, k, kT)
+    merged = est.free_energy_from_partials(np.concatenate([shard_a, shard_b], axis=1), lam, k, kT)
+    for key in ("dF_JE", "dF_fluct", "dF_G", "W_mean", "dF_com", "uncertainty", "acc_force", "mean_x",
+                "var_x", "gamma2", "se_JE", "se_fluct", "var_ZW"):
+        np.testing.assert_allclose(merged[key], direct[key], rtol=1e-10, atol=1e-12, err_msg=key)
+    # partials of a single replica: the window's plain sums
+    P = est.window_partials([samples[0][:1]], lam[:1], k, kT)
+    assert P.shape == (1, 1, 5) and P[0, 0, 2] == 40
+    np.testing.assert_allclose(P[0, 0, 3], np.sum(samples[0][0] - lam[0]), rtol=1e-12)

@@ -249,6 +249,131 @@ def bench_batch(args, pmf, torch, stream):
     print(json.dumps(line), flush=True)
 
 
+def bench_precision(args, pmf, torch):
+    """FP32 vs FP64 integration on the 104-bead workload with many replicas
+    (same seeds, same uids): per window pair, the JE increments of both runs
+    and their difference in units of the combined jackknife standard error;
+    the same for the full path; the wall time of each run."""
+    w = _workload(args.md_steps)
+    p, start, run = w["params"], w["start"], w["run"]
+    run.replicas = args.replicas
+    lam = run.lambdas
+    out = {}
+    for prec, name in ((0, "fp32"), (1, "fp64")):
+        sysh = pmf.pmf_create_system_chain([p], [start], precision=prec)
+        rr = pmf.pmf_run_prepare(sysh, lam, pmf.make_params(run))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rr.launch()
+        rr.wait()
+        el = time.perf_counter() - t0
+        out[name] = {"res": rr.free_energy(), "seconds": el}
+        rr.close()
+        sysh.close()
+
+    def incr(res):
+        return np.diff(res["dF_JE"]), np.sqrt(np.maximum(np.diff(res["se_JE"] ** 2), 0.0))
+
+    j32, s32 = incr(out["fp32"]["res"])
+    j64, s64 = incr(out["fp64"]["res"])
+    z = (j32 - j64) / np.hypot(s32, s64)
+    kT = run.kT
+    e32 = (float(out["fp32"]["res"]["dF_JE"][-1]), float(out["fp32"]["res"]["se_JE"][-1]))
+    e64 = (float(out["fp64"]["res"]["dF_JE"][-1]), float(out["fp64"]["res"]["se_JE"][-1]))
+    line = {"workload": "chain104_precision", "replicas_per_window": run.replicas, "windows": int(lam.size),
+            "md_steps_per_window": run.n_steps, "kT": kT,
+            "fp32_seconds": out["fp32"]["seconds"], "fp64_seconds": out["fp64"]["seconds"],
+            "path_dF_JE": {"fp32": e32, "fp64": e64},
+            "path_diff_kT": (e32[0] - e64[0]) / kT,
+            "path_z": (e32[0] - e64[0]) / math.hypot(e32[1], e64[1]),
+            "max_abs_z": float(np.max(np.abs(z))), "max_abs_diff_kT": float(np.max(np.abs(j32 - j64)) / kT),
+            "per_window_pair": [{"pair": [float(lam[i]), float(lam[i + 1])], "dJE_fp32": float(j32[i]),
+                                 "dJE_fp64": float(j64[i]), "se_fp32": float(s32[i]), "se_fp64": float(s64[i]),
+                                 "z": float(z[i])} for i in range(lam.size - 1)]}
+    print(json.dumps(line), flush=True)
+
+
+def bench_adaptive(args, pmf, torch):
+    """GPU-seconds to a path free energy within 0.2 kT of a converged
+    reference, learned window placement (11 windows + surrogate-guided
+    insertion with seeding) against the uniform 21-window grid, over a ladder
+    of window relaxation times and several dynamics seeds."""
+    from paper_1105_4840_gb300 import inputs
+
+    out = {"workload": "chain_adaptive_vs_uniform", "criterion_kT": 0.2, "chains": []}
+    for n_beads in args.adaptive_beads:
+        aw = inputs.adaptive_workload(n_beads)
+        if args.tau_ps:
+            aw["tau_ps"] = list(args.tau_ps)
+        if args.seeds:
+            aw["seeds"] = list(args.seeds)
+        p, start, run = aw["params"], aw["start"], aw["run"]
+        kT = run.kT
+        sysh = pmf.pmf_create_system_chain([p], [start])
+
+        def steps_of(tau_ps):
+            return int(round(tau_ps / run.dt))
+
+        def timed_uniform(s, R, n_steps, seed, uid_base=0):
+            lam = np.linspace(aw["lo"], aw["hi"], s)
+            run.replicas, run.n_steps, run.n_equil, run.seed = R, n_steps, n_steps // 10, seed
+            pr = pmf.make_params(run, uid_base=uid_base)
+            rr = pmf.pmf_run_prepare(sysh, lam, pr)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            torch.cuda.synchronize()
+            ev[0].record()
+            rr.launch()
+            rr.reduce()
+            ev[1].record()
+            rr.wait()
+            torch.cuda.synchronize()
+            res = rr.free_energy()
+            rr.close()
+            return res, ev[0].elapsed_time(ev[1]) / 1000.0
+
+        # converged reference: dense uniform grid, many replicas, long windows
+        ref, ref_s = timed_uniform(aw["s_reference"], aw["replicas_reference"], args.reference_steps, 1000)
+        F_ref, se_ref = float(ref["dF_JE"][-1]), float(ref["se_JE"][-1])
+        init = pmf.pack_mlp_params(inputs.mlp_init_params(2))
+        rows = {"uniform": [], "adaptive": []}
+        for seed in aw["seeds"]:
+            for tau in aw["tau_ps"]:
+                n_steps = steps_of(tau)
+                res, gs = timed_uniform(aw["s_uniform"], 32, n_steps, seed)
+                rows["uniform"].append({"seed": seed, "tau_ps": tau, "gpu_s": gs, "windows": aw["s_uniform"],
+                                        "dF": float(res["dF_JE"][-1]), "se": float(res["se_JE"][-1])})
+                run.replicas, run.n_steps, run.n_equil, run.seed = 32, n_steps, n_steps // 10, seed
+                lam0 = np.linspace(aw["lo"], aw["hi"], aw["s_adaptive0"])
+                meta, ares = pmf.pmf_run_adaptive(sysh, lam0, pmf.make_params(run), init, threshold=0.3,
+                                                  max_rounds=3, max_windows=81, mlp_steps=400, mlp_batch=512,
+                                                  mlp_lr=3e-3, mlp_seed=5 + seed)
+                rows["adaptive"].append({"seed": seed, "tau_ps": tau, "gpu_s": meta["gpu_seconds"],
+                                         "windows": meta["n_windows"], "rounds": meta["rounds"],
+                                         "dF": float(ares["dF_JE"][-1]), "se": float(ares["se_JE"][-1])})
+
+        def summary(rs):
+            per_seed = []
+            for seed in aw["seeds"]:
+                ladder = sorted([r for r in rs if r["seed"] == seed], key=lambda r: r["tau_ps"])
+                ok = [abs(r["dF"] - F_ref) < 0.2 * kT for r in ladder]
+                first = next((i for i in range(len(ladder)) if all(ok[i:])), None)
+                per_seed.append(None if first is None else {"tau_ps": ladder[first]["tau_ps"],
+                                                            "gpu_s": ladder[first]["gpu_s"],
+                                                            "ladder_gpu_s": sum(r["gpu_s"] for r in ladder[:first + 1])})
+            got = [x["gpu_s"] for x in per_seed if x is not None]
+            return {"median_gpu_s": statistics.median(got) if got else None,
+                    "seeds_converged": len(got), "per_seed": per_seed}
+
+        out["chains"].append({"beads": n_beads, "lambda": [aw["lo"], aw["hi"]], "kT": kT,
+                              "reference": {"dF_JE": F_ref, "se": se_ref, "gpu_s": ref_s,
+                                            "windows": aw["s_reference"], "replicas": aw["replicas_reference"],
+                                            "md_steps": args.reference_steps},
+                              "uniform": summary(rows["uniform"]), "adaptive": summary(rows["adaptive"]),
+                              "runs": rows})
+        sysh.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -257,8 +382,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--md-steps", type=int, default=400000, help="BAOAB steps per window (workload: 4e5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="chain104", choices=["chain104", "batch64"],
-                    help="chain104: the 104-bead PPP (default); batch64: 64 uneven chains in one graph")
+    ap.add_argument("--workload", default="chain104", choices=["chain104", "batch64", "precision", "adaptive"],
+                    help="chain104: the 104-bead PPP (default); batch64: 64 uneven chains in one graph; "
+                         "precision: FP32 vs FP64 integration study")
+    ap.add_argument("--replicas", type=int, default=1024, help="replicas per window (precision study)")
+    ap.add_argument("--adaptive-beads", type=int, nargs="+", default=[104, 200], help="chain lengths (adaptive)")
+    ap.add_argument("--reference-steps", type=int, default=1200000, help="steps per window of the reference")
+    ap.add_argument("--tau-ps", type=float, nargs="+", default=None, help="relaxation-time ladder (adaptive)")
+    ap.add_argument("--seeds", type=int, nargs="+", default=None, help="dynamics seeds (adaptive)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -289,6 +420,14 @@ def main():
     if args.workload == "batch64":
         if world == 1:
             bench_batch(args, pmf, torch, stream)
+        return
+    if args.workload == "adaptive":
+        if world == 1:
+            bench_adaptive(args, pmf, torch)
+        return
+    if args.workload == "precision":
+        if world == 1:
+            bench_precision(args, pmf, torch)
         return
     w = _workload(args.md_steps)
     p, start, run = w["params"], w["start"], w["run"]

@@ -36,17 +36,11 @@ def silu_grad(z):
 
 
 def init_params(seed: int, scale_in: float = 1.0):
-    """He-style initial weights from a seeded generator (the CUDA side is
-    given the same arrays)."""
-    g = np.random.Generator(np.random.PCG64(seed))
-    return {
-        "W1": g.normal(0.0, math.sqrt(2.0) / scale_in, (H, 1)),
-        "b1": np.zeros(H),
-        "W2": g.normal(0.0, math.sqrt(2.0 / H), (H, H)),
-        "b2": np.zeros(H),
-        "W3": g.normal(0.0, math.sqrt(1.0 / H), (2, H)),
-        "b3": np.zeros(2),
-    }
+    """He-style initial weights from the shared seeded input generator (the
+    CUDA side is given the same arrays)."""
+    from paper_1105_4840_gb300.inputs import mlp_init_params
+
+    return mlp_init_params(seed, H, scale_in)
 
 
 def forward(p, lam):

@@ -212,6 +212,41 @@ def batch_workload(n_chains: int = 64, n_min: int = 40, n_max: int = 400, w_min:
     return {"params": params, "starts": starts, "lambdas": lams, "run": run}
 
 
+def adaptive_workload(n_beads: int = 104, param_seed: int | None = None) -> dict:
+    """Learned window placement against the uniform grid: an n-bead chain
+    (parameter seed 1 for 104 beads, 2 otherwise) pulled from lo to hi =
+    (1.3, 3.3) nm x sqrt(n / 104) with the 104-bead workload's trap,
+    temperature and integrator; the adaptive protocol starts from 11 uniform
+    windows, the uniform protocol uses 21; 32 replicas per window; window
+    relaxation times tau of 0.05, 0.1, 0.2, 0.4, 0.8 ns; dynamics seeds 0..4;
+    the converged reference is 81 uniform windows x 64 replicas."""
+    ps = param_seed if param_seed is not None else (1 if n_beads == 104 else 2)
+    p = chain_params(n_beads, ps)
+    scale = math.sqrt(n_beads / 104.0)
+    lo, hi = 1.3 * scale, 3.3 * scale
+    start = chain_start(p, ps + 1000, target_x=lo)
+    run = RunSettings(k=500.0, kT=kT_of(300.0), dt=0.001, gamma=5.0, n_steps=0, n_equil=0, stride=100,
+                      replicas=32, seed=0)
+    return {"params": p, "start": start, "lo": lo, "hi": hi, "run": run,
+            "tau_ps": [50.0, 100.0, 200.0, 400.0, 800.0], "seeds": [0, 1, 2, 3, 4],
+            "s_uniform": 21, "s_adaptive0": 11, "s_reference": 81, "replicas_reference": 64}
+
+
+def mlp_init_params(seed: int, hidden: int = 64, scale_in: float = 1.0) -> dict:
+    """Seeded He-style initial weights of the surrogate 1 -> hidden -> hidden
+    -> 2 network (W1 [hidden, 1], b1, W2 [hidden, hidden], b2, W3 [2, hidden],
+    b3), FP64; both the oracle and the CUDA side start from these arrays."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    return {
+        "W1": g.normal(0.0, math.sqrt(2.0) / scale_in, (hidden, 1)),
+        "b1": np.zeros(hidden),
+        "W2": g.normal(0.0, math.sqrt(2.0 / hidden), (hidden, hidden)),
+        "b2": np.zeros(hidden),
+        "W3": g.normal(0.0, math.sqrt(1.0 / hidden), (2, hidden)),
+        "b3": np.zeros(2),
+    }
+
+
 def gaussian_x_samples(lambdas, k, kT, replicas, samples, seed, *, shift=0.3, gamma2=1.2):
     """Synthetic FP32 reaction-coordinate samples [s][R][T]: Gaussian around
     lambda_i - shift * (i % 3) / 3 with variance gamma2 * kT / k.  Used to feed

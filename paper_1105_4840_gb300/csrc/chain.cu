@@ -125,20 +125,25 @@ __device__ __forceinline__ void store_pos(const Smem<R> &s, int b, V3<R> p, R si
     s.posd[t * 64 + i + W] = v;
 }
 
-// The packed copy: ring position i of tile t is the first element of
-// entries i and i + W and the second element of entries (i - D) mod W and
-// that + W.
-__device__ __forceinline__ void store_posp(const Smem<float> &s, int b, V3<float> p, int n_tiles, int w_last)
+// The packed copy of one tile, rebuilt by the warp that owns the tile after
+// its positions moved: lane e < W writes entries e and e + W from its own
+// bead (ring position e) and the bead at ring position e + D, fetched with a
+// shuffle; every lane of the warp takes part (lanes >= W only supply data).
+__device__ __forceinline__ void pack_tile(const Smem<float> &s, int t, int lane, int W, V3<float> p, float sig)
 {
-    const int t = b >> 5, i = b & 31, W = tile_width(t, n_tiles, w_last), D = pair_offset(W);
-    float *base = reinterpret_cast<float *>(s.posp + 2 * 64 * t);
-    const int q = (i - D) & (W - 1);
-#pragma unroll
-    for (int rep = 0; rep < 2; ++rep) {
-        float *e1 = base + 8 * (i + rep * W);  // first element of entry i (+W)
-        e1[0] = p.x; e1[2] = p.y; e1[4] = p.z;
-        float *e2 = base + 8 * (q + rep * W);  // second element of entry q (+W)
-        e2[1] = p.x; e2[3] = p.y; e2[5] = p.z;
+    const int D = pair_offset(W);
+    const int src = (lane + D) & (W - 1);
+    const float qx = __shfl_sync(0xffffffffu, p.x, src);
+    const float qy = __shfl_sync(0xffffffffu, p.y, src);
+    const float qz = __shfl_sync(0xffffffffu, p.z, src);
+    const float qs = __shfl_sync(0xffffffffu, sig, src);
+    if (lane < W) {
+        float4 *base = s.posp + 2 * 64 * t;
+        const float4 lo = make_float4(p.x, qx, p.y, qy), hi = make_float4(p.z, qz, sig, qs);
+        base[2 * lane] = lo;
+        base[2 * lane + 1] = hi;
+        base[2 * (lane + W)] = lo;
+        base[2 * (lane + W) + 1] = hi;
     }
 }
 
@@ -264,9 +269,13 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // diagonal tile).  Four pairs per lane and step share one set of j loads and
 // one rotation (by two lanes) of the j-force streams, halving the shared
 // loads and shuffles per pair; the two i-beads form the packed f32x2 operand.
-template <int W>
-__device__ __forceinline__ void quad_piece(const Smem<float> &s, Vec4<float> *fw, int I, int J, int TB, int NST,
-                                           bool diag, bool near, int wI, int lane)
+//
+// SPLIT pieces jump from ring step TB + 6 to TB + 16 halfway (offsets 0..15
+// then 16..31 of an off-diagonal W 32 ring in one piece): the j-force streams
+// then rotate by ten lanes once instead of two.
+template <int W, int NST, bool SPLIT>
+__device__ __forceinline__ void quad_piece(const Smem<float> &s, Vec4<float> *fw, int I, int J, int TB, bool diag,
+                                           bool near, int wI, int lane)
 {
     constexpr int D = pair_offset(W);
     const int lr = lane & (W - 1);
@@ -287,12 +296,13 @@ __device__ __forceinline__ void quad_piece(const Smem<float> &s, Vec4<float> *fw
     const float4 *A = s.posp + 2 * (64 * J + lr);
     const float4 *E = s.eqp + 64 * J + lr;
     const int src = (lane & ~(W - 1)) | ((lr + 2) & (W - 1));
+    const int src_jump = (lane & ~(W - 1)) | ((lr + 10) & (W - 1));
     const int gi1 = I * 32 + lane, gi2 = I * 32 + l2;
     const bool mask_near = near && TB < 4;
     const bool mask_half = diag && lr >= (W >> 1);
-#pragma unroll 2
+#pragma unroll
     for (int k = 0; k < NST; ++k) {
-        const int t = TB + 2 * k;
+        const int t = TB + 2 * k + ((SPLIT && 2 * k >= NST) ? 8 : 0);
         const float4 a = A[2 * t], b = A[2 * t + 1], e = E[t];
         const float2 xj = f2(a.x, a.y), yj = f2(a.z, a.w), zj = f2(b.x, b.y), sj = f2(b.z, b.w);
         const float2 ej = f2(e.x, e.y), cj = f2(e.z, e.w);
@@ -324,12 +334,13 @@ __device__ __forceinline__ void quad_piece(const Smem<float> &s, Vec4<float> *fw
         fjx = __ffma2_rn(fr1, dx1, fjx); fjy = __ffma2_rn(fr1, dy1, fjy); fjz = __ffma2_rn(fr1, dz1, fjz);
         fjx = __ffma2_rn(fr2, dx2, fjx); fjy = __ffma2_rn(fr2, dy2, fjy); fjz = __ffma2_rn(fr2, dz2, fjz);
         if (k + 1 < NST) {
-            fjx.x = __shfl_sync(0xffffffffu, fjx.x, src);
-            fjx.y = __shfl_sync(0xffffffffu, fjx.y, src);
-            fjy.x = __shfl_sync(0xffffffffu, fjy.x, src);
-            fjy.y = __shfl_sync(0xffffffffu, fjy.y, src);
-            fjz.x = __shfl_sync(0xffffffffu, fjz.x, src);
-            fjz.y = __shfl_sync(0xffffffffu, fjz.y, src);
+            const int sl = (SPLIT && 2 * (k + 1) == NST) ? src_jump : src;
+            fjx.x = __shfl_sync(0xffffffffu, fjx.x, sl);
+            fjx.y = __shfl_sync(0xffffffffu, fjx.y, sl);
+            fjy.x = __shfl_sync(0xffffffffu, fjy.x, sl);
+            fjy.y = __shfl_sync(0xffffffffu, fjy.y, sl);
+            fjz.x = __shfl_sync(0xffffffffu, fjz.x, sl);
+            fjz.y = __shfl_sync(0xffffffffu, fjz.y, sl);
         }
     }
     if (on1) {
@@ -349,7 +360,7 @@ __device__ __forceinline__ void quad_piece(const Smem<float> &s, Vec4<float> *fw
         fjz.x += __shfl_xor_sync(0xffffffffu, fjz.x, o); fjz.y += __shfl_xor_sync(0xffffffffu, fjz.y, o);
     }
     if (lane < W) {
-        const int tl = TB + 2 * (NST - 1);
+        const int tl = TB + 2 * (NST - 1) + (SPLIT ? 8 : 0);
         const int ba = J * 32 + ((lr + tl) & (W - 1));
         Vec4<float> f = fw[ba];
         f.x += fjx.x; f.y += fjy.x; f.z += fjz.x;
@@ -412,6 +423,7 @@ __device__ __noinline__ void ragged_diag_piece(const Smem<float> &s, Vec4<float>
 
 // Piece kinds of the packed FP32 path (quad pieces):
 //   21: W 32, t = 1, 3, 5, 7 (+8)      22: W 32, t = 17, 19, 21, 23 (+8)
+//   26: W 32, t = 1, 3, 5, 7, 17, 19, 21, 23 (+8): 21 and 22 in one piece
 //   23: W 32 diagonal, t = 2, 4, 6, 8 (+8)
 //   24: W 16, t = 1, 3, 5, 7 (+8)       25: W 8, t = 1, 3 (+4)
 //   8, 10: diagonal of a ragged tile of width 16 / 8, scalar
@@ -419,11 +431,12 @@ __device__ __forceinline__ void run_packed_piece(const Smem<float> &s, Vec4<floa
                                                  bool near, int wI, int lane)
 {
     switch (kind) {
-    case 21: quad_piece<32>(s, fw, I, J, 1, 4, false, near, wI, lane); break;
-    case 22: quad_piece<32>(s, fw, I, J, 17, 4, false, near, wI, lane); break;
-    case 23: quad_piece<32>(s, fw, I, J, 2, 4, true, near, wI, lane); break;
-    case 24: quad_piece<16>(s, fw, I, J, 1, 4, false, near, wI, lane); break;
-    case 25: quad_piece<8>(s, fw, I, J, 1, 2, false, near, wI, lane); break;
+    case 21: quad_piece<32, 4, false>(s, fw, I, J, 1, false, near, wI, lane); break;
+    case 22: quad_piece<32, 4, false>(s, fw, I, J, 17, false, near, wI, lane); break;
+    case 23: quad_piece<32, 4, false>(s, fw, I, J, 2, true, near, wI, lane); break;
+    case 24: quad_piece<16, 4, false>(s, fw, I, J, 1, false, near, wI, lane); break;
+    case 26: quad_piece<32, 8, true>(s, fw, I, J, 1, false, near, wI, lane); break;
+    case 25: quad_piece<8, 2, false>(s, fw, I, J, 1, false, near, wI, lane); break;
     case 8: ragged_diag_piece(s, fw, J, 16, lane); break;
     case 10: ragged_diag_piece(s, fw, J, 8, lane); break;
     default: break;  // the host schedule emits only the kinds above
@@ -528,29 +541,43 @@ __device__ __forceinline__ R bonded_owner(const ChainArgs<R> &a, const Smem<R> &
 }
 
 // Normals of O-step `step`: block b of Philox counter (b, uid, step, 0)
-// gives dofs 4b..4b+3 (dof d = 3 bead + axis).  Generated by the threads at
-// the top of the CTA, which own few bonded terms.
-template <typename R, int NW>
-__device__ __forceinline__ void gen_noise(const ChainArgs<R> &a, const Smem<R> &s, uint32_t uid, uint32_t step)
+// gives dofs 4b..4b+3 (dof d = 3 bead + axis), stored in the noise buffer
+// of the step's parity (two buffers: the next step's normals are drawn while
+// the current step's are read).  Blocks [b0, b1) are spread over n_thr
+// threads, this thread being number `ti`.
+template <typename R>
+__device__ __forceinline__ void gen_noise(const ChainArgs<R> &a, const Smem<R> &s, uint32_t uid, long long step,
+                                          int b0, int b1, int ti, int n_thr)
 {
-    const int nblk = (3 * a.N + 3) >> 2;
-    for (int b = NW * 32 - 1 - (int)threadIdx.x; b < nblk; b += NW * 32) {
-        const Normal4<R> n = philox_normals<R>(a.seed, (uint32_t)b, uid, step, kTagOStep);
-        reinterpret_cast<Vec4<R> *>(s.noise)[b] = Vec4<R>{n.n0, n.n1, n.n2, n.n3};
+    Vec4<R> *buf = reinterpret_cast<Vec4<R> *>(s.noise) + (step & 1) * ((3 * a.N + 3) >> 2);
+    for (int b = b0 + ti; b < b1; b += n_thr) {
+        const Normal4<R> n = philox_normals<R>(a.seed, (uint32_t)b, uid, (uint32_t)step, kTagOStep);
+        buf[b] = Vec4<R>{n.n0, n.n1, n.n2, n.n3};
     }
+}
+
+// The first `early` noise blocks of the next step are drawn during the
+// position update by the warps that own no tile (one block per thread); the
+// rest during the force phase by the threads at the top of the CTA, which own
+// few bonded terms.
+__host__ __device__ __forceinline__ int early_noise_blocks(int N, int n_tiles, int NW)
+{
+    const int nblk = (3 * N + 3) / 4, idle = NW > n_tiles ? NW - n_tiles : 0;
+    return idle * 32 < nblk ? idle * 32 : nblk;
 }
 
 template <typename R, int NW>
 __device__ __forceinline__ void force_phase(const ChainArgs<R> &a, const Smem<R> &s, R lam, long long done,
-                                            long long nequil, long long sample_base, bool sample, uint32_t uid)
+                                            long long nequil, long long sample_base, bool first, uint32_t uid)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    gen_noise<R, NW>(a, s, uid, (uint32_t)done);
+    gen_noise<R>(a, s, uid, done, first ? 0 : early_noise_blocks(a.N, a.n_tiles, NW), (3 * a.N + 3) >> 2,
+                 NW * 32 - 1 - tid, NW * 32);
     for (int t = tid; t < a.N; t += NW * 32) {
         const R x = bonded_owner(a, s, t, lam);
         if (t == a.N - 1) {
             if (!(x == x) || x > R(1e30)) *s.flag = 1;
-            if (sample && done > nequil && (done - nequil) % a.stride == 0)
+            if (!first && done > nequil && (done - nequil) % a.stride == 0)
                 a.xout[sample_base + (done - nequil) / a.stride - 1] = (float)x;
         }
     }
@@ -658,45 +685,66 @@ __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s
     }
     const long long nequil = a.nequil_w[w];
     const long long sample_base = a.off_w[w] + (long long)r * a.tw[w];
-    force_phase<R, NW>(a, s, lam, s0, nequil, sample_base, false, uid);
+    force_phase<R, NW>(a, s, lam, s0, nequil, sample_base, true, uid);
     __syncthreads();
 
+    const int warp = tid >> 5, lane = tid & 31;
     for (long long step = s0;; ++step) {
-        for (int b = tid; b < a.N; b += NW * 32) {
-            Vec4<R> F = s.bslot[b];
-            if (b >= 1) { const Vec4<R> q = s.bslot[a.Np + b - 1]; F.x += q.x; F.y += q.y; F.z += q.z; }
-            if (b >= 2) { const Vec4<R> q = s.bslot[2 * a.Np + b - 2]; F.x += q.x; F.y += q.y; F.z += q.z; }
-            if (b >= 3) { const Vec4<R> q = s.bslot[3 * a.Np + b - 3]; F.x += q.x; F.y += q.y; F.z += q.z; }
+        // one warp per 32-bead tile (warp-uniform loop: the packed copy is
+        // rebuilt with shuffles by the whole warp)
+        for (int tile = warp; tile < a.n_tiles; tile += NW) {
+            const int b = tile * 32 + lane;
+            V3<R> pnew{R(0), R(0), R(0)};
+            R sig = R(0);
+            if (kPacked<R> && step < s1 && b >= a.N && lane < tile_width(tile, a.n_tiles, a.w_last)) {
+                const Vec4<R> pad = s.posd[tile * 64 + lane];  // pads never move
+                pnew = V3<R>{pad.x, pad.y, pad.z};
+                sig = pad.w;
+            }
+            if (b < a.N) {
+                Vec4<R> F = s.bslot[b];
+                if (b >= 1) { const Vec4<R> q = s.bslot[a.Np + b - 1]; F.x += q.x; F.y += q.y; F.z += q.z; }
+                if (b >= 2) { const Vec4<R> q = s.bslot[2 * a.Np + b - 2]; F.x += q.x; F.y += q.y; F.z += q.z; }
+                if (b >= 3) { const Vec4<R> q = s.bslot[3 * a.Np + b - 3]; F.x += q.x; F.y += q.y; F.z += q.z; }
 #pragma unroll
-            for (int q = 0; q < NW; ++q) {
-                const Vec4<R> g = s.fw[q * a.Np + b];
-                F.x += g.x; F.y += g.y; F.z += g.z;
-                s.fw[q * a.Np + b] = Vec4<R>{0, 0, 0, 0};
+                for (int q = 0; q < NW; ++q) {
+                    const Vec4<R> g = s.fw[q * a.Np + b];
+                    F.x += g.x; F.y += g.y; F.z += g.z;
+                    s.fw[q * a.Np + b] = Vec4<R>{0, 0, 0, 0};
+                }
+                const R im = a.bead_invm[b];
+                Vec4<R> v = s.vel[b];
+                if (step > s0) { v.x += hdt * F.x * im; v.y += hdt * F.y * im; v.z += hdt * F.z * im; }
+                if (step < s1) {
+                    V3<R> p = pos_of(s, b);
+                    v.x += hdt * F.x * im; v.y += hdt * F.y * im; v.z += hdt * F.z * im;
+                    p.x += hdt * v.x; p.y += hdt * v.y; p.z += hdt * v.z;
+                    const R sv = c2 * sqrt(a.kT * im);
+                    const R *xi = s.noise + (step & 1) * 4 * ((3 * a.N + 3) >> 2) + 3 * b;
+                    v.x = c1 * v.x + sv * xi[0];
+                    v.y = c1 * v.y + sv * xi[1];
+                    v.z = c1 * v.z + sv * xi[2];
+                    p.x += hdt * v.x; p.y += hdt * v.y; p.z += hdt * v.z;
+                    sig = a.bead_pos0[b].w;
+                    store_pos<R>(s, b, p, sig, a.n_tiles, a.w_last);
+                    pnew = p;
+                } else if (a.force_out != nullptr) {
+                    a.force_out[3 * b + 0] = (double)F.x;
+                    a.force_out[3 * b + 1] = (double)F.y;
+                    a.force_out[3 * b + 2] = (double)F.z;
+                }
+                s.vel[b] = v;
             }
-            const R im = a.bead_invm[b];
-            Vec4<R> v = s.vel[b];
-            if (step > s0) { v.x += hdt * F.x * im; v.y += hdt * F.y * im; v.z += hdt * F.z * im; }
-            if (step < s1) {
-                V3<R> p = pos_of(s, b);
-                v.x += hdt * F.x * im; v.y += hdt * F.y * im; v.z += hdt * F.z * im;
-                p.x += hdt * v.x; p.y += hdt * v.y; p.z += hdt * v.z;
-                const R sv = c2 * sqrt(a.kT * im);
-                v.x = c1 * v.x + sv * s.noise[3 * b + 0];
-                v.y = c1 * v.y + sv * s.noise[3 * b + 1];
-                v.z = c1 * v.z + sv * s.noise[3 * b + 2];
-                p.x += hdt * v.x; p.y += hdt * v.y; p.z += hdt * v.z;
-                store_pos<R>(s, b, p, a.bead_pos0[b].w, a.n_tiles, a.w_last);
-                if constexpr (kPacked<R>) store_posp(s, b, p, a.n_tiles, a.w_last);
-            } else if (a.force_out != nullptr) {
-                a.force_out[3 * b + 0] = (double)F.x;
-                a.force_out[3 * b + 1] = (double)F.y;
-                a.force_out[3 * b + 2] = (double)F.z;
+            if constexpr (kPacked<R>) {
+                if (step < s1) pack_tile(s, tile, lane, tile_width(tile, a.n_tiles, a.w_last), pnew, sig);
             }
-            s.vel[b] = v;
         }
+        if (warp >= a.n_tiles && step + 1 < s1)
+            gen_noise<R>(a, s, uid, step + 1, 0, early_noise_blocks(a.N, a.n_tiles, NW), tid - a.n_tiles * 32,
+                         (NW - a.n_tiles) * 32);
         if (step >= s1) break;
         __syncthreads();
-        force_phase<R, NW>(a, s, lam, step + 1, nequil, sample_base, true, uid);
+        force_phase<R, NW>(a, s, lam, step + 1, nequil, sample_base, false, uid);
         __syncthreads();
         if (*s.flag) {
             if (tid == 0) atomicOr(a.err, kErrNonFinite);
@@ -781,7 +829,7 @@ __global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW =
         s.vel = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np;
         s.fw = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * NW;
         s.bslot = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * 4;
-        s.noise = reinterpret_cast<R *>(p); p += sizeof(Vec4<R>) * ((3 * a.N + 3) >> 2);
+        s.noise = reinterpret_cast<R *>(p); p += 2 * sizeof(Vec4<R>) * ((3 * a.N + 3) >> 2);
         s.posp = nullptr;
         s.eqp = nullptr;
         if constexpr (kPacked<R>) {
@@ -864,8 +912,7 @@ std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed)
         for (int I = 0; I < J; ++I) {
             const int nr = J - I == 1 ? 1 : 0;
             if (W == 32) {
-                all.push_back(P{UnitDesc{I, -1, J, 21, nr, 0}, 4 * 75.0 + 60.0});
-                all.push_back(P{UnitDesc{I, -1, J, 22, nr, 0}, 4 * 75.0 + 60.0});
+                all.push_back(P{UnitDesc{I, -1, J, 26, nr, 0}, 8 * 75.0 + 60.0});
             } else if (W == 16) {
                 all.push_back(P{UnitDesc{I, -1, J, 24, nr, 0}, 4 * 75.0 + 70.0});
             } else {
@@ -900,8 +947,10 @@ std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed)
     std::vector<double> load(NW, 0.0);
     const int nt = NW * 32;
     for (int w = 0; w < NW; ++w) {
-        // bonded owners are threads 0..N-1, noise blocks run on threads nt-1 downwards
-        const int nblk = (3 * N + 3) / 4;
+        // bonded owners are threads 0..N-1; the noise blocks left for the
+        // force phase (after those drawn during the update) run on threads
+        // nt-1 downwards
+        const int nblk = (3 * N + 3) / 4 - early_noise_blocks(N, g.n_tiles, NW);
         for (int pass = 0; pass * nt < N; ++pass)
             if (w * 32 < N - pass * nt) load[w] += 400.0;
         for (int pass = 0; pass * nt < nblk; ++pass) {
@@ -922,7 +971,7 @@ std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed)
 template <typename R> size_t chain_smem_bytes(const ChainGeometry &g, int NW)
 {
     size_t b = sizeof(Vec4<R>) * g.n_tiles * 64 + sizeof(Vec2<R>) * g.n_tiles * 64 + sizeof(Vec4<R>) * g.Np * (1 + NW + 4) +
-               sizeof(Vec4<R>) * ((3 * g.N + 3) / 4) + 16;
+               2 * sizeof(Vec4<R>) * ((3 * g.N + 3) / 4) + 16;
     if (kPacked<R>) b += sizeof(float4) * 3 * 64 * g.n_tiles;
     return b;
 }

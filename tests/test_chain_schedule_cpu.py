@@ -24,7 +24,8 @@ KINDS = {0: (32, 0, 8, 0, 0), 1: (32, 8, 8, 0, 0), 2: (32, 16, 8, 0, 0), 3: (32,
          4: (32, 1, 8, 1, 0), 5: (32, 9, 8, 1, 0), 6: (16, 0, 8, 0, 0), 7: (16, 8, 8, 0, 0),
          8: (16, 1, 8, 1, 0), 9: (8, 0, 8, 0, 0), 10: (8, 1, 4, 1, 0),
          21: (32, 1, 4, 0, 8), 22: (32, 17, 4, 0, 8), 23: (32, 2, 4, 1, 8), 24: (16, 1, 4, 0, 8),
-         25: (8, 1, 2, 0, 4)}
+         25: (8, 1, 2, 0, 4), 26: (32, 1, 8, 0, 8)}
+SPLIT = {26}  # quad kinds whose ring steps jump by 10 halfway (t = 1..7, then 17..23)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -44,7 +45,7 @@ def test_ring_pieces_cover_pairs_once(N, NW, precision):
         W, TB, NST, DIAG, DP = KINDS[kind]
         assert (kind >= 21 or kind in (8, 10)) if precision == 0 else kind <= 10
         if DP:
-            _quad_piece(count, N, Np, n_tiles, w_last, I1, J, near1, W, TB, NST, DIAG, DP)
+            _quad_piece(count, N, Np, n_tiles, w_last, I1, J, near1, W, TB, NST, DIAG, DP, kind in SPLIT)
             continue
         assert W == _width(J, n_tiles, w_last)
         assert bool(DIAG) == (I1 == J)
@@ -90,23 +91,26 @@ def test_ring_pieces_cover_pairs_once(N, NW, precision):
     np.testing.assert_array_equal(count, want)
 
 
-def _quad_piece(count, N, Np, n_tiles, w_last, I, J, near, W, TB, NST, DIAG, D):
+def _quad_piece(count, N, Np, n_tiles, w_last, I, J, near, W, TB, NST, DIAG, D, split=False):
     """Replay of quad_piece: lane l holds i1 at ring index l and i2 at l + 1;
-    step k (t = TB + 2k) pairs both with ring positions l + t (stream a) and
-    l + t + D (stream b); both j-force streams rotate by two lanes."""
+    step k (t = TB + 2k, plus 8 in the second half of a split piece) pairs
+    both with ring positions l + t (stream a) and l + t + D (stream b); both
+    j-force streams rotate by the step's increment of t."""
     assert D == (8 if W == 32 else W // 2)
     lanes = np.arange(32)
     lr = lanes & (W - 1)
     l2 = (lanes & ~(W - 1)) | ((lr + 1) & (W - 1))
     assert sorted(l2) == list(range(32))  # a permutation: the i2 flush hits distinct beads
-    src = (lanes & ~(W - 1)) | ((lr + 2) & (W - 1))
+    def t_of(k):
+        return TB + 2 * k + (8 if split and 2 * k >= NST else 0)
+
     acc_a = (lr + TB) & (W - 1)
     acc_b = (lr + TB + D) & (W - 1)
     wI = _width(I, n_tiles, w_last)
     gi1, gi2 = I * 32 + lanes, I * 32 + l2
     on1, on2 = lanes < wI, l2 < wI
     for k in range(NST):
-        t = TB + 2 * k
+        t = t_of(k)
         assert (lr + t).max() < 2 * W  # packed entry index p = lr + t
         for stream, tt, acc in (("a", t, acc_a), ("b", t + D, acc_b)):
             assert np.all(acc == ((lr + tt) & (W - 1)))
@@ -123,8 +127,9 @@ def _quad_piece(count, N, Np, n_tiles, w_last, I, J, near, W, TB, NST, DIAG, D):
                 for a, b in zip(gi[ok], j[ok]):
                     count[min(a, b), max(a, b)] += 1
         if k + 1 < NST:
+            src = (lanes & ~(W - 1)) | ((lr + t_of(k + 1) - t) & (W - 1))
             acc_a, acc_b = acc_a[src], acc_b[src]
-    tl = TB + 2 * (NST - 1)
+    tl = t_of(NST - 1)
     fa = (lr + tl) & (W - 1)
     fb = (lr + tl + D) & (W - 1)
     assert np.all(acc_a == fa) and np.all(acc_b == fb)

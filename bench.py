@@ -438,7 +438,7 @@ def main():
     uid_base = shard_uid_base(rank, s, R)
     sysh = pmf.pmf_create_system_chain([p], [start])
     # untimed setup: pick warps per replica from short probes of this run
-    warps, _ = pmf.pmf_chain_autotune(sysh, run.lambdas, pmf.make_params(run, uid_base=uid_base), probe_steps=2000)
+    warps, _ = pmf.pmf_chain_autotune(sysh, run.lambdas, pmf.make_params(run, uid_base=uid_base), probe_steps=10000)
     _, grid_ctas, seg_steps = pmf.pmf_chain_get_launch(sysh, 0)
     rr = pmf.pmf_run_prepare(sysh, run.lambdas, pmf.make_params(run, uid_base=uid_base))
     replica_steps = n_rep * run.n_steps

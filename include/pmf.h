@@ -313,7 +313,9 @@ pmf_status pmf_chain_set_grid(pmf_system *sys, int chain, int ctas, int seg_step
  * by the calls above or chosen by pmf_chain_autotune); NULL outputs skipped. */
 pmf_status pmf_chain_get_launch(const pmf_system *sys, int chain, int *warps, int *ctas, int *seg_steps);
 /* Time probe_steps steps of the given run (every window and replica, one
- * warm-up launch each) for each warp count and each of two persistent
+ * warm-up launch and the best of two timed launches each; use several
+ * thousand steps so the persistent segments dominate the launch tail) for
+ * each warp count and each of two persistent
  * launch shapes (ctas = 0 and ctas = one per replica, see
  * pmf_chain_set_grid) and keep the fastest; *best_warps and *best_ms (may
  * be NULL) report the warp count chosen and its probe time. */

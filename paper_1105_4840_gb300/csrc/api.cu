@@ -1183,14 +1183,17 @@ pmf_status pmf_chain_autotune(pmf_system *sys, const double *lambda, int n_windo
         if (pmf_chain_set_warps(sys, p->chain, cand_fp32[c]) != PMF_OK) continue;
         for (int gsel = 0; gsel < 2; ++gsel) {
             if (m.set_grid(grids[gsel], seg) != cudaSuccess) continue;
-            if (pmf_status s = pmf_run_launch(run)) return s;  // warm-up
+            if (pmf_status s = pmf_run_launch(run)) return s;  // warm-up (and graph capture)
             if (pmf_status s = pmf_run_wait(run)) return s;
-            const double before = timer.ms;
-            timer.start();
-            if (pmf_status s = pmf_run_launch(run)) return s;
-            CK(timer.stop(), "autotune timer");
-            if (pmf_status s = pmf_run_wait(run)) return s;
-            const double t = timer.ms - before;
+            double t = 1e300;
+            for (int rep = 0; rep < 2; ++rep) {  // best of two timed launches
+                const double before = timer.ms;
+                timer.start();
+                if (pmf_status s = pmf_run_launch(run)) return s;
+                CK(timer.stop(), "autotune timer");
+                if (pmf_status s = pmf_run_wait(run)) return s;
+                t = std::min(t, timer.ms - before);
+            }
             if (t < best_t) {
                 best_t = t;
                 best = cand_fp32[c];

@@ -374,6 +374,42 @@ def bench_adaptive(args, pmf, torch):
     print(json.dumps(out), flush=True)
 
 
+def bench_mlp(args, pmf, torch, stream):
+    """Surrogate training throughput: Adam steps of the 1 -> 64 -> 64 -> 2
+    network (64 x 64 layer on tcgen05, BF16 operands, FP32 accumulators in
+    TMEM) on mini-batches drawn from a 1D run's sample store."""
+    from paper_1105_4840_gb300 import inputs
+
+    w = inputs.od1d_workload()
+    run = w["run"]
+    sysh = pmf.pmf_create_system_1d(w["a"], w["x0"])
+    rr = pmf.pmf_run_windows(sysh, run.lambdas, pmf.make_params(run))
+    lam = run.lambdas
+    mlp = pmf.Mlp(pmf.pack_mlp_params(inputs.mlp_init_params(2)), 0.5 * (lam[0] + lam[-1]),
+                  0.5 * (lam[-1] - lam[0]))
+    batch, steps = args.mlp_batch, args.mlp_steps
+    for _ in range(args.warmup):
+        mlp.train(rr, 50, batch, 3e-3, 1)
+    times = []
+    for i in range(args.steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        loss = mlp.train(rr, steps, batch, 3e-3, 100 + i)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        times.append(e[0].elapsed_time(e[1]) / 1000.0)
+    t = statistics.median(times)
+    tiles = (batch + 127) // 128
+    flops = steps * tiles * 3 * 2 * 128 * 64 * 64  # Z2, dH1, dW2 of the 64 x 64 layer
+    peak = float(_peaks().get("bf16_tflops", 1939.8))
+    line = {"workload": "surrogate_training", "metric": "adam_steps/s", "value": steps / t, "unit": "steps/s",
+            "batch": batch, "steps_per_launch": steps, "samples_per_s": steps * batch / t,
+            "us_per_step": 1e6 * t / steps, "loss": loss, "ctas": 1,
+            "tensor": {"achieved": flops / t / 1e12, "unit": "TFLOP/s", "peak": peak,
+                       "frac": flops / t / 1e12 / peak, "note": "one CTA by design; latency bound"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,10 +418,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--md-steps", type=int, default=400000, help="BAOAB steps per window (workload: 4e5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="chain104", choices=["chain104", "batch64", "precision", "adaptive"],
+    ap.add_argument("--workload", default="chain104",
+                    choices=["chain104", "batch64", "precision", "adaptive", "mlp"],
                     help="chain104: the 104-bead PPP (default); batch64: 64 uneven chains in one graph; "
                          "precision: FP32 vs FP64 integration study")
     ap.add_argument("--replicas", type=int, default=1024, help="replicas per window (precision study)")
+    ap.add_argument("--mlp-steps", type=int, default=2000, help="Adam steps per timed launch (mlp)")
+    ap.add_argument("--mlp-batch", type=int, default=512, help="mini-batch (mlp)")
     ap.add_argument("--adaptive-beads", type=int, nargs="+", default=[104, 200], help="chain lengths (adaptive)")
     ap.add_argument("--reference-steps", type=int, default=1200000, help="steps per window of the reference")
     ap.add_argument("--tau-ps", type=float, nargs="+", default=None, help="relaxation-time ladder (adaptive)")
@@ -420,6 +459,10 @@ def main():
     if args.workload == "batch64":
         if world == 1:
             bench_batch(args, pmf, torch, stream)
+        return
+    if args.workload == "mlp":
+        if world == 1:
+            bench_mlp(args, pmf, torch, stream)
         return
     if args.workload == "adaptive":
         if world == 1:

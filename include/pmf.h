@@ -148,6 +148,22 @@ pmf_status pmf_run_prepare_seeded(pmf_system *sys, const double *lambda, int n_w
 pmf_status pmf_run_wait(pmf_run *run);
 void pmf_destroy_run(pmf_run *run);
 
+/* Sequential pulling protocol (Sec. III (i)): each of p->replicas
+ * independent simulations starts from x_o at lambda_1, relaxes p->n_steps
+ * steps (tau) while x is recorded, then continues from the state reached with
+ * the trap moved to lambda_2, and so on to lambda_s, in one continuous run
+ * (steps numbered 0 .. s * tau - 1 for the noise; equilibration n_equil and
+ * sampling count from each window's first step).  Simulation r uses uid
+ * uid_base + r for every window.  The samples land in the layout of
+ * pmf_run_info (window w, replica r = simulation r), so every estimator call
+ * applies unchanged; pmf_final_state returns one state per simulation.
+ * n_steps_per_window must be NULL; 1 <= n_windows <= 1024; s * tau < 2^32.
+ * Launch, wait and the reductions as for pmf_run_prepare.  Chain runs use
+ * the persistent launch (segments of at most pmf_chain_set_grid's seg_steps
+ * inside each window). */
+pmf_status pmf_run_prepare_sequential(pmf_system *sys, const double *lambda, int n_windows,
+                                      const pmf_run_params *p, pmf_run **out);
+
 /* Batched runs.  One pmf_batch_item is one independent PPP path (Sec. III
  * (ii)): windows lambda[n_windows] (strictly monotone) on chain `chain` of
  * the system (ignored for the 1D model).  pmf_run_batch_prepare lays the
@@ -285,7 +301,8 @@ pmf_status pmf_free_energy_noalloc(const float *x, const double *lambda, int n_w
                                    int64_t samples_per_window, double k, double kT, double *out);
 
 /* Final state of every replica: pos/vel [window][replica][bead][3] (chain) or
- * [window][replica] (1D, vel unused).  Capacity in doubles of each buffer. */
+ * [window][replica] (1D, vel unused); sequential runs: [replica][bead][3] or
+ * [replica].  Capacity in doubles of each buffer. */
 pmf_status pmf_final_state(const pmf_run *run, double *pos, double *vel, size_t capacity,
                            size_t *n_written);
 

@@ -40,12 +40,20 @@ def lib():
                                     C.c_double, C.c_double, C.c_long, C.c_long, C.c_long,
                                     C.c_uint64, C.c_uint32, _D, _D, C.c_int, _D]
         L.orc_chain_run.restype = C.c_long
+        L.orc_chain_run_from.argtypes = [C.POINTER(_OrcChain), C.c_double, C.c_double, C.c_double,
+                                         C.c_double, C.c_double, C.c_long, C.c_long, C.c_long, C.c_long,
+                                         C.c_uint64, C.c_uint32, _D, _D, C.c_int, _D]
+        L.orc_chain_run_from.restype = C.c_long
         L.orc_od1d_force.argtypes = [C.c_double] * 4
         L.orc_od1d_force.restype = C.c_double
         L.orc_od1d_run.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_long, C.c_long, C.c_long, C.c_uint64,
                                    C.c_uint32, C.c_double, _D, _D]
         L.orc_od1d_run.restype = C.c_long
+        L.orc_od1d_run_from.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                        C.c_double, C.c_long, C.c_long, C.c_long, C.c_long, C.c_uint64,
+                                        C.c_uint32, C.c_double, _D, _D]
+        L.orc_od1d_run_from.restype = C.c_long
         _lib = L
     return _lib
 
@@ -108,14 +116,16 @@ class Chain:
         return v
 
     def run(self, r0, lam, k, kT, dt, gamma, n_steps, n_equil, stride, seed, uid,
-            v0=None):
-        """One replica in one window; returns (samples, r_final, v_final)."""
+            v0=None, step0=0):
+        """One replica in one window (time steps numbered from step0);
+        returns (samples, r_final, v_final).  Velocities are drawn when v0 is
+        None."""
         r = np.array(r0, dtype=np.float64, order="C", copy=True)
         v = np.zeros_like(r) if v0 is None else np.array(v0, dtype=np.float64, order="C", copy=True)
         n_samp = max(0, (n_steps - n_equil) // stride)
         out = np.zeros(max(n_samp, 1))
-        ns = lib().orc_chain_run(C.byref(self.s), lam, k, kT, dt, gamma, n_steps, n_equil, stride,
-                                 seed, uid, _dp(r), _dp(v), int(v0 is None), _dp(out))
+        ns = lib().orc_chain_run_from(C.byref(self.s), lam, k, kT, dt, gamma, step0, n_steps, n_equil, stride,
+                                      seed, uid, _dp(r), _dp(v), int(v0 is None), _dp(out))
         if ns < 0:
             raise FloatingPointError("oracle chain run became non-finite")
         return out[:ns], r, v
@@ -125,10 +135,10 @@ def od1d_force(a, lam, k, x):
     return lib().orc_od1d_force(a, lam, k, x)
 
 
-def od1d_run(a, lam, k, kT, gamma, dt, n_steps, n_equil, stride, seed, uid, x0):
+def od1d_run(a, lam, k, kT, gamma, dt, n_steps, n_equil, stride, seed, uid, x0, step0=0):
     n_samp = max(0, (n_steps - n_equil) // stride)
     out = np.zeros(max(n_samp, 1))
     xf = C.c_double(0.0)
-    ns = lib().orc_od1d_run(a, lam, k, kT, gamma, dt, n_steps, n_equil, stride, seed, uid, x0,
-                            _dp(out), C.byref(xf))
+    ns = lib().orc_od1d_run_from(a, lam, k, kT, gamma, dt, step0, n_steps, n_equil, stride, seed, uid, x0,
+                                 _dp(out), C.byref(xf))
     return out[:ns], xf.value

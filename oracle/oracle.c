@@ -330,9 +330,26 @@ void orc_chain_init_velocities(const orc_chain *c, double kT, uint64_t seed, uin
  * stored.  r, v are read as the start state and overwritten with the final
  * state.  If init_v != 0 velocities are drawn first.  Returns the number of
  * samples written, or -1 if a coordinate became non-finite. */
+long orc_chain_run_from(const orc_chain *c, double lambda, double k, double kT, double dt, double gamma,
+                        long step0, long n_steps, long n_equil, long stride, uint64_t seed, uint32_t uid,
+                        double *r, double *v, int init_v, double *samples);
+
 long orc_chain_run(const orc_chain *c, double lambda, double k, double kT, double dt, double gamma,
                    long n_steps, long n_equil, long stride, uint64_t seed, uint32_t uid,
                    double *r, double *v, int init_v, double *samples)
+{
+    return orc_chain_run_from(c, lambda, k, kT, dt, gamma, 0, n_steps, n_equil, stride, seed, uid, r, v, init_v,
+                              samples);
+}
+
+/* As orc_chain_run, with the time steps numbered step0 .. step0 + n_steps - 1
+ * for the O-step noise (counter (block, uid, step, 0)); equilibration and
+ * sampling count from the first of them.  The sequential pulling protocol
+ * (Sec. III (i)) runs window i with step0 = i * tau from the state window
+ * i - 1 left. */
+long orc_chain_run_from(const orc_chain *c, double lambda, double k, double kT, double dt, double gamma,
+                        long step0, long n_steps, long n_equil, long stride, uint64_t seed, uint32_t uid,
+                        double *r, double *v, int init_v, double *samples)
 {
     const int n = c->n;
     double *f = (double *)malloc(sizeof(double) * 3 * (size_t)n);
@@ -344,7 +361,7 @@ long orc_chain_run(const orc_chain *c, double lambda, double k, double kT, doubl
     orc_chain_forces(c, r, lambda, k, f);
     long ns = 0;
     for (long step = 0; step < n_steps; ++step) {
-        dof_normals(n, seed, uid, (uint32_t)step, ORC_TAG_OSTEP, xi);
+        dof_normals(n, seed, uid, (uint32_t)(step0 + step), ORC_TAG_OSTEP, xi);
         for (int i = 0; i < n; ++i) {
             double im = 1.0 / c->mass[i];
             double sv = sqrt(kT * im);
@@ -392,17 +409,32 @@ double orc_od1d_force(double a, double lambda, double k, double x)
  *   x_{n+1} = x_n + F(x_n) dt / gamma + sqrt(2 kT dt / gamma) xi_n,
  * xi_n = normal (n mod 4) of the Philox block (0, uid, n div 4, TAG_OSTEP).
  * Sampling schedule as in orc_chain_run.  Returns the sample count. */
+long orc_od1d_run_from(double a, double lambda, double k, double kT, double gamma, double dt, long step0,
+                       long n_steps, long n_equil, long stride, uint64_t seed, uint32_t uid,
+                       double x0, double *samples, double *x_final);
+
 long orc_od1d_run(double a, double lambda, double k, double kT, double gamma, double dt,
                   long n_steps, long n_equil, long stride, uint64_t seed, uint32_t uid,
                   double x0, double *samples, double *x_final)
+{
+    return orc_od1d_run_from(a, lambda, k, kT, gamma, dt, 0, n_steps, n_equil, stride, seed, uid, x0, samples,
+                             x_final);
+}
+
+/* As orc_od1d_run with the steps numbered step0 .. step0 + n_steps - 1 for
+ * the noise (normal n mod 4 of block (0, uid, n div 4, 0)). */
+long orc_od1d_run_from(double a, double lambda, double k, double kT, double gamma, double dt, long step0,
+                       long n_steps, long n_equil, long stride, uint64_t seed, uint32_t uid,
+                       double x0, double *samples, double *x_final)
 {
     double x = x0;
     double xi[4] = {0, 0, 0, 0};
     const double amp = sqrt(2.0 * kT * dt / gamma);
     long ns = 0;
     for (long step = 0; step < n_steps; ++step) {
-        if ((step & 3) == 0) orc_normals4(seed, 0u, uid, (uint32_t)(step >> 2), ORC_TAG_OSTEP, xi);
-        x = x + orc_od1d_force(a, lambda, k, x) * dt / gamma + amp * xi[step & 3];
+        const long n = step0 + step;
+        if ((n & 3) == 0 || step == 0) orc_normals4(seed, 0u, uid, (uint32_t)(n >> 2), ORC_TAG_OSTEP, xi);
+        x = x + orc_od1d_force(a, lambda, k, x) * dt / gamma + amp * xi[n & 3];
         long done = step + 1;
         if (done > n_equil && (done - n_equil) % stride == 0) samples[ns++] = x;
     }

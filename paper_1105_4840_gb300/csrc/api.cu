@@ -73,6 +73,7 @@ struct pmf_run {
     cudaGraphExec_t graph = nullptr;   // captured launch sequence
     std::vector<unsigned> graph_gen;   // schedule generation per item at capture time
     int chain = 0, n_windows = 0, replicas = 0, stride = 1;
+    bool sequential = false;  // sequential protocol: replicas visit the windows in order
     double k = 0, kT = 1, dt = 0, gamma = 1, timeout_s = 0;
     unsigned long long seed = 0;
     uint32_t uid_base = 0;
@@ -206,7 +207,7 @@ pmf_status pmf_create_system(const pmf_system_desc *d, pmf_system **out)
 void pmf_destroy_system(pmf_system *sys) { delete sys; }
 
 static pmf_status prepare_items(pmf_system *sys, const pmf_batch_item *items, int n_items, const pmf_run_params *p,
-                                pmf_run **out)
+                                pmf_run **out, bool sequential = false)
 {
     if (!sys || !items || !p || !out || n_items < 1) return fail(PMF_EINVAL, "pmf_run_prepare: null argument");
     *out = nullptr;
@@ -232,8 +233,11 @@ static pmf_status prepare_items(pmf_system *sys, const pmf_batch_item *items, in
     if (p->replicas < 1 || p->sample_stride < 1) return fail(PMF_EINVAL, "replicas >= 1 and sample_stride >= 1");
     if (p->replicas > 65535 || (long long)n_windows * p->replicas > (1LL << 31) - 1)
         return fail(PMF_EINVAL, "too many replicas (at most 65535 per window)");
+    if (sequential && (n_items != 1 || p->n_steps_per_window))
+        return fail(PMF_EINVAL, "the sequential protocol takes one path with one relaxation time for every window");
     auto run = std::make_unique<pmf_run>();
     run->sys = sys;
+    run->sequential = sequential;
     run->chain = items[0].chain;
     run->n_windows = n_windows;
     run->replicas = p->replicas;
@@ -254,7 +258,7 @@ static pmf_status prepare_items(pmf_system *sys, const pmf_batch_item *items, in
         ri.nw = items[it].n_windows;
         ri.state_stride = sys->model == PMF_MODEL_CHAIN ? sys->chains[ri.chain]->state_bytes_per_replica() : sizeof(double);
         ri.state_off = state_off;
-        state_off += ri.state_stride * (size_t)ri.nw * p->replicas;
+        state_off += ri.state_stride * (size_t)(sequential ? 1 : ri.nw) * p->replicas;
         run->items.push_back(ri);
         run->lambda.insert(run->lambda.end(), items[it].lambda, items[it].lambda + items[it].n_windows);
         w0 += ri.nw;
@@ -320,6 +324,17 @@ pmf_status pmf_run_batch_prepare(pmf_system *sys, const pmf_batch_item *items, i
     return prepare_items(sys, items, n_items, p, out);
 }
 
+pmf_status pmf_run_prepare_sequential(pmf_system *sys, const double *lambda, int n_windows, const pmf_run_params *p,
+                                      pmf_run **out)
+{
+    if (!p) return fail(PMF_EINVAL, "pmf_run_prepare_sequential: null params");
+    if (n_windows < 1 || n_windows > 1024) return fail(PMF_EINVAL, "n_windows must be in [1, 1024]");
+    if ((long long)n_windows * p->n_steps >= (1LL << 32))
+        return fail(PMF_EINVAL, "the sequential run's total step count must be below 2^32");
+    pmf_batch_item it{p->chain, n_windows, lambda};
+    return prepare_items(sys, &it, 1, p, out, true);
+}
+
 // Modelled cost of one replica of an item: pair interactions x steps.
 static double item_cost(const pmf_run *run, const RunItem &ri)
 {
@@ -354,6 +369,17 @@ static cudaError_t enqueue_item(pmf_run *run, const RunItem &ri, cudaStream_t st
     L.kT = run->kT;
     L.dt = run->dt;
     L.gamma = run->gamma;
+    if (run->sequential) {
+        // one launch: each replica visits every window, nsteps[0] steps each
+        L.sequential = true;
+        L.window_steps = run->nsteps[0];
+        L.uid_base = run->uid_base;
+        L.n_blocks = run->replicas;
+        L.step_begin = 0;
+        L.step_end = run->nsteps[0] * ri.nw;
+        return run->sys->model == PMF_MODEL_CHAIN ? run->sys->chains[ri.chain]->launch(L, st)
+                                                  : od1d_launch(run->sys->od, L, run->replicas, st);
+    }
     const int n_rep = ri.nw * run->replicas;
     L.n_blocks = n_rep;
     long long max_steps = 0;
@@ -1245,7 +1271,7 @@ pmf_status pmf_free_energy_noalloc(const float *x, const double *lambda, int n_w
 pmf_status pmf_final_state(const pmf_run *run, double *pos, double *vel, size_t capacity, size_t *n_written)
 {
     if (pmf_status s = need_finished(run)) return s;
-    const int n_rep = run->n_windows * run->replicas;
+    const int n_rep = (run->sequential ? 1 : run->n_windows) * run->replicas;
     if (run->sys->model == PMF_MODEL_1D_DOUBLEWELL) {
         if (n_written) *n_written = (size_t)n_rep;
         if (!pos || capacity < (size_t)n_rep) return fail(PMF_EINVAL, "pmf_final_state: capacity too small");
@@ -1253,8 +1279,8 @@ pmf_status pmf_final_state(const pmf_run *run, double *pos, double *vel, size_t 
         return PMF_OK;
     }
     size_t need = 0;
-    for (const RunItem &ri : run->items)
-        need += (size_t)ri.nw * run->replicas * run->sys->chains[ri.chain]->n_beads() * 3;
+    const auto sims = [&](const RunItem &ri) { return (run->sequential ? 1 : ri.nw) * run->replicas; };
+    for (const RunItem &ri : run->items) need += (size_t)sims(ri) * run->sys->chains[ri.chain]->n_beads() * 3;
     if (n_written) *n_written = need;
     if ((!pos && !vel) || capacity < need) return fail(PMF_EINVAL, "pmf_final_state: capacity too small");
     std::vector<unsigned char> raw(run->state_bytes);
@@ -1265,7 +1291,7 @@ pmf_status pmf_final_state(const pmf_run *run, double *pos, double *vel, size_t 
         const int N = m.n_beads(), Np = m.n_padded();
         const bool dbl = m.precision() == PMF_FP64;
         const unsigned char *base = raw.data() + ri.state_off;
-        for (int q = 0; q < ri.nw * run->replicas; ++q)
+        for (int q = 0; q < sims(ri); ++q)
             for (int b = 0; b < N; ++b, o += 3)
                 for (int a = 0; a < 3; ++a) {
                     const size_t ip = ((size_t)q * 2 * Np + b) * 4 + a, iv = ((size_t)q * 2 * Np + Np + b) * 4 + a;

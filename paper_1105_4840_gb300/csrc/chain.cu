@@ -59,6 +59,9 @@ template <typename R> struct ChainArgs {
     int *done;                 // persistent mode: [n_rep] segments finished (zeroed)
     long long n_items;         // persistent mode: n_rep x segments
     int n_rep, seg_steps, persistent;
+    int sequential;            // sequential protocol: every simulation visits the windows in order,
+    long long window_steps;    //   window_steps steps each, in subs_per_window segments of
+    int subs_per_window;       //   at most seg_steps steps
     long long step_begin, step_end;
     int N, Np, n_tiles, w_last, replicas, max_units, stride;
     uint32_t uid_base;
@@ -615,16 +618,17 @@ template <> __device__ __forceinline__ Vec4<double> load_cg<double>(const Vec4<d
     return Vec4<double>{u.x, u.y, v.x, v.y};
 }
 
-// Steps [s0, s1) of replica `rep` (s1 clipped to the window's step count).
+// Steps [s0, s1) of the simulation whose state record and noise stream are
+// number `rep`, in window w as its replica r; the window started at step
+// `origin` (0 for the parallel protocol, w x tau for the sequential one).
 // State comes from x_o / the seeded start (s0 == 0) or from the replica's
 // state record, and goes back to it at the end, so a replica's trajectory
 // does not depend on how its steps are cut into launches or segments.
 // Returns false when the run was aborted (non-finite state).
 template <typename R, int NW>
-__device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s, int rep, long long s0,
-                                         long long s1)
+__device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s, int rep, int w, int r,
+                                         long long s0, long long s1, long long origin)
 {
-    const int w = rep / a.replicas, r = rep % a.replicas;
     const uint32_t uid = a.uid_base + (uint32_t)rep;
     const int tid = threadIdx.x;
     const R lam = (R)a.lambda[w];
@@ -683,7 +687,7 @@ __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s
         }
         __syncthreads();
     }
-    const long long nequil = a.nequil_w[w];
+    const long long nequil = origin + a.nequil_w[w];  // equilibration counts from the window's first step
     const long long sample_base = a.off_w[w] + (long long)r * a.tw[w];
     force_phase<R, NW>(a, s, lam, s0, nequil, sample_base, true, uid);
     __syncthreads();
@@ -848,16 +852,30 @@ __global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW =
         if (it < 0) return;
         const int rep = (int)(it % a.n_rep);
         const long long seg = it / a.n_rep;
-        const long long nsteps = a.nsteps_w[rep / a.replicas];
-        long long s0 = a.step_begin, s1 = a.step_end;
-        if (a.persistent) {
-            s0 += seg * a.seg_steps;
-            s1 = s0 + a.seg_steps < a.step_end ? s0 + a.seg_steps : a.step_end;
-        } else if (*((volatile int *)a.err) != 0) {
-            return;
+        int w, r;
+        long long s0 = a.step_begin, s1 = a.step_end, origin = 0;
+        if (a.sequential) {
+            // simulation rep, segment seg: part seg % subs of window seg / subs,
+            // the window covering steps [w tau, (w + 1) tau)
+            w = (int)(seg / a.subs_per_window);
+            r = rep;
+            origin = (long long)w * a.window_steps;
+            s0 = origin + (seg % a.subs_per_window) * a.seg_steps;
+            s1 = s0 + a.seg_steps < origin + a.window_steps ? s0 + a.seg_steps : origin + a.window_steps;
+        } else {
+            // parallel protocol: simulation rep is replica rep % R of window rep / R
+            w = rep / a.replicas;
+            r = rep % a.replicas;
+            if (a.persistent) {
+                s0 += seg * a.seg_steps;
+                s1 = s0 + a.seg_steps < a.step_end ? s0 + a.seg_steps : a.step_end;
+            } else if (*((volatile int *)a.err) != 0) {
+                return;
+            }
+            const long long nsteps = a.nsteps_w[w];
+            s1 = s1 < nsteps ? s1 : nsteps;
         }
-        s1 = s1 < nsteps ? s1 : nsteps;
-        if ((s0 < s1 || a.force_out != nullptr) && !simulate<R, NW>(a, s, rep, s0, s1)) return;
+        if ((s0 < s1 || a.force_out != nullptr) && !simulate<R, NW>(a, s, rep, w, r, s0, s1, origin)) return;
         if (a.persistent) {
             __syncthreads();  // the replica's state record is written
             if (threadIdx.x == 0) {
@@ -1174,6 +1192,16 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     a.n_rep = L.n_blocks;
     a.seg_steps = m->seg_steps;
     a.persistent = 0;
+    a.sequential = L.sequential ? 1 : 0;
+    a.window_steps = L.window_steps;
+    a.subs_per_window = 1;
+    if (L.sequential) {
+        // a window's steps in equal segments of at most seg_steps (no segment
+        // crosses a window boundary)
+        const long long subs = (L.window_steps + m->seg_steps - 1) / m->seg_steps;
+        a.subs_per_window = (int)subs;
+        a.seg_steps = (int)((L.window_steps + subs - 1) / subs);
+    }
     a.n_items = 0;
     const size_t smem = chain_smem_bytes<R>(m->geo, NW);
     // The attribute is the kernel's upper limit, shared by every chain that
@@ -1191,7 +1219,9 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     e = cudaFuncSetAttribute(chain_kernel<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
     if (e != cudaSuccess) return e;
     int grid = L.n_blocks;
-    if (L.queue != nullptr && L.done != nullptr && m->grid_ctas >= 0 && L.force_out == nullptr &&
+    if (L.sequential && (L.queue == nullptr || L.done == nullptr || L.window_steps < 1 || L.step_begin != 0))
+        return cudaErrorInvalidValue;
+    if (L.queue != nullptr && L.done != nullptr && (m->grid_ctas >= 0 || L.sequential) && L.force_out == nullptr &&
         L.step_end > L.step_begin) {
         // persistent: as many CTAs as fit at once (or as requested), never
         // more than there are replicas
@@ -1201,7 +1231,7 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
             return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         const long long slots = (long long)std::max(occ, 1) * sms;
-        long long want = m->grid_ctas;
+        long long want = m->grid_ctas > 0 ? m->grid_ctas : 0;
         if (want == 0) {
             // auto: fill every slot when there are enough replicas; otherwise a
             // whole number of CTAs per SM (replicas in excess of it keep the
@@ -1211,7 +1241,8 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
             want = L.n_blocks >= slots ? slots : (per_sm >= 3 ? per_sm * sms : L.n_blocks);
         }
         grid = (int)std::min<long long>(want, L.n_blocks);
-        const long long nseg = (L.step_end - L.step_begin + a.seg_steps - 1) / a.seg_steps;
+        const long long nseg = L.sequential ? (L.step_end / L.window_steps) * a.subs_per_window
+                                            : (L.step_end - L.step_begin + a.seg_steps - 1) / a.seg_steps;
         a.persistent = 1;
         a.n_items = nseg * L.n_blocks;
         if ((e = cudaMemsetAsync(L.queue, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;

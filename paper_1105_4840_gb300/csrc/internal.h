@@ -49,6 +49,10 @@ struct RunLaunch {
     // per-replica segment counters, both zeroed by the launch itself
     unsigned long long *queue = nullptr;
     int *done = nullptr;
+    // sequential protocol: n_blocks simulations each visit every window for
+    // window_steps steps (steps [0, n_windows x window_steps)); persistent only
+    bool sequential = false;
+    long long window_steps = 0;
     long long step_begin = 0, step_end = 0;
     int replicas = 0, stride = 1, n_blocks = 0;
     uint32_t uid_base = 0;

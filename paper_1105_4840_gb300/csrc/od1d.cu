@@ -20,12 +20,45 @@ struct Od1dArgs {
     int replicas, stride, n_rep;
     uint32_t uid_base;
     unsigned long long seed;
+    int sequential, n_windows;  // sequential protocol: each thread visits every window
+    long long window_steps;     //   for window_steps steps, in order
 };
+
+// Sequential pulling protocol (Sec. III (i)): simulation r visits the
+// windows in order, window w covering steps [w tau, (w + 1) tau) of one
+// continuous run; equilibration and sampling count from the window's start.
+__device__ void od1d_sequential(const Od1dArgs &a, int r)
+{
+    const uint32_t uid = a.uid_base + (uint32_t)r;
+    const double amp = sqrt(2.0 * a.kT * a.dt / a.gamma);
+    double x = a.start ? a.start[r] : a.x0;
+    for (int w = 0; w < a.n_windows; ++w) {
+        const double lam = a.lambda[w];
+        const long long origin = (long long)w * a.window_steps, nequil = a.nequil_w[w];
+        const long long base = a.off_w[w] + (long long)r * a.tw[w];
+        Normal4<double> n = philox_normals<double>(a.seed, 0u, uid, (uint32_t)(origin >> 2), kTagOStep);
+        for (long long step = origin; step < origin + a.window_steps; ++step) {
+            const int lane = (int)(step & 3);
+            if (lane == 0) n = philox_normals<double>(a.seed, 0u, uid, (uint32_t)(step >> 2), kTagOStep);
+            const double xi = lane == 0 ? n.n0 : (lane == 1 ? n.n1 : (lane == 2 ? n.n2 : n.n3));
+            const double f = -4.0 * a.a * x * (x * x - 1.0) - a.k * (x - lam);
+            x = x + f * a.dt / a.gamma + amp * xi;
+            const long long done = step + 1 - origin;
+            if (done > nequil && (done - nequil) % a.stride == 0) a.xout[base + (done - nequil) / a.stride - 1] = (float)x;
+        }
+    }
+    if (!isfinite(x)) atomicOr(a.err, kErrNonFinite);
+    a.state[r] = x;
+}
 
 __global__ void od1d_kernel(const Od1dArgs a)
 {
     const int rep = blockIdx.x * blockDim.x + threadIdx.x;
     if (rep >= a.n_rep) return;
+    if (a.sequential) {
+        od1d_sequential(a, rep);
+        return;
+    }
     const int w = rep / a.replicas, r = rep % a.replicas;
     const uint32_t uid = a.uid_base + (uint32_t)rep;
     const double lam = a.lambda[w];
@@ -74,6 +107,10 @@ cudaError_t od1d_launch(const Od1dParams &m, const RunLaunch &L, int n_rep, cuda
     a.n_rep = n_rep;
     a.uid_base = L.uid_base;
     a.seed = L.seed;
+    a.sequential = L.sequential ? 1 : 0;
+    a.window_steps = L.window_steps;
+    a.n_windows = L.sequential ? (int)(L.step_end / L.window_steps) : 0;
+    if (L.sequential && (L.window_steps < 1 || L.step_begin != 0)) return cudaErrorInvalidValue;
     const int threads = 128;
     od1d_kernel<<<(n_rep + threads - 1) / threads, threads, 0, st>>>(a);
     return cudaGetLastError();

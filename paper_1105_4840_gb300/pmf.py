@@ -91,6 +91,7 @@ def _load():
     for name in ("pmf_run_windows", "pmf_run_prepare"):
         getattr(L, name).argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.POINTER(P)]
     L.pmf_run_prepare_seeded.argtypes = [P, _D, C.c_int, C.POINTER(RunParams), _D, C.POINTER(P)]
+    L.pmf_run_prepare_sequential.argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.POINTER(P)]
     L.pmf_run_batch_prepare.argtypes = [P, C.POINTER(BatchItem), C.c_int, C.POINTER(RunParams), C.POINTER(P)]
     L.pmf_free_energy_item.argtypes = [P, C.c_int, C.POINTER(FreeEnergyResult)]
     L.pmf_run_launch.argtypes = [P]
@@ -133,6 +134,7 @@ def _load():
     L.pmf_last_error.restype = C.c_char_p
     L.pmf_version.restype = C.c_char_p
     for name in ("pmf_create_system", "pmf_run_windows", "pmf_run_prepare", "pmf_run_prepare_seeded", "pmf_run_batch_prepare",
+                 "pmf_run_prepare_sequential",
                  "pmf_free_energy_item", "pmf_run_launch",
                  "pmf_run_wait", "pmf_get_run_info", "pmf_x_samples", "pmf_work_samples",
                  "pmf_free_energy", "pmf_free_energy_from_samples", "pmf_final_state",
@@ -317,6 +319,17 @@ def pmf_run_prepare(system: System, lambdas, params) -> Run:
     p, keep = params
     h = C.c_void_p()
     _check(lib.pmf_run_prepare(system.handle, _dp(lam), lam.size, C.byref(p), C.byref(h)), "pmf_run_prepare")
+    return Run(h, lam, keep=(p, keep, system))
+
+
+def pmf_run_prepare_sequential(system: System, lambdas, params) -> Run:
+    """Sequential pulling protocol: params.replicas simulations each visit
+    every window in order for params.n_steps steps."""
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    p, keep = params
+    h = C.c_void_p()
+    _check(lib.pmf_run_prepare_sequential(system.handle, _dp(lam), lam.size, C.byref(p), C.byref(h)),
+           "pmf_run_prepare_sequential")
     return Run(h, lam, keep=(p, keep, system))
 
 

@@ -410,6 +410,57 @@ def bench_mlp(args, pmf, torch, stream):
     print(json.dumps(line), flush=True)
 
 
+def bench_spp(args, pmf, torch, stream):
+    """Sequential pulling protocol on the 104-bead chain: `--replicas`
+    independent simulations (672 by default, the parallel workload's count)
+    each visit the 21 windows in order, `--md-steps` steps per window."""
+    w = _workload(args.md_steps)
+    p, start, run = w["params"], w["start"], w["run"]
+    run.replicas = args.replicas
+    sysh = pmf.pmf_create_system_chain([p], [start])
+    rr = pmf.pmf_run_prepare_sequential(sysh, run.lambdas, pmf.make_params(run))
+    for _ in range(args.warmup):
+        rr.launch()
+        rr.wait()
+    sim_ms, red_ms = [], []
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.5)
+    for _ in range(args.steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        rr.launch()
+        e[1].record(stream)
+        rr.reduce()
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        sim_ms.append(e[0].elapsed_time(e[1]))
+        red_ms.append(e[1].elapsed_time(e[2]))
+    clocks.stop()
+    rr.wait()
+    res = rr.free_energy()
+    steps = run.replicas * run.lambdas.size * run.n_steps
+    t = statistics.mean(a + b for a, b in zip(sim_ms, red_ms))
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sm_count * 128 * 2 * float(_peaks().get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    achieved = steps * flops_per_replica_step(N_BEADS) / (statistics.mean(sim_ms) / 1000.0) / 1e12
+    clk = clocks.summary()
+    warps, ctas, seg = pmf.pmf_chain_get_launch(sysh, 0)
+    line = {"workload": "chain104_spp", "metric": "replica-steps/s", "value": steps / (t / 1000.0),
+            "unit": "replica-steps/s", "ms_per_step": t, "steps": args.steps, "warmup": args.warmup,
+            "config": {"simulations": run.replicas, "windows": int(run.lambdas.size),
+                       "md_steps_per_window": run.n_steps, "warps_per_replica": warps,
+                       "launch": f"persistent, {'auto' if ctas == 0 else ctas} CTAs, segments <= {seg} steps"},
+            "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+                       "reasons": clk.get("reasons")},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak},
+            "dF_JE_end": float(res["dF_JE"][-1]), "se_JE_end": float(res["se_JE"][-1]),
+            "dF_fluct_end": float(res["dF_fluct"][-1])}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,7 +470,7 @@ def main():
     ap.add_argument("--md-steps", type=int, default=400000, help="BAOAB steps per window (workload: 4e5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="chain104",
-                    choices=["chain104", "batch64", "precision", "adaptive", "mlp"],
+                    choices=["chain104", "batch64", "precision", "adaptive", "mlp", "spp"],
                     help="chain104: the 104-bead PPP (default); batch64: 64 uneven chains in one graph; "
                          "precision: FP32 vs FP64 integration study")
     ap.add_argument("--replicas", type=int, default=1024, help="replicas per window (precision study)")
@@ -459,6 +510,12 @@ def main():
     if args.workload == "batch64":
         if world == 1:
             bench_batch(args, pmf, torch, stream)
+        return
+    if args.workload == "spp":
+        if world == 1:
+            if args.replicas == 1024:  # the precision study's default is not meant here
+                args.replicas = 672
+            bench_spp(args, pmf, torch, stream)
         return
     if args.workload == "mlp":
         if world == 1:

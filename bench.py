@@ -461,6 +461,34 @@ def bench_spp(args, pmf, torch, stream):
     print(json.dumps(line), flush=True)
 
 
+def bench_histograms(args, pmf, torch, stream):
+    """App. C work distributions on the 104-bead workload's samples with the
+    paper's bins (dx = 0.001 A, dW = 0.01 kcal/mol, W in +-150 kcal/mol),
+    after a PPP run of --md-steps steps per window."""
+    w = _workload(args.md_steps)
+    p, start, run = w["params"], w["start"], w["run"]
+    sysh = pmf.pmf_create_system_chain([p], [start])
+    rr = pmf.pmf_run_windows(sysh, run.lambdas, pmf.make_params(run))
+    dx, K = 1e-4, 50000                      # 0.001 A bins over 0..5 nm
+    dw = 0.01 * 4.184                        # 0.01 kcal/mol in kJ/mol
+    M = int(round(150 * 4.184 / dw))         # +-150 kcal/mol
+    for _ in range(args.warmup):
+        rr.work_distributions(0.0, dx, K, dw, M, with_omega=False)
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = rr.work_distributions(0.0, dx, K, dw, M, with_omega=False)
+        times.append(time.perf_counter() - t0)
+    res = rr.free_energy()
+    line = {"workload": "chain104_app_c_histograms", "metric": "ms", "value": 1000 * statistics.median(times),
+            "unit": "ms per call (host wall clock, synchronous)", "x_bins": K, "w_bins": 2 * M + 1,
+            "samples": int(run.lambdas.size * run.replicas * ((run.n_steps - run.n_equil) // run.stride)),
+            "dF_JE_end_hist": float(g["dF_JE"][-1]), "dF_JE_end_factorised": float(res["dF_JE"][-1]),
+            "lost_max": float(g["lost"].max())}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,7 +498,7 @@ def main():
     ap.add_argument("--md-steps", type=int, default=400000, help="BAOAB steps per window (workload: 4e5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="chain104",
-                    choices=["chain104", "batch64", "precision", "adaptive", "mlp", "spp"],
+                    choices=["chain104", "batch64", "precision", "adaptive", "mlp", "spp", "histograms"],
                     help="chain104: the 104-bead PPP (default); batch64: 64 uneven chains in one graph; "
                          "precision: FP32 vs FP64 integration study")
     ap.add_argument("--replicas", type=int, default=1024, help="replicas per window (precision study)")
@@ -510,6 +538,10 @@ def main():
     if args.workload == "batch64":
         if world == 1:
             bench_batch(args, pmf, torch, stream)
+        return
+    if args.workload == "histograms":
+        if world == 1:
+            bench_histograms(args, pmf, torch, stream)
         return
     if args.workload == "spp":
         if world == 1:

@@ -268,6 +268,33 @@ pmf_status pmf_run_partials(const pmf_run *run, double *out, size_t capacity, si
 pmf_status pmf_free_energy_from_partials(const double *partials, const double *lambda, int n_windows,
                                          int replicas, double k, double kT, pmf_free_energy_result *res);
 
+/* Work distributions of App. C.  Each window's x samples are counted into
+ * n_x bins [x_lo + j dx, x_lo + (j + 1) dx) (rho_i, divided by the window's
+ * sample count; samples outside are lost).  The distribution of the work
+ * accumulated over the first i - 1 pulling steps, Omega_i, lives on the bins
+ * W = b dw, b = -M..M; Omega_1 is all at W = 0 and Omega_{i+1} adds the
+ * increment of Eq. (9) at every x bin of window i, weighted by rho_i.  With
+ * left_edge = 0 (the default reading) a bin stands for its centre and a work
+ * value goes to the nearest bin; left_edge = 1 follows the rule as printed
+ * (left edges, floor, and the W = 0 bin smoothed as the mean of its
+ * neighbours after every step).  The recursion runs through Omega_s.
+ * Outputs (each may be NULL): omega[s][2M + 1] (host, capacity in doubles),
+ * dF_JE[i] = -kT ln sum_b Omega_i(b) exp(-b dw / kT) / sum_b Omega_i(b),
+ * var_ZW[i] = the App. C variance with sigma_W of Omega_i and Q its non-zero
+ * bins, lost[i] = 1 - sum_b Omega_i(b): probability that left the W or x
+ * range (with left_edge = 1 also the change the smoothing makes).  The run must
+ * be finished and single-item; every window needs a sample inside the x
+ * range.  As dx, dw -> 0 (bin centres) dF_JE tends to pmf_free_energy's. */
+typedef struct {
+    double x_lo, dx;            /* x bins                                        */
+    int n_x;                    /* number of x bins (<= 2^26)                    */
+    double dw;                  /* work bin width                                */
+    int M;                      /* work bins b = -M..M (<= 2^24)                 */
+    int left_edge;              /* 0: bin centres, nearest bin; 1: as printed    */
+} pmf_hist_params;
+pmf_status pmf_work_distributions(const pmf_run *run, const pmf_hist_params *hp, double *omega,
+                                  size_t omega_capacity, double *dF_JE, double *var_ZW, double *lost);
+
 /* The same reduction on caller-supplied samples x (layout of pmf_run_info
  * with `replicas` and samples_per_window[n_windows]); x is a host pointer
  * (x_on_device = 0) or a device pointer (x_on_device = 1). */

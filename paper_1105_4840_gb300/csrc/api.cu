@@ -655,6 +655,98 @@ pmf_status pmf_free_energy(const pmf_run *run, pmf_free_energy_result *res)
     return copy_result(h.data(), run->n_windows, res);
 }
 
+pmf_status pmf_work_distributions(const pmf_run *run, const pmf_hist_params *hp, double *omega,
+                                  size_t omega_capacity, double *dF_JE, double *var_ZW, double *lost)
+{
+    if (pmf_status s = need_finished(run)) return s;
+    if (!hp) return fail(PMF_EINVAL, "pmf_work_distributions: null parameters");
+    if (run->items.size() != 1) return fail(PMF_EINVAL, "pmf_work_distributions: single-item runs only");
+    if (!(hp->dx > 0) || !(hp->dw > 0) || !std::isfinite(hp->x_lo) || hp->n_x < 1 || hp->n_x > (1 << 26) ||
+        hp->M < 1 || hp->M > (1 << 24))
+        return fail(PMF_EINVAL, "pmf_work_distributions: bad bins");
+    const int s = run->n_windows;
+    const long long M = hp->M, nb = 2 * M + 1;
+    if (omega && omega_capacity < (size_t)s * nb) return fail(PMF_EINVAL, "pmf_work_distributions: omega too small");
+    struct Tmp {
+        unsigned long long *cnt = nullptr, *outside = nullptr;
+        int *jmin = nullptr, *jmax = nullptr;
+        double *om = nullptr, *g = nullptr, *stats = nullptr;
+        long long *sup = nullptr;
+        ~Tmp() { cudaFree(cnt); cudaFree(outside); cudaFree(jmin); cudaFree(jmax); cudaFree(om); cudaFree(g);
+                 cudaFree(stats); cudaFree(sup); }
+    } t;
+    CK(cudaMalloc(&t.cnt, sizeof(unsigned long long) * (size_t)s * hp->n_x), "alloc counts");
+    CK(cudaMalloc(&t.outside, sizeof(unsigned long long) * s), "alloc");
+    CK(cudaMalloc(&t.jmin, sizeof(int) * s), "alloc");
+    CK(cudaMalloc(&t.jmax, sizeof(int) * s), "alloc");
+    CK(cudaMalloc(&t.om, sizeof(double) * (size_t)s * nb), "alloc omega");
+    CK(cudaMalloc(&t.stats, sizeof(double) * 4 * s), "alloc");
+    CK(cudaMalloc(&t.sup, sizeof(long long) * 2 * s), "alloc");
+    CK(cudaMemsetAsync(t.cnt, 0, sizeof(unsigned long long) * (size_t)s * hp->n_x, g_stream), "clear");
+    CK(cudaMemsetAsync(t.outside, 0, sizeof(unsigned long long) * s, g_stream), "clear");
+    CK(cudaMemsetAsync(t.jmin, 0x7f, sizeof(int) * s, g_stream), "clear");
+    CK(cudaMemsetAsync(t.jmax, 0xff, sizeof(int) * s, g_stream), "clear");
+    CK(cudaMemsetAsync(t.om, 0, sizeof(double) * (size_t)s * nb, g_stream), "clear");
+    CK(hist_count_launch(run->d_x, run->d_off, run->d_tw, s, run->replicas, hp->x_lo, hp->dx, hp->n_x, t.cnt, t.outside,
+                         t.jmin, t.jmax, g_stream), "count");
+    std::vector<int> jmin(s), jmax(s);
+    CK(cudaMemcpyAsync(jmin.data(), t.jmin, sizeof(int) * s, cudaMemcpyDeviceToHost, g_stream), "copy");
+    CK(cudaMemcpyAsync(jmax.data(), t.jmax, sizeof(int) * s, cudaMemcpyDeviceToHost, g_stream), "copy");
+    CK(cudaStreamSynchronize(g_stream), "sync");
+    for (int i = 0; i + 1 < s; ++i)
+        if (jmax[i] < jmin[i]) return fail(PMF_EINVAL, "pmf_work_distributions: a window has no sample in the x range");
+    // supports: Omega_1 at b = 0, then Omega_{i+1} = Omega_i * g_i
+    std::vector<long long> sup(2 * (size_t)s);
+    std::vector<HistStep> steps(s > 1 ? s - 1 : 0);
+    sup[0] = sup[1] = 0;
+    long long max_ng = 1;
+    for (int i = 0; i + 1 < s; ++i) {
+        HistStep &h = steps[i];
+        h.x_lo = hp->x_lo;
+        h.dx = hp->dx;
+        h.dw = hp->dw;
+        h.hk = 0.5 * run->k;
+        h.d = run->lambda[i + 1] - run->lambda[i];
+        h.lsum = run->lambda[i + 1] + run->lambda[i];
+        h.left_edge = hp->left_edge ? 1 : 0;
+        h.jmin = jmin[i];
+        h.jmax = jmax[i];
+        const long long a = hist_shift_host(h, h.jmin), b = hist_shift_host(h, h.jmax);
+        h.gmin = std::min(a, b) - 1;
+        h.gmax = std::max(a, b) + 1;
+        max_ng = std::max(max_ng, h.gmax - h.gmin + 1);
+        long long lo = sup[2 * i] + h.gmin, hi = sup[2 * i + 1] + h.gmax;
+        if (h.left_edge) {
+            lo = std::min(lo, -1LL);
+            hi = std::max(hi, 1LL);
+        }
+        sup[2 * (i + 1)] = std::max(lo, -M);
+        sup[2 * (i + 1) + 1] = std::min(hi, M);
+    }
+    CK(cudaMalloc(&t.g, sizeof(double) * (size_t)max_ng), "alloc shifts");
+    const double one = 1.0;
+    CK(cudaMemcpyAsync(t.om + M, &one, sizeof(double), cudaMemcpyHostToDevice, g_stream), "init");
+    for (int i = 0; i + 1 < s; ++i) {
+        const double inv_n = 1.0 / (double)(run->tw[i] * run->replicas);
+        CK(hist_step_launch(steps[i], t.cnt + (size_t)i * hp->n_x, inv_n, t.g, t.om + (size_t)i * nb, sup[2 * i],
+                            sup[2 * i + 1], t.om + (size_t)(i + 1) * nb, sup[2 * (i + 1)], sup[2 * (i + 1) + 1], M,
+                            g_stream),
+           "convolution");
+    }
+    CK(cudaMemcpyAsync(t.sup, sup.data(), sizeof(long long) * 2 * s, cudaMemcpyHostToDevice, g_stream), "upload");
+    CK(hist_stats_launch(t.om, s, M, hp->dw, run->kT, t.sup, t.stats, g_stream), "stats");
+    std::vector<double> st(4 * (size_t)s);
+    CK(cudaMemcpyAsync(st.data(), t.stats, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, g_stream), "copy");
+    if (omega) CK(cudaMemcpyAsync(omega, t.om, sizeof(double) * (size_t)s * nb, cudaMemcpyDeviceToHost, g_stream), "copy");
+    CK(cudaStreamSynchronize(g_stream), "sync");
+    for (int i = 0; i < s; ++i) {
+        if (dF_JE) dF_JE[i] = st[4 * i];
+        if (var_ZW) var_ZW[i] = st[4 * i + 1];
+        if (lost) lost[i] = i == 0 ? 0.0 : std::max(0.0, 1.0 - st[4 * i + 2]);
+    }
+    return PMF_OK;
+}
+
 pmf_status pmf_run_partials(const pmf_run *run, double *out, size_t capacity, size_t *n_written)
 {
     if (pmf_status s = need_finished(run)) return s;

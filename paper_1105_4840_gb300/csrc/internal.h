@@ -162,6 +162,24 @@ struct SeedJob {
 cudaError_t seed_launch(const SeedJob *jobs, int n_jobs, int max_cand, int N, int Np, int replicas, bool fp64,
                         double *start, cudaStream_t st);
 
+// Work distributions of App. C (histogram.cu)
+struct HistStep {
+    double x_lo = 0, dx = 1, dw = 1;  // x bins and work bin width
+    double hk = 0, d = 0, lsum = 0;   // k/2, lambda_{i+1} - lambda_i, lambda_{i+1} + lambda_i
+    int left_edge = 0;                // the printed rule: bin left edges and floor
+    long long jmin = 0, jmax = -1;    // occupied x bins of the window
+    long long gmin = 0, gmax = -1;    // support of the shift distribution
+};
+cudaError_t hist_count_launch(const float *x, const long long *off_w, const long long *tw, int n_windows, int replicas,
+                              double x_lo, double dx, int n_x, unsigned long long *cnt, unsigned long long *outside,
+                              int *jmin, int *jmax, cudaStream_t st);
+long long hist_shift_host(const HistStep &h, long long j);
+cudaError_t hist_step_launch(const HistStep &h, const unsigned long long *cnt_w, double inv_n, double *g,
+                             const double *in, long long in_lo, long long in_hi, double *out, long long out_lo,
+                             long long out_hi, long long M, cudaStream_t st);
+cudaError_t hist_stats_launch(const double *om, int n_windows, long long M, double dw, double kT, const long long *sup,
+                              double *stats, cudaStream_t st);
+
 cudaError_t philox_launch(unsigned long long seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int n,
                           uint32_t *raw, float *normals, cudaStream_t st);
 

@@ -55,6 +55,11 @@ class BatchItem(C.Structure):
     _fields_ = [("chain", C.c_int), ("n_windows", C.c_int), ("lambda_", _D)]
 
 
+class HistParams(C.Structure):
+    _fields_ = [("x_lo", C.c_double), ("dx", C.c_double), ("n_x", C.c_int), ("dw", C.c_double), ("M", C.c_int),
+                ("left_edge", C.c_int)]
+
+
 class RunInfo(C.Structure):
     _fields_ = [("n_windows", C.c_int), ("replicas", C.c_int), ("total_samples", C.c_int64),
                 ("samples_per_window", C.c_int64 * MAX_RUN_WINDOWS),
@@ -104,6 +109,7 @@ def _load():
     L.pmf_free_energy.argtypes = [P, C.POINTER(FreeEnergyResult)]
     L.pmf_free_energy_from_samples.argtypes = [C.c_void_p, C.c_int, _D, C.c_int, C.c_int, _I64,
                                                C.c_double, C.c_double, C.POINTER(FreeEnergyResult)]
+    L.pmf_work_distributions.argtypes = [P, C.POINTER(HistParams), _D, C.c_size_t, _D, _D, _D]
     L.pmf_run_partials.argtypes = [P, _D, C.c_size_t, C.POINTER(C.c_size_t)]
     L.pmf_free_energy_from_partials.argtypes = [_D, _D, C.c_int, C.c_int, C.c_double, C.c_double,
                                                 C.POINTER(FreeEnergyResult)]
@@ -138,7 +144,7 @@ def _load():
                  "pmf_free_energy_item", "pmf_run_launch",
                  "pmf_run_wait", "pmf_get_run_info", "pmf_x_samples", "pmf_work_samples",
                  "pmf_free_energy", "pmf_free_energy_from_samples", "pmf_final_state",
-                 "pmf_run_partials", "pmf_free_energy_from_partials", "pmf_philox",
+                 "pmf_run_partials", "pmf_free_energy_from_partials", "pmf_work_distributions", "pmf_philox",
                  "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_free_energy_noalloc",
                  "pmf_mlp_create", "pmf_mlp_get_params", "pmf_mlp_predict", "pmf_mlp_gradient", "pmf_mlp_train",
                  "pmf_overlap", "pmf_run_adaptive", "pmf_chain_set_warps", "pmf_chain_set_grid", "pmf_chain_get_launch",
@@ -289,6 +295,18 @@ class Run:
     def free_energy_item(self, item, n_windows):
         return _fe_call(lambda res: lib.pmf_free_energy_item(self.handle, item, C.byref(res)), n_windows,
                         "pmf_free_energy_item")
+
+    def work_distributions(self, x_lo, dx, n_x, dw, M, left_edge=False, with_omega=True):
+        """App. C work distributions: dict with omega [s, 2M + 1] (if asked),
+        dF_JE, var_ZW, lost."""
+        s = self.lambdas.size
+        hp = HistParams(x_lo, dx, n_x, dw, M, int(left_edge))
+        om = np.zeros((s, 2 * M + 1)) if with_omega else None
+        dF, var, lost = np.zeros(s), np.zeros(s), np.zeros(s)
+        _check(lib.pmf_work_distributions(self.handle, C.byref(hp), _dp(om) if om is not None else None,
+                                          om.size if om is not None else 0, _dp(dF), _dp(var), _dp(lost)),
+               "pmf_work_distributions")
+        return {"omega": om, "dF_JE": dF, "var_ZW": var, "lost": lost}
 
     def partials(self):
         """Per-replica partial sums [n_windows, replicas, 5] (pmf_run_partials)."""

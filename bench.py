@@ -489,6 +489,37 @@ def bench_histograms(args, pmf, torch, stream):
     print(json.dumps(line), flush=True)
 
 
+def bench_sweeps(args, pmf, torch, stream):
+    """The experiments of Sec. IV B-D on the 104-bead chain: the 21-window
+    run's estimates from every second window (s = 11), a spring-constant sweep
+    and a relaxation-time sweep, with the wall time of each run."""
+    from paper_1105_4840_gb300 import sweeps
+
+    w = _workload(args.md_steps)
+    p, start, run = w["params"], w["start"], w["run"]
+    sysh = pmf.pmf_create_system_chain([p], [start])
+    lam = run.lambdas
+    t0 = time.perf_counter()
+    rr = pmf.pmf_run_windows(sysh, lam, pmf.make_params(run))
+    full = rr.free_energy()
+    t_full = time.perf_counter() - t0
+    sub = sweeps.subsample(rr, lam, run.k, run.kT, every=2)
+    ks = sweeps.k_sweep(sysh, lam, run, [100.0, 500.0, 2500.0])
+    taus = sweeps.tau_sweep(sysh, lam, run, [int(t / run.dt) for t in (50.0, 100.0, 200.0, 400.0, 800.0)],
+                            at_lambda=2.6)
+    kT = run.kT
+    line = {"workload": "chain104_sweeps", "kT": kT, "md_steps_per_window": run.n_steps,
+            "delta_lambda": {"s21": {"dF_JE": float(full["dF_JE"][-1]), "dF_fluct": float(full["dF_fluct"][-1]),
+                                     "seconds": t_full},
+                             "s11": {"dF_JE": float(sub["dF_JE"][-1]), "dF_fluct": float(sub["dF_fluct"][-1])}},
+            "k_sweep": [{"k": o["k"], "dF_JE": float(o["result"]["dF_JE"][-1]),
+                         "dF_fluct": float(o["result"]["dF_fluct"][-1]),
+                         "min_dF_fluct": float(o["result"]["dF_fluct"].min()),
+                         "gamma2_mean": float(np.mean(o["result"]["gamma2"])), "seconds": o["seconds"]} for o in ks],
+            "tau_sweep": taus}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -498,7 +529,7 @@ def main():
     ap.add_argument("--md-steps", type=int, default=400000, help="BAOAB steps per window (workload: 4e5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="chain104",
-                    choices=["chain104", "batch64", "precision", "adaptive", "mlp", "spp", "histograms"],
+                    choices=["chain104", "batch64", "precision", "adaptive", "mlp", "spp", "histograms", "sweeps"],
                     help="chain104: the 104-bead PPP (default); batch64: 64 uneven chains in one graph; "
                          "precision: FP32 vs FP64 integration study")
     ap.add_argument("--replicas", type=int, default=1024, help="replicas per window (precision study)")
@@ -538,6 +569,10 @@ def main():
     if args.workload == "batch64":
         if world == 1:
             bench_batch(args, pmf, torch, stream)
+        return
+    if args.workload == "sweeps":
+        if world == 1:
+            bench_sweeps(args, pmf, torch, stream)
         return
     if args.workload == "histograms":
         if world == 1:

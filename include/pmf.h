@@ -186,6 +186,27 @@ typedef struct {
 pmf_status pmf_run_batch_prepare(pmf_system *sys, const pmf_batch_item *items, int n_items,
                                  const pmf_run_params *p, pmf_run **out);
 
+/* Constant-velocity pulling, the steered-MD comparator the paper measures
+ * against (Sec. I, the work -v k int (x - lambda_1 - v t) dt): p->replicas
+ * simulations start from x_o with the trap at lambda1, relax p->n_equil
+ * steps (n_equil < 0: 10 % of n_steps), then the trap centre advances by
+ * velocity * dt per step for the remaining steps; each move from lambda to
+ * lambda' does the work of Eq. (9), k/2 (lambda' - lambda)(lambda' + lambda -
+ * 2 x), at the reaction coordinate of that moment (chain: at the force
+ * evaluation ending a step; 1D: before the step).  Every sample_stride steps
+ * of pulling, x (pmf_x_samples, one window) and the accumulated work
+ * (pmf_smd_work, FP64, [replica][record]) are recorded; record j is at trap
+ * position lambda1 + velocity dt (j + 1) sample_stride.  pmf_smd_free_energy
+ * gives per record: dF_JE = -kT ln <exp(-W/kT)> over the replicas (Eq. (1)),
+ * dF_cumulant = <W> - var(W)/2kT (the second-order cumulant estimate of the
+ * PMF method), <W>, var(W) (divisor replicas) and <x>; arrays of capacity
+ * >= the record count, any may be NULL. */
+pmf_status pmf_run_prepare_smd(pmf_system *sys, double lambda1, double velocity, const pmf_run_params *p,
+                               pmf_run **out);
+pmf_status pmf_smd_work(const pmf_run *run, double *out, size_t capacity, size_t *n_written);
+pmf_status pmf_smd_free_energy(const pmf_run *run, double *lambda, double *dF_JE, double *dF_cumulant,
+                               double *W_mean, double *W_var, double *mean_x, int capacity);
+
 /* Shape of a run's sample store: x[w][r][t], t fastest; window w holds
  * replicas * samples_per_window[w] floats starting at sample_offset[w]. */
 typedef struct {

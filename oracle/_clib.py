@@ -54,6 +54,14 @@ def lib():
                                         C.c_double, C.c_long, C.c_long, C.c_long, C.c_long, C.c_uint64,
                                         C.c_uint32, C.c_double, _D, _D]
         L.orc_od1d_run_from.restype = C.c_long
+        L.orc_chain_smd.argtypes = [C.POINTER(_OrcChain), C.c_double, C.c_double, C.c_double, C.c_double,
+                                    C.c_double, C.c_double, C.c_long, C.c_long, C.c_long, C.c_uint64, C.c_uint32,
+                                    _D, _D, _D, _D]
+        L.orc_chain_smd.restype = C.c_long
+        L.orc_od1d_smd.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                   C.c_double, C.c_long, C.c_long, C.c_long, C.c_uint64, C.c_uint32, C.c_double,
+                                   _D, _D]
+        L.orc_od1d_smd.restype = C.c_long
         _lib = L
     return _lib
 
@@ -130,9 +138,30 @@ class Chain:
             raise FloatingPointError("oracle chain run became non-finite")
         return out[:ns], r, v
 
+    def smd(self, r0, lam1, vdt, k, kT, dt, gamma, n_steps, n_equil, stride, seed, uid):
+        """Constant-velocity pull of one replica: (x records, work records,
+        r_final, v_final)."""
+        r = np.array(r0, dtype=np.float64, order="C", copy=True)
+        v = np.zeros_like(r)
+        n = max(0, (n_steps - n_equil) // stride)
+        xo, wo = np.zeros(max(n, 1)), np.zeros(max(n, 1))
+        ns = lib().orc_chain_smd(C.byref(self.s), lam1, vdt, k, kT, dt, gamma, n_steps, n_equil, stride, seed, uid,
+                                 _dp(r), _dp(v), _dp(xo), _dp(wo))
+        if ns < 0:
+            raise FloatingPointError("oracle chain run became non-finite")
+        return xo[:ns], wo[:ns], r, v
+
 
 def od1d_force(a, lam, k, x):
     return lib().orc_od1d_force(a, lam, k, x)
+
+
+def od1d_smd(a, lam1, vdt, k, kT, gamma, dt, n_steps, n_equil, stride, seed, uid, x0):
+    """Constant-velocity pull of the 1D model: (x records, work records)."""
+    n = max(0, (n_steps - n_equil) // stride)
+    xo, wo = np.zeros(max(n, 1)), np.zeros(max(n, 1))
+    ns = lib().orc_od1d_smd(a, lam1, vdt, k, kT, gamma, dt, n_steps, n_equil, stride, seed, uid, x0, _dp(xo), _dp(wo))
+    return xo[:ns], wo[:ns]
 
 
 def od1d_run(a, lam, k, kT, gamma, dt, n_steps, n_equil, stride, seed, uid, x0, step0=0):

@@ -387,6 +387,66 @@ long orc_chain_run_from(const orc_chain *c, double lambda, double k, double kT, 
     return ns;
 }
 
+/* Constant-velocity pulling (the steered-MD comparator of Sec. I): n_equil
+ * BAOAB steps with the trap at lambda1, then the trap centre advances by
+ * vdt per step: at the force evaluation that ends step n (time n + 1) it
+ * sits at lambda(n + 1) = lambda1 + vdt (n + 1 - n_equil) for n + 1 > n_equil,
+ * and the move from lambda(n) to lambda(n + 1) does the work of Eq. (9) at
+ * the reaction coordinate of that moment,
+ *   k/2 (lambda(n+1) - lambda(n)) (lambda(n+1) + lambda(n) - 2 x),
+ * the discrete form of -v k int (x - lambda1 - v t) dt.  Every `stride` steps
+ * of pulling, x and the accumulated work are recorded. */
+long orc_chain_smd(const orc_chain *c, double lambda1, double vdt, double k, double kT, double dt, double gamma,
+                   long n_steps, long n_equil, long stride, uint64_t seed, uint32_t uid,
+                   double *r, double *v, double *x_out, double *w_out)
+{
+    const int n = c->n;
+    double *f = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *xi = (double *)malloc(sizeof(double) * 4 * (size_t)((3 * n + 3) / 4));
+    if (!f || !xi) { free(f); free(xi); return -1; }
+    orc_chain_init_velocities(c, kT, seed, uid, v);
+    const double c1 = exp(-gamma * dt);
+    const double c2 = sqrt(1.0 - c1 * c1);
+    double lam = lambda1, work = 0.0;
+    orc_chain_forces(c, r, lam, k, f);
+    long ns = 0;
+    for (long step = 0; step < n_steps; ++step) {
+        dof_normals(n, seed, uid, (uint32_t)step, ORC_TAG_OSTEP, xi);
+        for (int i = 0; i < n; ++i) {
+            double im = 1.0 / c->mass[i];
+            double sv = sqrt(kT * im);
+            for (int a = 0; a < 3; ++a) {
+                double *vv = v + 3 * i + a, *rr = r + 3 * i + a;
+                *vv += 0.5 * dt * f[3 * i + a] * im;
+                *rr += 0.5 * dt * (*vv);
+                *vv = c1 * (*vv) + c2 * sv * xi[3 * i + a];
+                *rr += 0.5 * dt * (*vv);
+            }
+        }
+        const long done = step + 1;
+        if (done > n_equil) {
+            const double lam_new = lambda1 + vdt * (double)(done - n_equil);
+            const double x = orc_chain_rc(c, r);
+            work += 0.5 * k * (lam_new - lam) * (lam_new + lam - 2.0 * x);
+            lam = lam_new;
+        }
+        orc_chain_forces(c, r, lam, k, f);
+        for (int i = 0; i < n; ++i) {
+            double im = 1.0 / c->mass[i];
+            for (int a = 0; a < 3; ++a) v[3 * i + a] += 0.5 * dt * f[3 * i + a] * im;
+        }
+        if (done > n_equil && (done - n_equil) % stride == 0) {
+            x_out[ns] = orc_chain_rc(c, r);
+            w_out[ns] = work;
+            ++ns;
+        }
+        if (!isfinite(r[0]) || !isfinite(r[3 * (n - 1)])) { free(f); free(xi); return -1; }
+    }
+    free(f);
+    free(xi);
+    return ns;
+}
+
 /* Kinetic energy sum m v^2 / 2. */
 double orc_chain_kinetic(const orc_chain *c, const double *v)
 {
@@ -398,6 +458,38 @@ double orc_chain_kinetic(const orc_chain *c, const double *v)
 /* ------------------------------------------------------------------ */
 /* 1D model                                                             */
 /* ------------------------------------------------------------------ */
+
+double orc_od1d_force(double a, double lambda, double k, double x);
+
+/* Constant-velocity pulling of the 1D model: step n moves x with the trap at
+ * lambda(n) = lambda1 + vdt max(0, n - n_equil); before step n (n > n_equil)
+ * the trap moves from lambda(n - 1) with the work of Eq. (9) at the current
+ * x.  Records x and the accumulated work every `stride` steps of pulling. */
+long orc_od1d_smd(double a, double lambda1, double vdt, double k, double kT, double gamma, double dt,
+                  long n_steps, long n_equil, long stride, uint64_t seed, uint32_t uid, double x0,
+                  double *x_out, double *w_out)
+{
+    double x = x0, lam = lambda1, work = 0.0;
+    double xi[4] = {0, 0, 0, 0};
+    const double amp = sqrt(2.0 * kT * dt / gamma);
+    long ns = 0;
+    for (long step = 0; step < n_steps; ++step) {
+        if (step > n_equil) {
+            const double lam_new = lambda1 + vdt * (double)(step - n_equil);
+            work += 0.5 * k * (lam_new - lam) * (lam_new + lam - 2.0 * x);
+            lam = lam_new;
+        }
+        if ((step & 3) == 0) orc_normals4(seed, 0u, uid, (uint32_t)(step >> 2), ORC_TAG_OSTEP, xi);
+        x = x + orc_od1d_force(a, lam, k, x) * dt / gamma + amp * xi[step & 3];
+        const long done = step + 1;
+        if (done > n_equil && (done - n_equil) % stride == 0) {
+            x_out[ns] = x;
+            w_out[ns] = work;
+            ++ns;
+        }
+    }
+    return ns;
+}
 
 /* Force of U(x) = a (x^2 - 1)^2 plus the trap k/2 (x - lambda)^2. */
 double orc_od1d_force(double a, double lambda, double k, double x)

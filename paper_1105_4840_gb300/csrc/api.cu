@@ -74,6 +74,8 @@ struct pmf_run {
     std::vector<unsigned> graph_gen;   // schedule generation per item at capture time
     int chain = 0, n_windows = 0, replicas = 0, stride = 1;
     bool sequential = false;  // sequential protocol: replicas visit the windows in order
+    double smd_vdt = 0;       // constant-velocity pulling: trap advance per step
+    double *d_w = nullptr;    // constant-velocity pulling: work at the records
     double k = 0, kT = 1, dt = 0, gamma = 1, timeout_s = 0;
     unsigned long long seed = 0;
     uint32_t uid_base = 0;
@@ -109,6 +111,7 @@ struct pmf_run {
         cudaFree(d_start);
         cudaFree(d_queue);
         cudaFree(d_done);
+        cudaFree(d_w);
         if (done) cudaEventDestroy(done);
         if (graph) cudaGraphExecDestroy(graph);
         if (cap) cudaStreamDestroy(cap);
@@ -361,6 +364,8 @@ static cudaError_t enqueue_item(pmf_run *run, const RunItem &ri, cudaStream_t st
     L.start = run->d_start;
     L.queue = run->d_queue;  // set for single-item chain runs only
     L.done = run->d_done;
+    L.wout = run->d_w;       // set for pulled runs only
+    L.smd_vdt = run->smd_vdt;
     L.replicas = run->replicas;
     L.stride = run->stride;
     L.uid_base = run->uid_base + (uint32_t)(ri.w0 * run->replicas);
@@ -486,6 +491,60 @@ pmf_status pmf_run_wait(pmf_run *run)
     CK(cudaMemcpy(&err, run->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read flag");
     run->finished = true;
     if (err) return fail(PMF_ENUMERIC, "a trajectory became non-finite");
+    return PMF_OK;
+}
+
+pmf_status pmf_run_prepare_smd(pmf_system *sys, double lambda1, double velocity, const pmf_run_params *p,
+                               pmf_run **out)
+{
+    if (!p || !out) return fail(PMF_EINVAL, "pmf_run_prepare_smd: null argument");
+    if (!std::isfinite(lambda1) || !std::isfinite(velocity)) return fail(PMF_EINVAL, "lambda1 and velocity must be finite");
+    if (p->n_steps_per_window) return fail(PMF_EINVAL, "pmf_run_prepare_smd: one pull, no per-window steps");
+    if (pmf_status st = pmf_run_prepare(sys, &lambda1, 1, p, out)) return st;
+    pmf_run *run = *out;
+    run->smd_vdt = velocity * p->dt;
+    cudaError_t e = cudaMalloc(&run->d_w, sizeof(double) * (size_t)run->total);
+    if (e != cudaSuccess) {
+        pmf_destroy_run(run);
+        *out = nullptr;
+        return cuda_fail(e, "alloc work records");
+    }
+    return PMF_OK;
+}
+
+pmf_status pmf_smd_work(const pmf_run *run, double *out, size_t capacity, size_t *n_written)
+{
+    if (pmf_status s = need_finished(run)) return s;
+    if (!run->d_w) return fail(PMF_EINVAL, "pmf_smd_work: not a pulled run");
+    if (n_written) *n_written = (size_t)run->total;
+    if (!out || capacity < (size_t)run->total) return fail(PMF_EINVAL, "pmf_smd_work: capacity too small");
+    CK(cudaMemcpyAsync(out, run->d_w, sizeof(double) * run->total, cudaMemcpyDeviceToHost, g_stream), "copy");
+    CK(cudaStreamSynchronize(g_stream), "sync");
+    return PMF_OK;
+}
+
+pmf_status pmf_smd_free_energy(const pmf_run *run, double *lambda, double *dF_JE, double *dF_cumulant,
+                               double *W_mean, double *W_var, double *mean_x, int capacity)
+{
+    if (pmf_status s = need_finished(run)) return s;
+    if (!run->d_w) return fail(PMF_EINVAL, "pmf_smd_free_energy: not a pulled run");
+    const long long T = run->tw[0];
+    if (capacity < T) return fail(PMF_EINVAL, "pmf_smd_free_energy: capacity smaller than the records");
+    double *d_out = nullptr;
+    CK(cudaMalloc(&d_out, sizeof(double) * 5 * (size_t)T), "alloc");
+    cudaError_t e = smd_stats_launch(run->d_w, run->d_x, run->replicas, T, run->kT, d_out, g_stream);
+    std::vector<double> h(5 * (size_t)T);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), d_out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    cudaFree(d_out);
+    if (e != cudaSuccess) return cuda_fail(e, "pmf_smd_free_energy");
+    double *dst[5] = {dF_JE, dF_cumulant, W_mean, W_var, mean_x};
+    for (int q = 0; q < 5; ++q)
+        if (dst[q]) std::memcpy(dst[q], h.data() + (size_t)q * T, sizeof(double) * T);
+    if (lambda)
+        for (long long j = 0; j < T; ++j)
+            lambda[j] = run->lambda[0] + run->smd_vdt * (double)((j + 1) * run->stride);
     return PMF_OK;
 }
 

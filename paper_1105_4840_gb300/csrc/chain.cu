@@ -59,6 +59,9 @@ template <typename R> struct ChainArgs {
     int *done;                 // persistent mode: [n_rep] segments finished (zeroed)
     long long n_items;         // persistent mode: n_rep x segments
     int n_rep, seg_steps, persistent;
+    double *wout;              // constant-velocity pulling: accumulated work at the records
+    int smd;                   // constant-velocity pulling: the trap advances smd_vdt per step
+    double smd_vdt;            //   after the window's equilibration
     int sequential;            // sequential protocol: every simulation visits the windows in order,
     long long window_steps;    //   window_steps steps each, in subs_per_window segments of
     int subs_per_window;       //   at most seg_steps steps
@@ -569,6 +572,26 @@ __host__ __device__ __forceinline__ int early_noise_blocks(int N, int n_tiles, i
     return idle * 32 < nblk ? idle * 32 : nblk;
 }
 
+// Constant-velocity pulling: trap centre at time `done` (steps completed).
+__device__ __forceinline__ double smd_lambda(double lam1, double vdt, long long done, long long nequil)
+{
+    return done > nequil ? lam1 + vdt * (double)(done - nequil) : lam1;
+}
+
+// The accumulated work of a pulled replica lives in the unused fourth
+// components of the first two velocity records (carried through the state
+// record between launches and segments): FP64 directly, FP32 as an
+// unevaluated sum hi + lo of two floats (about 48 bits).
+__device__ __forceinline__ double work_get(const Smem<float> &s) { return (double)s.vel[0].w + (double)s.vel[1].w; }
+__device__ __forceinline__ void work_set(const Smem<float> &s, double W)
+{
+    const float hi = (float)W;
+    s.vel[0].w = hi;
+    s.vel[1].w = (float)(W - (double)hi);
+}
+__device__ __forceinline__ double work_get(const Smem<double> &s) { return s.vel[0].w; }
+__device__ __forceinline__ void work_set(const Smem<double> &s, double W) { s.vel[0].w = W; }
+
 template <typename R, int NW>
 __device__ __forceinline__ void force_phase(const ChainArgs<R> &a, const Smem<R> &s, R lam, long long done,
                                             long long nequil, long long sample_base, bool first, uint32_t uid)
@@ -580,8 +603,22 @@ __device__ __forceinline__ void force_phase(const ChainArgs<R> &a, const Smem<R>
         const R x = bonded_owner(a, s, t, lam);
         if (t == a.N - 1) {
             if (!(x == x) || x > R(1e30)) *s.flag = 1;
-            if (!first && done > nequil && (done - nequil) % a.stride == 0)
+            double W = 0.0;
+            if (a.smd) {
+                // the trap moved from lambda(done - 1) to lambda(done) = lam at
+                // this x: the work of Eq. (9)
+                W = work_get(s);
+                if (!first && done > nequil) {
+                    const double ln = smd_lambda(a.lambda[0], a.smd_vdt, done, nequil);
+                    const double lo = smd_lambda(a.lambda[0], a.smd_vdt, done - 1, nequil);
+                    W += 0.5 * (double)a.k * (ln - lo) * (ln + lo - 2.0 * (double)x);
+                    work_set(s, W);
+                }
+            }
+            if (!first && done > nequil && (done - nequil) % a.stride == 0) {
                 a.xout[sample_base + (done - nequil) / a.stride - 1] = (float)x;
+                if (a.smd) a.wout[sample_base + (done - nequil) / a.stride - 1] = W;
+            }
         }
     }
     if (a.nonbonded) {
@@ -689,7 +726,8 @@ __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s
     }
     const long long nequil = origin + a.nequil_w[w];  // equilibration counts from the window's first step
     const long long sample_base = a.off_w[w] + (long long)r * a.tw[w];
-    force_phase<R, NW>(a, s, lam, s0, nequil, sample_base, true, uid);
+    force_phase<R, NW>(a, s, a.smd ? (R)smd_lambda(a.lambda[0], a.smd_vdt, s0, nequil) : lam, s0, nequil,
+                       sample_base, true, uid);
     __syncthreads();
 
     const int warp = tid >> 5, lane = tid & 31;
@@ -748,7 +786,8 @@ __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s
                          (NW - a.n_tiles) * 32);
         if (step >= s1) break;
         __syncthreads();
-        force_phase<R, NW>(a, s, lam, step + 1, nequil, sample_base, false, uid);
+        force_phase<R, NW>(a, s, a.smd ? (R)smd_lambda(a.lambda[0], a.smd_vdt, step + 1, nequil) : lam, step + 1,
+                           nequil, sample_base, false, uid);
         __syncthreads();
         if (*s.flag) {
             if (tid == 0) atomicOr(a.err, kErrNonFinite);
@@ -1191,6 +1230,9 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     a.done = L.done;
     a.n_rep = L.n_blocks;
     a.seg_steps = m->seg_steps;
+    a.wout = L.wout;
+    a.smd = L.smd_vdt != 0.0 || L.wout != nullptr ? 1 : 0;
+    a.smd_vdt = L.smd_vdt;
     a.persistent = 0;
     a.sequential = L.sequential ? 1 : 0;
     a.window_steps = L.window_steps;

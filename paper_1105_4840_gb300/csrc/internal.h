@@ -53,6 +53,10 @@ struct RunLaunch {
     // window_steps steps (steps [0, n_windows x window_steps)); persistent only
     bool sequential = false;
     long long window_steps = 0;
+    // constant-velocity pulling (one window): the trap advances smd_vdt per
+    // step after the equilibration; accumulated work recorded into wout
+    double smd_vdt = 0;
+    double *wout = nullptr;
     long long step_begin = 0, step_end = 0;
     int replicas = 0, stride = 1, n_blocks = 0;
     uint32_t uid_base = 0;
@@ -115,6 +119,10 @@ cudaError_t reduce_launch(const ReduceLayout &L, void *scratch, double *out, cud
 // sum (x - lambda_i)^2}; combine turns them into the results (window_scratch:
 // >= reduce_scratch_bytes - partial_bytes).
 constexpr int kPartialDoubles = 5;
+// Constant-velocity pulling estimators per record j of T: out[5][T] =
+// {JE, mean - var / 2kT, mean work, work variance (divisor R), mean x}.
+cudaError_t smd_stats_launch(const double *W, const float *x, int R, long long T, double kT, double *out,
+                             cudaStream_t st);
 size_t partial_bytes(int n_windows, int replicas);
 cudaError_t partials_launch(const ReduceLayout &L, void *partials, cudaStream_t st);
 cudaError_t combine_launch(const ReduceLayout &L, const void *partials, void *window_scratch, double *out,

@@ -22,6 +22,8 @@ struct Od1dArgs {
     unsigned long long seed;
     int sequential, n_windows;  // sequential protocol: each thread visits every window
     long long window_steps;     //   for window_steps steps, in order
+    double *wout;               // constant-velocity pulling: work at the records
+    double smd_vdt;             //   trap advance per step after the equilibration
 };
 
 // Sequential pulling protocol (Sec. III (i)): simulation r visits the
@@ -69,14 +71,26 @@ __global__ void od1d_kernel(const Od1dArgs a)
     const double amp = sqrt(2.0 * a.kT * a.dt / a.gamma);
     const long long base = a.off_w[w] + (long long)r * a.tw[w];
     Normal4<double> n = philox_normals<double>(a.seed, 0u, uid, (uint32_t)(s0 >> 2), kTagOStep);
+    // constant-velocity pulling: before step m > nequil the trap moves to
+    // lam + vdt (m - nequil) with the work of Eq. (9) at the current x
+    // (one launch covers the whole run, so the work lives in a register)
+    double lam_now = lam, W = 0.0;
     for (long long step = s0; step < s1; ++step) {
+        if (a.wout && step > nequil) {
+            const double ln = lam + a.smd_vdt * (double)(step - nequil);
+            W += 0.5 * a.k * (ln - lam_now) * (ln + lam_now - 2.0 * x);
+            lam_now = ln;
+        }
         const int lane = (int)(step & 3);
         if (lane == 0) n = philox_normals<double>(a.seed, 0u, uid, (uint32_t)(step >> 2), kTagOStep);
         const double xi = lane == 0 ? n.n0 : (lane == 1 ? n.n1 : (lane == 2 ? n.n2 : n.n3));
-        const double f = -4.0 * a.a * x * (x * x - 1.0) - a.k * (x - lam);
+        const double f = -4.0 * a.a * x * (x * x - 1.0) - a.k * (x - lam_now);
         x = x + f * a.dt / a.gamma + amp * xi;
         const long long done = step + 1;
-        if (done > nequil && (done - nequil) % a.stride == 0) a.xout[base + (done - nequil) / a.stride - 1] = (float)x;
+        if (done > nequil && (done - nequil) % a.stride == 0) {
+            a.xout[base + (done - nequil) / a.stride - 1] = (float)x;
+            if (a.wout) a.wout[base + (done - nequil) / a.stride - 1] = W;
+        }
     }
     if (!isfinite(x)) atomicOr(a.err, kErrNonFinite);
     a.state[rep] = x;
@@ -109,6 +123,9 @@ cudaError_t od1d_launch(const Od1dParams &m, const RunLaunch &L, int n_rep, cuda
     a.seed = L.seed;
     a.sequential = L.sequential ? 1 : 0;
     a.window_steps = L.window_steps;
+    a.wout = L.wout;
+    a.smd_vdt = L.smd_vdt;
+    if (L.wout && L.step_begin != 0) return cudaErrorInvalidValue;  // pulled runs are one launch
     a.n_windows = L.sequential ? (int)(L.step_end / L.window_steps) : 0;
     if (L.sequential && (L.window_steps < 1 || L.step_begin != 0)) return cudaErrorInvalidValue;
     const int threads = 128;

@@ -254,6 +254,50 @@ cudaError_t combine_launch(const ReduceLayout &L, const void *P, void *window_sc
     return cudaGetLastError();
 }
 
+// Constant-velocity pulling, record j (one block each): over the replicas,
+// the Jarzynski average of the accumulated work, its mean and variance (the
+// second-order cumulant estimate) and the mean reaction coordinate.
+__global__ void __launch_bounds__(kWindowThreads) smd_stats_kernel(const double *W, const float *x, int R, long long T,
+                                                                   double kT, double *out)
+{
+    __shared__ double red[kWindowThreads / 32 + 1];
+    const long long j = blockIdx.x;
+    double m = INFINITY;
+    for (int r = threadIdx.x; r < R; r += kWindowThreads) m = fmin(m, W[(size_t)r * T + j]);
+    m = block_min<kWindowThreads>(m, red);
+    double se = 0, ce = 0, sw = 0, cw = 0, sx = 0, cx = 0;
+    for (int r = threadIdx.x; r < R; r += kWindowThreads) {
+        const double w = W[(size_t)r * T + j];
+        neumaier(se, ce, exp(-(w - m) / kT));
+        neumaier(sw, cw, w);
+        neumaier(sx, cx, (double)x[(size_t)r * T + j]);
+    }
+    const double S = block_sum<kWindowThreads>(se + ce, red);
+    const double mean = block_sum<kWindowThreads>(sw + cw, red) / R;
+    const double mx = block_sum<kWindowThreads>(sx + cx, red) / R;
+    double sv = 0, cv = 0;
+    for (int r = threadIdx.x; r < R; r += kWindowThreads) {
+        const double d = W[(size_t)r * T + j] - mean;
+        neumaier(sv, cv, d * d);
+    }
+    const double var = block_sum<kWindowThreads>(sv + cv, red) / R;
+    if (threadIdx.x == 0) {
+        out[0 * T + j] = m - kT * log(S / R);
+        out[1 * T + j] = mean - var / (2.0 * kT);
+        out[2 * T + j] = mean;
+        out[3 * T + j] = var;
+        out[4 * T + j] = mx;
+    }
+}
+
+cudaError_t smd_stats_launch(const double *W, const float *x, int R, long long T, double kT, double *out,
+                             cudaStream_t st)
+{
+    if (T < 1) return cudaSuccess;
+    smd_stats_kernel<<<(unsigned)T, kWindowThreads, 0, st>>>(W, x, R, T, kT, out);
+    return cudaGetLastError();
+}
+
 size_t partial_bytes(int n_windows, int replicas) { return sizeof(Partial) * (size_t)n_windows * replicas; }
 
 cudaError_t reduce_launch(const ReduceLayout &L, void *scratch, double *out, cudaStream_t st)

@@ -97,6 +97,9 @@ def _load():
         getattr(L, name).argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.POINTER(P)]
     L.pmf_run_prepare_seeded.argtypes = [P, _D, C.c_int, C.POINTER(RunParams), _D, C.POINTER(P)]
     L.pmf_run_prepare_sequential.argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.POINTER(P)]
+    L.pmf_run_prepare_smd.argtypes = [P, C.c_double, C.c_double, C.POINTER(RunParams), C.POINTER(P)]
+    L.pmf_smd_work.argtypes = [P, _D, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.pmf_smd_free_energy.argtypes = [P, _D, _D, _D, _D, _D, _D, C.c_int]
     L.pmf_run_batch_prepare.argtypes = [P, C.POINTER(BatchItem), C.c_int, C.POINTER(RunParams), C.POINTER(P)]
     L.pmf_free_energy_item.argtypes = [P, C.c_int, C.POINTER(FreeEnergyResult)]
     L.pmf_run_launch.argtypes = [P]
@@ -140,7 +143,7 @@ def _load():
     L.pmf_last_error.restype = C.c_char_p
     L.pmf_version.restype = C.c_char_p
     for name in ("pmf_create_system", "pmf_run_windows", "pmf_run_prepare", "pmf_run_prepare_seeded", "pmf_run_batch_prepare",
-                 "pmf_run_prepare_sequential",
+                 "pmf_run_prepare_sequential", "pmf_run_prepare_smd", "pmf_smd_work", "pmf_smd_free_energy",
                  "pmf_free_energy_item", "pmf_run_launch",
                  "pmf_run_wait", "pmf_get_run_info", "pmf_x_samples", "pmf_work_samples",
                  "pmf_free_energy", "pmf_free_energy_from_samples", "pmf_final_state",
@@ -308,6 +311,21 @@ class Run:
                "pmf_work_distributions")
         return {"omega": om, "dF_JE": dF, "var_ZW": var, "lost": lost}
 
+    def smd_work(self):
+        """Accumulated work [replicas, records] of a pulled run."""
+        n = C.c_size_t()
+        lib.pmf_smd_work(self.handle, None, 0, C.byref(n))
+        out = np.zeros(n.value)
+        _check(lib.pmf_smd_work(self.handle, _dp(out), out.size, C.byref(n)), "pmf_smd_work")
+        return out.reshape(self.info()["replicas"], -1)
+
+    def smd_free_energy(self):
+        T = int(self.info()["samples_per_window"][0])
+        names = ("lambda", "dF_JE", "dF_cumulant", "W_mean", "W_var", "mean_x")
+        arrs = {k: np.zeros(T) for k in names}
+        _check(lib.pmf_smd_free_energy(self.handle, *[_dp(arrs[k]) for k in names], T), "pmf_smd_free_energy")
+        return arrs
+
     def partials(self):
         """Per-replica partial sums [n_windows, replicas, 5] (pmf_run_partials)."""
         n = C.c_size_t()
@@ -349,6 +367,16 @@ def pmf_run_prepare_sequential(system: System, lambdas, params) -> Run:
     _check(lib.pmf_run_prepare_sequential(system.handle, _dp(lam), lam.size, C.byref(p), C.byref(h)),
            "pmf_run_prepare_sequential")
     return Run(h, lam, keep=(p, keep, system))
+
+
+def pmf_run_prepare_smd(system: System, lambda1, velocity, params) -> Run:
+    """Constant-velocity pulling: params.replicas simulations, the trap at
+    lambda1 for params.n_equil steps, then advancing velocity * dt per step."""
+    p, keep = params
+    h = C.c_void_p()
+    _check(lib.pmf_run_prepare_smd(system.handle, float(lambda1), float(velocity), C.byref(p), C.byref(h)),
+           "pmf_run_prepare_smd")
+    return Run(h, np.array([lambda1]), keep=(p, keep, system))
 
 
 def pmf_run_prepare_seeded(system: System, lambdas, params, start) -> Run:

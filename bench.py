@@ -520,6 +520,41 @@ def bench_sweeps(args, pmf, torch, stream):
     print(json.dumps(line), flush=True)
 
 
+def bench_smd(args, pmf, torch, stream):
+    """Constant-velocity pulling of the 104-bead chain from 1.3 to 3.3 nm:
+    `--replicas` trajectories (672 by default), 10 % of `--md-steps` at the
+    start position, then the trap moves 2 nm over the remaining steps."""
+    w = _workload(args.md_steps)
+    p, start, run = w["params"], w["start"], w["run"]
+    run.replicas = args.replicas
+    run.n_equil = run.n_steps // 10
+    v = 2.0 / ((run.n_steps - run.n_equil) * run.dt)  # nm / ps
+    sysh = pmf.pmf_create_system_chain([p], [start])
+    rr = pmf.pmf_run_prepare_smd(sysh, 1.3, v, pmf.make_params(run))
+    for _ in range(args.warmup):
+        rr.launch()
+        rr.wait()
+    times = []
+    for _ in range(args.steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        rr.launch()
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        times.append(e[0].elapsed_time(e[1]))
+    rr.wait()
+    res = rr.smd_free_energy()
+    steps = run.replicas * run.n_steps
+    t = statistics.mean(times)
+    line = {"workload": "chain104_smd", "metric": "replica-steps/s", "value": steps / (t / 1000.0),
+            "unit": "replica-steps/s", "ms_per_step": t, "trajectories": run.replicas, "md_steps": run.n_steps,
+            "velocity_nm_per_ns": v * 1000.0, "lambda_end": float(res["lambda"][-1]),
+            "dF_JE_end": float(res["dF_JE"][-1]), "dF_cumulant_end": float(res["dF_cumulant"][-1]),
+            "W_mean_end": float(res["W_mean"][-1]), "W_sd_end": float(math.sqrt(res["W_var"][-1]))}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -529,7 +564,8 @@ def main():
     ap.add_argument("--md-steps", type=int, default=400000, help="BAOAB steps per window (workload: 4e5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="chain104",
-                    choices=["chain104", "batch64", "precision", "adaptive", "mlp", "spp", "histograms", "sweeps"],
+                    choices=["chain104", "batch64", "precision", "adaptive", "mlp", "spp", "histograms", "sweeps",
+                             "smd"],
                     help="chain104: the 104-bead PPP (default); batch64: 64 uneven chains in one graph; "
                          "precision: FP32 vs FP64 integration study")
     ap.add_argument("--replicas", type=int, default=1024, help="replicas per window (precision study)")
@@ -569,6 +605,12 @@ def main():
     if args.workload == "batch64":
         if world == 1:
             bench_batch(args, pmf, torch, stream)
+        return
+    if args.workload == "smd":
+        if world == 1:
+            if args.replicas == 1024:
+                args.replicas = 672
+            bench_smd(args, pmf, torch, stream)
         return
     if args.workload == "sweeps":
         if world == 1:

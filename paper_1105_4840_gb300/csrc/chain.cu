@@ -592,7 +592,7 @@ __device__ __forceinline__ void work_set(const Smem<float> &s, double W)
 __device__ __forceinline__ double work_get(const Smem<double> &s) { return s.vel[0].w; }
 __device__ __forceinline__ void work_set(const Smem<double> &s, double W) { s.vel[0].w = W; }
 
-template <typename R, int NW>
+template <typename R, int NW, bool SMD>
 __device__ __forceinline__ void force_phase(const ChainArgs<R> &a, const Smem<R> &s, R lam, long long done,
                                             long long nequil, long long sample_base, bool first, uint32_t uid)
 {
@@ -604,7 +604,7 @@ __device__ __forceinline__ void force_phase(const ChainArgs<R> &a, const Smem<R>
         if (t == a.N - 1) {
             if (!(x == x) || x > R(1e30)) *s.flag = 1;
             double W = 0.0;
-            if (a.smd) {
+            if constexpr (SMD) {
                 // the trap moved from lambda(done - 1) to lambda(done) = lam at
                 // this x: the work of Eq. (9)
                 W = work_get(s);
@@ -617,7 +617,7 @@ __device__ __forceinline__ void force_phase(const ChainArgs<R> &a, const Smem<R>
             }
             if (!first && done > nequil && (done - nequil) % a.stride == 0) {
                 a.xout[sample_base + (done - nequil) / a.stride - 1] = (float)x;
-                if (a.smd) a.wout[sample_base + (done - nequil) / a.stride - 1] = W;
+                if constexpr (SMD) a.wout[sample_base + (done - nequil) / a.stride - 1] = W;
             }
         }
     }
@@ -662,7 +662,7 @@ template <> __device__ __forceinline__ Vec4<double> load_cg<double>(const Vec4<d
 // state record, and goes back to it at the end, so a replica's trajectory
 // does not depend on how its steps are cut into launches or segments.
 // Returns false when the run was aborted (non-finite state).
-template <typename R, int NW>
+template <typename R, int NW, bool SMD>
 __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s, int rep, int w, int r,
                                          long long s0, long long s1, long long origin)
 {
@@ -726,8 +726,8 @@ __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s
     }
     const long long nequil = origin + a.nequil_w[w];  // equilibration counts from the window's first step
     const long long sample_base = a.off_w[w] + (long long)r * a.tw[w];
-    force_phase<R, NW>(a, s, a.smd ? (R)smd_lambda(a.lambda[0], a.smd_vdt, s0, nequil) : lam, s0, nequil,
-                       sample_base, true, uid);
+    force_phase<R, NW, SMD>(a, s, SMD ? (R)smd_lambda(a.lambda[0], a.smd_vdt, s0, nequil) : lam, s0, nequil,
+                            sample_base, true, uid);
     __syncthreads();
 
     const int warp = tid >> 5, lane = tid & 31;
@@ -786,8 +786,8 @@ __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s
                          (NW - a.n_tiles) * 32);
         if (step >= s1) break;
         __syncthreads();
-        force_phase<R, NW>(a, s, a.smd ? (R)smd_lambda(a.lambda[0], a.smd_vdt, step + 1, nequil) : lam, step + 1,
-                           nequil, sample_base, false, uid);
+        force_phase<R, NW, SMD>(a, s, SMD ? (R)smd_lambda(a.lambda[0], a.smd_vdt, step + 1, nequil) : lam,
+                                step + 1, nequil, sample_base, false, uid);
         __syncthreads();
         if (*s.flag) {
             if (tid == 0) atomicOr(a.err, kErrNonFinite);
@@ -848,9 +848,11 @@ __device__ long long next_item(const ChainArgs<R> &a)
     return (long long)it;
 }
 
-template <typename R, int NW>
+template <typename R, int NW, bool SMD>
 __global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW == 6 ? 4 : 3)) : 1)
     chain_kernel(const ChainArgs<R> a)
+// SMD: the constant-velocity pulling variant (a separate instantiation, so
+// the window runs carry none of its per-step work bookkeeping).
 // FP32 with 4 warps: five CTAs per SM fit; 6 and 8 warps trade occupancy for
 // registers.  Two modes:
 //  * one CTA per replica (blockIdx.x), steps [step_begin, step_end);
@@ -914,7 +916,7 @@ __global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW =
             const long long nsteps = a.nsteps_w[w];
             s1 = s1 < nsteps ? s1 : nsteps;
         }
-        if ((s0 < s1 || a.force_out != nullptr) && !simulate<R, NW>(a, s, rep, w, r, s0, s1, origin)) return;
+        if ((s0 < s1 || a.force_out != nullptr) && !simulate<R, NW, SMD>(a, s, rep, w, r, s0, s1, origin)) return;
         if (a.persistent) {
             __syncthreads();  // the replica's state record is written
             if (threadIdx.x == 0) {
@@ -1231,7 +1233,8 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     a.n_rep = L.n_blocks;
     a.seg_steps = m->seg_steps;
     a.wout = L.wout;
-    a.smd = L.smd_vdt != 0.0 || L.wout != nullptr ? 1 : 0;
+    if (L.smd_vdt != 0.0 && L.wout == nullptr) return cudaErrorInvalidValue;  // a pulled run records its work
+    a.smd = L.wout != nullptr ? 1 : 0;
     a.smd_vdt = L.smd_vdt;
     a.persistent = 0;
     a.sequential = L.sequential ? 1 : 0;
@@ -1246,6 +1249,7 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     }
     a.n_items = 0;
     const size_t smem = chain_smem_bytes<R>(m->geo, NW);
+    void (*kern)(const ChainArgs<R>) = a.smd ? chain_kernel<R, NW, true> : chain_kernel<R, NW, false>;
     // The attribute is the kernel's upper limit, shared by every chain that
     // launches it: raise it to the device's opt-in maximum rather than to this
     // chain's size, so launches captured earlier in a graph (other chains,
@@ -1255,10 +1259,10 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     cudaFuncAttributes fa{};
-    if ((e = cudaFuncGetAttributes(&fa, chain_kernel<R, NW>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
     const int dyn_max = optin - (int)fa.sharedSizeBytes;  // static + dynamic <= opt-in limit
     if (smem > (size_t)dyn_max) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(chain_kernel<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
     if (e != cudaSuccess) return e;
     int grid = L.n_blocks;
     if (L.sequential && (L.queue == nullptr || L.done == nullptr || L.window_steps < 1 || L.step_begin != 0))
@@ -1268,7 +1272,7 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
         // persistent: as many CTAs as fit at once (or as requested), never
         // more than there are replicas
         int occ = 0, sms = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chain_kernel<R, NW>, NW * 32, smem)) !=
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NW * 32, smem)) !=
             cudaSuccess)
             return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -1290,7 +1294,7 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
         if ((e = cudaMemsetAsync(L.queue, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(L.done, 0, sizeof(int) * (size_t)L.n_blocks, st)) != cudaSuccess) return e;
     }
-    chain_kernel<R, NW><<<grid, NW * 32, smem, st>>>(a);
+    kern<<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 

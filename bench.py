@@ -42,6 +42,14 @@ def flops_per_replica_step(n: int) -> int:
     return 36 * pairs + 20 * (n - 1) + 60 * (n - 2) + 110 * (n - 3) + 33 * n
 
 
+def workload_config(run, world=1):
+    """The `config` of the default line, shared by both arms."""
+    return {"workload": WORKLOAD, "beads": N_BEADS, "windows": int(run.lambdas.size),
+            "replicas_per_window": run.replicas, "md_steps_per_window": run.n_steps, "dt_ps": run.dt,
+            "sample_stride": run.stride, "forces": "fp32", "reductions": "fp64",
+            "parallelism": f"replicas x{world}", "l2": "256 MB flush between timed steps"}
+
+
 def _workload(n_steps=None):
     from paper_1105_4840_gb300 import inputs
 
@@ -173,7 +181,7 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * 21 * 32 * 400000 / v, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "oracle": "FP64 CPU, bounded sample per step"},
+            "config": workload_config(_workload().get("run"), world),
             "cpu_baseline": {**vals[-1], "value": v},
             "e2e": {"value": v, "unit": "replica-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -745,13 +753,9 @@ def main():
     line = {"metric": "replica-steps/s", "value": value, "unit": "replica-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "beads": N_BEADS, "windows": s, "replicas_per_window": R,
-                       "md_steps_per_window": run.n_steps, "dt_ps": run.dt, "sample_stride": run.stride,
-                       "forces": "fp32", "reductions": "fp64", "parallelism": f"replicas x{world}",
-                       "warps_per_replica": warps,
-                       "launch": (f"persistent, {'auto' if grid_ctas == 0 else grid_ctas} CTAs, "
-                                  f"{seg_steps}-step segments"),
-                       "l2": "256 MB flush between timed steps"},
+            "config": workload_config(run, world),
+            "launch": {"warps_per_replica": warps, "ctas": "auto" if grid_ctas == 0 else grid_ctas,
+                       "segment_steps": seg_steps, "mode": "persistent"},
             "e2e": {"value": e2e_value, "unit": "replica-steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * (chunks + 3),

@@ -331,3 +331,39 @@ def test_partials_export_and_shard_merge(pmf):
     want = pmf.pmf_free_energy_from_samples(pooled.astype(np.float32), lam, 2 * run.replicas, [T] * lam.size,
                                             run.k, run.kT)
     _compare_profiles(got, want, run.kT, rel=1e-11)
+
+
+@pytest.mark.parametrize("replicas,warps", [(32, 4), (32, 6), (1024, 4)])
+def test_full_size_launch_sampled_replicas(pmf, replicas, warps):
+    """The 104-bead workload at its full replica counts (21 x 32, and 21 x 1024
+    of the precision study) in the benchmark's launch configuration
+    (persistent grid, autotuned warp counts), shortened to 300 steps in
+    100-step segments so two segment hand-overs occur while the FP32 and FP64
+    trajectories still agree closely (chaos amplifies rounding differences
+    by roughly e per 0.1 ps): sampled replicas of the first, middle and last
+    windows against the oracle."""
+    import concurrent.futures as cf
+    import os
+
+    w = inputs.chain_workload(n_steps=300, replicas=replicas)
+    p, start, run = w["params"], w["start"], w["run"]
+    run.n_equil, run.stride = 100, 50
+    sysh = pmf.pmf_create_system_chain([p], [start])
+    pmf.pmf_chain_set_warps(sysh, 0, warps)
+    pmf.pmf_chain_set_grid(sysh, 0, 0, 100)
+    rr = pmf.pmf_run_windows(sysh, run.lambdas, pmf.make_params(run))
+    pos = rr.final_state()[0].reshape(21, replicas, 104, 3)
+    xs = rr.x_samples()
+    picks = [(0, 0), (10, replicas // 2), (20, replicas - 1), (5, 7 % replicas)]
+    ch = _clib.Chain(p)
+
+    def one(job):
+        wi, r = job
+        xo, ro, _ = ch.run(start, run.lambdas[wi], run.k, run.kT, run.dt, run.gamma, run.n_steps, run.n_equil,
+                           run.stride, run.seed, wi * replicas + r)
+        return np.abs(pos[wi, r] - ro).max(), np.abs(xs[wi][r] - xo).max()
+
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        errs = list(ex.map(one, picks))
+    assert max(e[0] for e in errs) <= 2e-4, errs
+    assert max(e[1] for e in errs) <= 1e-4, errs

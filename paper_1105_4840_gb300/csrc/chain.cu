@@ -101,7 +101,8 @@ template <typename R> struct Smem {
     Vec4<R> *vel;    // [Np]
     Vec4<R> *fw;     // [NW][Np]
     Vec4<R> *bslot;  // [4][Np]
-    R *noise;        // [4 * n_blocks] normals of the next O-step, dof d = 3 b + axis
+    R *noise;        // [2][4 * n_blocks] normals of an O-step (by step parity), dof d = 3 b + axis
+    Vec2<R> *mass;   // [Np] (1/m, c2 sqrt(kT/m)) of the O-step, per run
     // FP32 packed path: entry p of tile T pairs ring positions p and p + D
     // (D = pair_offset(W)): posp[2(64T + p)] = (x_p, x_{p+D}, y_p, y_{p+D}),
     // posp[2(64T + p) + 1] = (z_p, z_{p+D}, s_p, s_{p+D}),
@@ -704,6 +705,8 @@ __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s
         }
         store_pos<R>(s, b, V3<R>{p.x, p.y, p.z}, p.w, a.n_tiles, a.w_last);
         s.vel[b] = v;
+        const R im = a.bead_invm[b];
+        s.mass[b] = Vec2<R>{im, c2 * sqrt(a.kT * im)};
         for (int q = 0; q < NW; ++q) s.fw[q * a.Np + b] = Vec4<R>{0, 0, 0, 0};
         for (int m = 0; m < 4; ++m) s.bslot[m * a.Np + b] = Vec4<R>{0, 0, 0, 0};
     }
@@ -754,20 +757,22 @@ __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s
                     F.x += g.x; F.y += g.y; F.z += g.z;
                     s.fw[q * a.Np + b] = Vec4<R>{0, 0, 0, 0};
                 }
-                const R im = a.bead_invm[b];
+                const Vec2<R> ms = s.mass[b];
+                const R im = ms.x;
                 Vec4<R> v = s.vel[b];
                 if (step > s0) { v.x += hdt * F.x * im; v.y += hdt * F.y * im; v.z += hdt * F.z * im; }
                 if (step < s1) {
-                    V3<R> p = pos_of(s, b);
+                    const Vec4<R> p4 = s.posd[(b >> 5) * 64 + (b & 31)];  // position and sigma/2
+                    V3<R> p{p4.x, p4.y, p4.z};
                     v.x += hdt * F.x * im; v.y += hdt * F.y * im; v.z += hdt * F.z * im;
                     p.x += hdt * v.x; p.y += hdt * v.y; p.z += hdt * v.z;
-                    const R sv = c2 * sqrt(a.kT * im);
+                    const R sv = ms.y;
                     const R *xi = s.noise + (step & 1) * 4 * ((3 * a.N + 3) >> 2) + 3 * b;
                     v.x = c1 * v.x + sv * xi[0];
                     v.y = c1 * v.y + sv * xi[1];
                     v.z = c1 * v.z + sv * xi[2];
                     p.x += hdt * v.x; p.y += hdt * v.y; p.z += hdt * v.z;
-                    sig = a.bead_pos0[b].w;
+                    sig = p4.w;
                     store_pos<R>(s, b, p, sig, a.n_tiles, a.w_last);
                     pnew = p;
                 } else if (a.force_out != nullptr) {
@@ -875,6 +880,7 @@ __global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW =
         s.fw = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * NW;
         s.bslot = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * 4;
         s.noise = reinterpret_cast<R *>(p); p += 2 * sizeof(Vec4<R>) * ((3 * a.N + 3) >> 2);
+        s.mass = reinterpret_cast<Vec2<R> *>(p); p += sizeof(Vec2<R>) * a.Np;
         s.posp = nullptr;
         s.eqp = nullptr;
         if constexpr (kPacked<R>) {
@@ -1030,7 +1036,7 @@ std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed)
 template <typename R> size_t chain_smem_bytes(const ChainGeometry &g, int NW)
 {
     size_t b = sizeof(Vec4<R>) * g.n_tiles * 64 + sizeof(Vec2<R>) * g.n_tiles * 64 + sizeof(Vec4<R>) * g.Np * (1 + NW + 4) +
-               2 * sizeof(Vec4<R>) * ((3 * g.N + 3) / 4) + 16;
+               2 * sizeof(Vec4<R>) * ((3 * g.N + 3) / 4) + sizeof(Vec2<R>) * g.Np + 16;
     if (kPacked<R>) b += sizeof(float4) * 3 * 64 * g.n_tiles;
     return b;
 }

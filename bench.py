@@ -563,6 +563,66 @@ def bench_smd(args, pmf, torch, stream):
     print(json.dumps(line), flush=True)
 
 
+def od1d_cpu_baseline(w):
+    """The FP64 oracle on the whole 1D workload (cpu_baseline leg), one thread
+    per core over the replicas."""
+    import concurrent.futures as cf
+
+    from oracle import _clib
+
+    run = w["run"]
+    cores = os.cpu_count() or 1
+    jobs = [(i, r) for i in range(run.lambdas.size) for r in range(run.replicas)]
+
+    def one(job):
+        i, r = job
+        _clib.od1d_run(w["a"], run.lambdas[i], run.k, run.kT, run.gamma, run.dt, run.n_steps, run.n_equil,
+                       run.stride, run.seed, i * run.replicas + r, w["x0"])
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(one, jobs))
+    el = time.perf_counter() - t0
+    return {"value": len(jobs) * run.n_steps / el, "unit": "replica-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"the whole 1D workload ({len(jobs)} replicas x {run.n_steps} steps, FP64, {el:.2f} s)"}
+
+
+def bench_od1d(args, pmf, torch, stream):
+    """The 1D double-well workload (21 windows x 8 replicas x 2e4 steps,
+    FP64): the whole PPP and its reductions per timed step."""
+    from paper_1105_4840_gb300 import inputs
+
+    w = inputs.od1d_workload()
+    run = w["run"]
+    sysh = pmf.pmf_create_system_1d(w["a"], w["x0"])
+    rr = pmf.pmf_run_prepare(sysh, run.lambdas, pmf.make_params(run))
+    for _ in range(args.warmup):
+        rr.launch()
+        rr.reduce()
+        rr.wait()
+    times = []
+    for _ in range(args.steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        rr.launch()
+        rr.reduce()
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        times.append(e[0].elapsed_time(e[1]))
+    rr.wait()
+    res = rr.free_energy()
+    t = statistics.median(times)
+    steps = run.lambdas.size * run.replicas * run.n_steps
+    line = {"workload": "od1d_ppp", "metric": "replica-steps/s", "value": steps / (t / 1000.0),
+            "unit": "replica-steps/s", "ms_per_step": t, "dtype": "f64", "windows": int(run.lambdas.size),
+            "replicas_per_window": run.replicas, "md_steps_per_window": run.n_steps,
+            "dF_JE_end": float(res["dF_JE"][-1]), "dF_JE_min": float(res["dF_JE"].min())}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = od1d_cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -573,7 +633,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="chain104",
                     choices=["chain104", "batch64", "precision", "adaptive", "mlp", "spp", "histograms", "sweeps",
-                             "smd"],
+                             "smd", "od1d"],
                     help="chain104: the 104-bead PPP (default); batch64: 64 uneven chains in one graph; "
                          "precision: FP32 vs FP64 integration study")
     ap.add_argument("--replicas", type=int, default=1024, help="replicas per window (precision study)")
@@ -613,6 +673,10 @@ def main():
     if args.workload == "batch64":
         if world == 1:
             bench_batch(args, pmf, torch, stream)
+        return
+    if args.workload == "od1d":
+        if world == 1:
+            bench_od1d(args, pmf, torch, stream)
         return
     if args.workload == "smd":
         if world == 1:

@@ -76,6 +76,8 @@ struct pmf_run {
     bool sequential = false;  // sequential protocol: replicas visit the windows in order
     double smd_vdt = 0;       // constant-velocity pulling: trap advance per step
     double *d_w = nullptr;    // constant-velocity pulling: work at the records
+    double *d_noise = nullptr;  // 1D model: normals of a block of steps
+    long long noise_steps = 0;
     double k = 0, kT = 1, dt = 0, gamma = 1, timeout_s = 0;
     unsigned long long seed = 0;
     uint32_t uid_base = 0;
@@ -112,6 +114,7 @@ struct pmf_run {
         cudaFree(d_queue);
         cudaFree(d_done);
         cudaFree(d_w);
+        cudaFree(d_noise);
         if (done) cudaEventDestroy(done);
         if (graph) cudaGraphExecDestroy(graph);
         if (cap) cudaStreamDestroy(cap);
@@ -259,7 +262,8 @@ static pmf_status prepare_items(pmf_system *sys, const pmf_batch_item *items, in
         ri.chain = sys->model == PMF_MODEL_CHAIN ? items[it].chain : 0;
         ri.w0 = w0;
         ri.nw = items[it].n_windows;
-        ri.state_stride = sys->model == PMF_MODEL_CHAIN ? sys->chains[ri.chain]->state_bytes_per_replica() : sizeof(double);
+        ri.state_stride =
+            sys->model == PMF_MODEL_CHAIN ? sys->chains[ri.chain]->state_bytes_per_replica() : 2 * sizeof(double);
         ri.state_off = state_off;
         state_off += ri.state_stride * (size_t)(sequential ? 1 : ri.nw) * p->replicas;
         run->items.push_back(ri);
@@ -297,6 +301,12 @@ static pmf_status prepare_items(pmf_system *sys, const pmf_batch_item *items, in
     CK(cudaMalloc(&run->d_res, sizeof(double) * kResFields * max_nw), "alloc results");
     CK(cudaEventCreateWithFlags(&run->done, cudaEventDisableTiming), "event");
     CK(cudaStreamCreateWithFlags(&run->cap, cudaStreamNonBlocking), "capture stream");
+    if (sys->model == PMF_MODEL_1D_DOUBLEWELL) {
+        // one noise block per item (a batch's items run concurrently)
+        const long long sims = sequential ? p->replicas : (long long)n_windows * p->replicas;
+        run->noise_steps = od1d_noise_steps((int)std::min<long long>(sims, 1 << 30));
+        CK(cudaMalloc(&run->d_noise, sizeof(double) * (size_t)run->noise_steps * sims), "alloc noise");
+    }
     if (n_items == 1 && sys->model == PMF_MODEL_CHAIN) {
         CK(cudaMalloc(&run->d_queue, sizeof(unsigned long long)), "alloc queue");
         CK(cudaMalloc(&run->d_done, sizeof(int) * (size_t)n_windows * p->replicas), "alloc segment counters");
@@ -366,6 +376,9 @@ static cudaError_t enqueue_item(pmf_run *run, const RunItem &ri, cudaStream_t st
     L.done = run->d_done;
     L.wout = run->d_w;       // set for pulled runs only
     L.smd_vdt = run->smd_vdt;
+    // 1D runs: this item's block of the noise buffer
+    L.noise = run->d_noise ? run->d_noise + (size_t)run->noise_steps * ri.w0 * run->replicas : nullptr;
+    L.noise_steps = run->noise_steps;
     L.replicas = run->replicas;
     L.stride = run->stride;
     L.uid_base = run->uid_base + (uint32_t)(ri.w0 * run->replicas);
@@ -1168,7 +1181,7 @@ pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, cons
     const int N = chain ? sys->chains[p->chain]->n_beads() : 0;
     const int Np = chain ? sys->chains[p->chain]->n_padded() : 0;
     const bool fp64 = chain && sys->chains[p->chain]->precision() == PMF_FP64;
-    const size_t state_stride = chain ? sys->chains[p->chain]->state_bytes_per_replica() : sizeof(double);
+    const size_t state_stride = chain ? sys->chains[p->chain]->state_bytes_per_replica() : 2 * sizeof(double);
     for (int round = 0; round < ap->max_rounds; ++round) {
         std::sort(win.begin(), win.end(), [&](const Window &a, const Window &b) { return dir * a.lam < dir * b.lam; });
         Merged m;
@@ -1426,7 +1439,9 @@ pmf_status pmf_final_state(const pmf_run *run, double *pos, double *vel, size_t 
     if (run->sys->model == PMF_MODEL_1D_DOUBLEWELL) {
         if (n_written) *n_written = (size_t)n_rep;
         if (!pos || capacity < (size_t)n_rep) return fail(PMF_EINVAL, "pmf_final_state: capacity too small");
-        CK(cudaMemcpy(pos, run->d_state, sizeof(double) * n_rep, cudaMemcpyDeviceToHost), "copy state");
+        std::vector<double> st(2 * (size_t)n_rep);  // (x, pulling work) per simulation
+        CK(cudaMemcpy(st.data(), run->d_state, sizeof(double) * st.size(), cudaMemcpyDeviceToHost), "copy state");
+        for (int q = 0; q < n_rep; ++q) pos[q] = st[2 * (size_t)q];
         return PMF_OK;
     }
     size_t need = 0;

@@ -57,6 +57,9 @@ struct RunLaunch {
     // step after the equilibration; accumulated work recorded into wout
     double smd_vdt = 0;
     double *wout = nullptr;
+    // 1D model: buffer for the normals of noise_steps steps of every simulation
+    double *noise = nullptr;
+    long long noise_steps = 0;
     long long step_begin = 0, step_end = 0;
     int replicas = 0, stride = 1, n_blocks = 0;
     uint32_t uid_base = 0;
@@ -95,7 +98,10 @@ private:
 struct Od1dParams {
     double a = 2.0, x0 = -1.0;
 };
+// Launches the noise pre-pass and the integration per block of noise_steps
+// steps; the state holds x and the pulling work per simulation (2 doubles).
 cudaError_t od1d_launch(const Od1dParams &m, const RunLaunch &L, int n_rep, cudaStream_t st);
+long long od1d_noise_steps(int n_rep);
 
 // FP64 reductions of x samples into the estimators.
 struct ReduceLayout {

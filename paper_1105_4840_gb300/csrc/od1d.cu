@@ -1,5 +1,6 @@
 // Overdamped Langevin particle in the 1D double well, FP64, one thread per
-// (window, replica): the PPP of Sec. III (ii) on the model
+// simulation: the PPP of Sec. III (ii) (and the sequential protocol and
+// constant-velocity pulling) on the model
 // H(lambda, x) = a (x^2 - 1)^2 + k/2 (x - lambda)^2 (kT units).
 //   x_{n+1} = x_n + F(x_n) dt / gamma + sqrt(2 kT dt / gamma) xi_n,
 // xi_n = normal (n mod 4) of the Philox block (0, uid, n div 4, 0).
@@ -12,92 +13,138 @@ struct Od1dArgs {
     double a, x0, k, kT, dt, gamma;
     const double *lambda;
     const long long *nsteps_w, *nequil_w, *off_w, *tw;
-    double *state;
+    double *state;              // [n_rep][2]: x and the accumulated pulling work
     const double *start;
     float *xout;
     int *err;
-    long long step_begin, step_end;
+    long long c0, c1;           // this launch's steps
     int replicas, stride, n_rep;
     uint32_t uid_base;
     unsigned long long seed;
-    int sequential, n_windows;  // sequential protocol: each thread visits every window
-    long long window_steps;     //   for window_steps steps, in order
+    int sequential;             // sequential protocol: window = step / window_steps
+    long long window_steps;
     double *wout;               // constant-velocity pulling: work at the records
     double smd_vdt;             //   trap advance per step after the equilibration
+    const double *noise;        // [c1 - c0][n_rep] normals of this launch's steps
 };
 
-// Sequential pulling protocol (Sec. III (i)): simulation r visits the
-// windows in order, window w covering steps [w tau, (w + 1) tau) of one
-// continuous run; equilibration and sampling count from the window's start.
-__device__ void od1d_sequential(const Od1dArgs &a, int r)
+// The normals do not depend on the trajectory, so they are drawn for a block
+// of steps by every thread of the grid at once (one Philox block = four
+// steps of one replica) before the sequential integration reads them.
+__global__ void od1d_noise_kernel(unsigned long long seed, uint32_t uid_base, int n_rep, long long c0, long long c1,
+                                  double *noise)
 {
-    const uint32_t uid = a.uid_base + (uint32_t)r;
-    const double amp = sqrt(2.0 * a.kT * a.dt / a.gamma);
-    double x = a.start ? a.start[r] : a.x0;
-    for (int w = 0; w < a.n_windows; ++w) {
-        const double lam = a.lambda[w];
-        const long long origin = (long long)w * a.window_steps, nequil = a.nequil_w[w];
-        const long long base = a.off_w[w] + (long long)r * a.tw[w];
-        Normal4<double> n = philox_normals<double>(a.seed, 0u, uid, (uint32_t)(origin >> 2), kTagOStep);
-        for (long long step = origin; step < origin + a.window_steps; ++step) {
-            const int lane = (int)(step & 3);
-            if (lane == 0) n = philox_normals<double>(a.seed, 0u, uid, (uint32_t)(step >> 2), kTagOStep);
-            const double xi = lane == 0 ? n.n0 : (lane == 1 ? n.n1 : (lane == 2 ? n.n2 : n.n3));
-            const double f = -4.0 * a.a * x * (x * x - 1.0) - a.k * (x - lam);
-            x = x + f * a.dt / a.gamma + amp * xi;
-            const long long done = step + 1 - origin;
-            if (done > nequil && (done - nequil) % a.stride == 0) a.xout[base + (done - nequil) / a.stride - 1] = (float)x;
-        }
-    }
-    if (!isfinite(x)) atomicOr(a.err, kErrNonFinite);
-    a.state[r] = x;
+    const long long nb = (c1 - c0 + 3) >> 2;  // c0 is a multiple of 4
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= nb * n_rep) return;
+    const int rep = (int)(i % n_rep);
+    const long long blk = i / n_rep;
+    const long long n0 = c0 + 4 * blk;
+    const Normal4<double> z =
+        philox_normals<double>(seed, 0u, uid_base + (uint32_t)rep, (uint32_t)(n0 >> 2), kTagOStep);
+    const double v[4] = {z.n0, z.n1, z.n2, z.n3};
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+        if (n0 + l < c1) noise[(n0 + l - c0) * n_rep + rep] = v[l];
+}
+
+// One thread per simulation, steps [c0, c1): the parallel protocol (window
+// rep / R throughout), the sequential protocol (window = step / tau, Sec.
+// III (i)) or constant-velocity pulling (the trap at lambda_1 + vdt (n -
+// n_equil) from step n_equil on, the move before step n doing the work of
+// Eq. (9) at the current x).
+// First `done` count (steps completed in the window) > from at which a sample
+// is recorded: nequil + m stride, m >= 1.
+__device__ __forceinline__ long long next_sample(long long from, long long nequil, int stride)
+{
+    const long long m = from < nequil + stride ? 1 : (from - nequil) / stride + 1;
+    return nequil + m * stride;
 }
 
 __global__ void od1d_kernel(const Od1dArgs a)
 {
     const int rep = blockIdx.x * blockDim.x + threadIdx.x;
     if (rep >= a.n_rep) return;
-    if (a.sequential) {
-        od1d_sequential(a, rep);
-        return;
-    }
-    const int w = rep / a.replicas, r = rep % a.replicas;
-    const uint32_t uid = a.uid_base + (uint32_t)rep;
-    const double lam = a.lambda[w];
-    const long long nsteps = a.nsteps_w[w], nequil = a.nequil_w[w];
-    const long long s0 = a.step_begin, s1 = a.step_end < nsteps ? a.step_end : nsteps;
-    if (s0 >= s1) return;
-    double x = s0 == 0 ? (a.start ? a.start[rep] : a.x0) : a.state[rep];
+    const int r = a.sequential ? rep : rep % a.replicas;
+    int w = a.sequential ? (int)(a.c0 / a.window_steps) : rep / a.replicas;
+    long long c1 = a.c1;
+    if (!a.sequential) c1 = c1 < a.nsteps_w[w] ? c1 : a.nsteps_w[w];
+    if (a.c0 >= c1) return;
+    double x = a.c0 == 0 ? (a.start ? a.start[rep] : a.x0) : a.state[2 * rep];
+    double W = a.c0 == 0 ? 0.0 : a.state[2 * rep + 1];
     const double amp = sqrt(2.0 * a.kT * a.dt / a.gamma);
-    const long long base = a.off_w[w] + (long long)r * a.tw[w];
-    Normal4<double> n = philox_normals<double>(a.seed, 0u, uid, (uint32_t)(s0 >> 2), kTagOStep);
-    // constant-velocity pulling: before step m > nequil the trap moves to
-    // lam + vdt (m - nequil) with the work of Eq. (9) at the current x
-    // (one launch covers the whole run, so the work lives in a register)
-    double lam_now = lam, W = 0.0;
-    for (long long step = s0; step < s1; ++step) {
-        if (a.wout && step > nequil) {
-            const double ln = lam + a.smd_vdt * (double)(step - nequil);
-            W += 0.5 * a.k * (ln - lam_now) * (ln + lam_now - 2.0 * x);
-            lam_now = ln;
+    const double lam1 = a.lambda[0], dtg = a.dt / a.gamma;
+    // per-window quantities, refreshed when a sequential run enters a window
+    long long origin = a.sequential ? (long long)w * a.window_steps : 0;
+    long long win_end = a.sequential ? origin + a.window_steps : c1;
+    long long nequil = a.nequil_w[w];
+    double lam = a.lambda[w];
+    long long base = a.off_w[w] + (long long)r * a.tw[w];
+    long long next = next_sample(a.c0 - origin, nequil, a.stride);  // in the window's step count
+    if (a.wout && a.c0 - 1 > nequil) lam = lam1 + a.smd_vdt * (double)(a.c0 - 1 - nequil);  // pulled so far
+    // normals in blocks of kPre steps, the next block's loads issued before the
+    // current block is integrated (the dependent steps are short; an L2 load
+    // per step would otherwise stall every step)
+    constexpr int kPre = 8;
+    const double *xi = a.noise + rep;
+    double cur[kPre], nxt[kPre];
+#pragma unroll
+    for (int j = 0; j < kPre; ++j) cur[j] = a.c0 + j < c1 ? xi[(long long)j * a.n_rep] : 0.0;
+    for (long long n0 = a.c0; n0 < c1; n0 += kPre) {
+#pragma unroll
+        for (int j = 0; j < kPre; ++j) {
+            const long long m = n0 + kPre + j;
+            nxt[j] = m < c1 ? xi[(m - a.c0) * a.n_rep] : 0.0;
         }
-        const int lane = (int)(step & 3);
-        if (lane == 0) n = philox_normals<double>(a.seed, 0u, uid, (uint32_t)(step >> 2), kTagOStep);
-        const double xi = lane == 0 ? n.n0 : (lane == 1 ? n.n1 : (lane == 2 ? n.n2 : n.n3));
-        const double f = -4.0 * a.a * x * (x * x - 1.0) - a.k * (x - lam_now);
-        x = x + f * a.dt / a.gamma + amp * xi;
-        const long long done = step + 1;
-        if (done > nequil && (done - nequil) % a.stride == 0) {
-            a.xout[base + (done - nequil) / a.stride - 1] = (float)x;
-            if (a.wout) a.wout[base + (done - nequil) / a.stride - 1] = W;
+#pragma unroll
+        for (int j = 0; j < kPre; ++j) {
+        const long long n = n0 + j;
+        if (n >= c1) break;
+        if (n == win_end) {  // sequential protocol: the trap moves to the next window
+            ++w;
+            origin = n;
+            win_end = n + a.window_steps;
+            nequil = a.nequil_w[w];
+            lam = a.lambda[w];
+            base = a.off_w[w] + (long long)r * a.tw[w];
+            next = next_sample(0, nequil, a.stride);
         }
+        const double xi_c = cur[j];
+        if (a.wout && n > nequil) {
+            const double lo = lam;
+            lam = lam1 + a.smd_vdt * (double)(n - nequil);
+            W += 0.5 * a.k * (lam - lo) * (lam + lo - 2.0 * x);
+        }
+        const double f = -4.0 * a.a * x * (x * x - 1.0) - a.k * (x - lam);
+        x = x + f * dtg + amp * xi_c;
+        if (n + 1 - origin == next) {
+            const long long at = base + (next - nequil) / a.stride - 1;
+            a.xout[at] = (float)x;
+            if (a.wout) a.wout[at] = W;
+            next += a.stride;
+        }
+        }
+#pragma unroll
+        for (int j = 0; j < kPre; ++j) cur[j] = nxt[j];
     }
     if (!isfinite(x)) atomicOr(a.err, kErrNonFinite);
-    a.state[rep] = x;
+    a.state[2 * rep] = x;
+    a.state[2 * rep + 1] = W;
+}
+
+long long od1d_noise_steps(int n_rep)
+{
+    // at most 2^23 normals (64 MB) per launch, between 64 and 8192 steps
+    long long c = (1LL << 23) / (n_rep > 0 ? n_rep : 1);
+    c = c < 64 ? 64 : (c > 8192 ? 8192 : c);
+    return c & ~3LL;
 }
 
 cudaError_t od1d_launch(const Od1dParams &m, const RunLaunch &L, int n_rep, cudaStream_t st)
 {
+    if (L.noise == nullptr || L.noise_steps < 4 || (L.noise_steps & 3) != 0 || (L.step_begin & 3) != 0)
+        return cudaErrorInvalidValue;
+    if (L.sequential && L.window_steps < 1) return cudaErrorInvalidValue;
     Od1dArgs a{};
     a.a = m.a;
     a.x0 = m.x0;
@@ -114,8 +161,6 @@ cudaError_t od1d_launch(const Od1dParams &m, const RunLaunch &L, int n_rep, cuda
     a.start = L.start;
     a.xout = L.xout;
     a.err = L.err;
-    a.step_begin = L.step_begin;
-    a.step_end = L.step_end;
     a.replicas = L.replicas;
     a.stride = L.stride;
     a.n_rep = n_rep;
@@ -125,12 +170,21 @@ cudaError_t od1d_launch(const Od1dParams &m, const RunLaunch &L, int n_rep, cuda
     a.window_steps = L.window_steps;
     a.wout = L.wout;
     a.smd_vdt = L.smd_vdt;
-    if (L.wout && L.step_begin != 0) return cudaErrorInvalidValue;  // pulled runs are one launch
-    a.n_windows = L.sequential ? (int)(L.step_end / L.window_steps) : 0;
-    if (L.sequential && (L.window_steps < 1 || L.step_begin != 0)) return cudaErrorInvalidValue;
+    a.noise = L.noise;
     const int threads = 128;
-    od1d_kernel<<<(n_rep + threads - 1) / threads, threads, 0, st>>>(a);
-    return cudaGetLastError();
+    for (long long c0 = L.step_begin; c0 < L.step_end; c0 += L.noise_steps) {
+        const long long c1 = c0 + L.noise_steps < L.step_end ? c0 + L.noise_steps : L.step_end;
+        const long long cells = ((c1 - c0 + 3) >> 2) * n_rep;
+        od1d_noise_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(L.seed, L.uid_base, n_rep, c0, c1,
+                                                                           L.noise);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        a.c0 = c0;
+        a.c1 = c1;
+        od1d_kernel<<<(n_rep + threads - 1) / threads, threads, 0, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Philox test hook: the same generator and FP32 Box-Muller as the integrator.

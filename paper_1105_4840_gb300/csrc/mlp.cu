@@ -135,12 +135,14 @@ struct MlpSmem {
     uint64_t *mbar;
     uint32_t *tmem_slot;
     float *red;            // [8]
+    long long *win_off;    // [kMaxSmemWindows] first sample of each window (training)
 };
 
 constexpr int kLd = 65;  // padded row length of the fp32 staging arrays
+constexpr int kMaxSmemWindows = 1024;  // window offsets kept in shared memory up to this count
 constexpr size_t kSmemTiles = 16384 * 2 + 8192 * 2 + 32768 + 16384;
 constexpr size_t kSmemBytes = kSmemTiles + 2 * sizeof(float) * kTile * kLd + sizeof(float) * (kTile * 2 + kTile) +
-                              2 * sizeof(float) * kMlpParams + 64 + 1024;
+                              2 * sizeof(float) * kMlpParams + 64 + 1024 + sizeof(long long) * kMaxSmemWindows;
 
 struct MlpArgs {
     float *params;              // [kMlpParams] fp32 master weights (in/out)
@@ -236,7 +238,12 @@ __device__ bool mlp_tile(const MlpArgs &a, const MlpSmem &s, uint32_t tmem, uint
     const float r = xv - mu;
     const float dmu = live ? -r * e * inv_batch : 0.f;
     const float dlv = live ? 0.5f * (1.f - r * r * e) * inv_batch : 0.f;
-    if (live) atomicAdd(loss_acc, (double)(0.5f * (lv + r * r * e)));
+    {  // loss: one shared-memory atomic per warp instead of one per sample
+        float lo = live ? 0.5f * (lv + r * r * e) : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lo += __shfl_xor_sync(0xffffffffu, lo, o);
+        if ((t & 31) == 0) atomicAdd(loss_acc, (double)lo);
+    }
     s.dout[2 * t] = dmu;
     s.dout[2 * t + 1] = dlv;
 #pragma unroll 8
@@ -268,20 +275,25 @@ __device__ bool mlp_tile(const MlpArgs &a, const MlpSmem &s, uint32_t tmem, uint
         mma_commit(s.mbar);
     }
     // meanwhile: dW3, db3 and db2 by feature threads
+    // (sums over the tile's samples in four interleaved partial sums, so
+    // consecutive additions do not wait on one another)
     for (int j = t; j < 2 * kH + 2 + kH; j += kTile) {
-        float acc = 0.f;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
         if (j < 2 * kH) {
             const int o = j >> 6, f = j & 63;
-            for (int q = 0; q < kTile; ++q) acc = fmaf(s.dout[2 * q + o], s.h2[q * kLd + f], acc);
-            s.grad[oW3 + j] += acc;
+#pragma unroll 4
+            for (int q = 0; q < kTile; ++q) acc[q & 3] = fmaf(s.dout[2 * q + o], s.h2[q * kLd + f], acc[q & 3]);
+            s.grad[oW3 + j] += (acc[0] + acc[1]) + (acc[2] + acc[3]);
         } else if (j < 2 * kH + 2) {
             const int o = j - 2 * kH;
-            for (int q = 0; q < kTile; ++q) acc += s.dout[2 * q + o];
-            s.grad[oB3 + o] += acc;
+#pragma unroll 4
+            for (int q = 0; q < kTile; ++q) acc[q & 3] += s.dout[2 * q + o];
+            s.grad[oB3 + o] += (acc[0] + acc[1]) + (acc[2] + acc[3]);
         } else {
             const int f = j - 2 * kH - 2;
-            for (int q = 0; q < kTile; ++q) acc += s.dz2[q * kLd + f];
-            s.grad[oB2 + f] += acc;
+#pragma unroll 4
+            for (int q = 0; q < kTile; ++q) acc[q & 3] += s.dz2[q * kLd + f];
+            s.grad[oB2 + f] += (acc[0] + acc[1]) + (acc[2] + acc[3]);
         }
     }
     if (!mbar_wait(s.mbar, phase)) return false;
@@ -304,13 +316,15 @@ __device__ bool mlp_tile(const MlpArgs &a, const MlpSmem &s, uint32_t tmem, uint
     __syncthreads();
     for (int j = t; j < 2 * kH; j += kTile) {
         const int f = j & 63;
-        float acc = 0.f;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
         if (j < kH) {
-            for (int q = 0; q < kTile; ++q) acc = fmaf(s.h2[q * kLd + f], s.lam[q], acc);
-            s.grad[oW1 + f] += acc;
+#pragma unroll 4
+            for (int q = 0; q < kTile; ++q) acc[q & 3] = fmaf(s.h2[q * kLd + f], s.lam[q], acc[q & 3]);
+            s.grad[oW1 + f] += (acc[0] + acc[1]) + (acc[2] + acc[3]);
         } else {
-            for (int q = 0; q < kTile; ++q) acc += s.h2[q * kLd + f];
-            s.grad[oB1 + f] += acc;
+#pragma unroll 4
+            for (int q = 0; q < kTile; ++q) acc[q & 3] += s.h2[q * kLd + f];
+            s.grad[oB1 + f] += (acc[0] + acc[1]) + (acc[2] + acc[3]);
         }
     }
     __syncthreads();
@@ -366,10 +380,13 @@ __global__ void __launch_bounds__(kTile, 1) mlp_kernel(const MlpArgs a)
     p = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
     s.mbar = reinterpret_cast<uint64_t *>(p); p += 16;
     s.tmem_slot = reinterpret_cast<uint32_t *>(p); p += 16;
+    s.win_off = reinterpret_cast<long long *>(p); p += sizeof(long long) * kMaxSmemWindows;
     __shared__ double loss_acc;
 
     const int t = threadIdx.x, warp = t >> 5;
     for (int e = t; e < kMlpParams; e += kTile) s.w[e] = a.params[e];
+    if (a.mode == 2 && a.n_windows <= kMaxSmemWindows)
+        for (int e = t; e < a.n_windows; e += kTile) s.win_off[e] = a.win_off[e];
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(s.mbar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -421,8 +438,15 @@ __global__ void __launch_bounds__(kTile, 1) mlp_kernel(const MlpArgs a)
             for (int tile = 0; tile < tiles && ok; ++tile) {
                 __syncthreads();
                 const long long idx = pick_sample(a.seed, a.adam_t + step, tile * kTile + t, a.total);
-                int w = 0;
-                while (w + 1 < a.n_windows && a.win_off[w + 1] <= idx) ++w;
+                // window of the sample: the last offset <= idx (bisection)
+                const long long *off = a.n_windows <= kMaxSmemWindows ? s.win_off : a.win_off;
+                int lo = 0, hi = a.n_windows - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (off[mid] <= idx) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int w = lo;
                 s.lam[t] = (float)((a.win_lambda[w] - a.c) * ih);
                 s.dout[2 * t] = (float)(((double)a.xs[idx] - a.c) * ih);
                 __syncthreads();
@@ -434,6 +458,7 @@ __global__ void __launch_bounds__(kTile, 1) mlp_kernel(const MlpArgs a)
             const int tt = a.adam_t + step + 1;
             const float b1 = 0.9f, b2 = 0.999f;
             const float c1 = 1.f - powf(b1, (float)tt), c2 = 1.f - powf(b2, (float)tt);
+#pragma unroll 8
             for (int e = t; e < kMlpParams; e += kTile) {
                 const float g = s.grad[e];
                 const float m = b1 * a.adam_m[e] + (1.f - b1) * g;

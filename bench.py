@@ -792,6 +792,10 @@ def main():
         r2.close()
         sys2.close()
     e2e_value = world * replica_steps / statistics.median(e2e_times)
+    # after the timed region: the measured FP32 FMA rate of this GPU (scalar
+    # and packed f32x2), the practical ceiling beside the derived peak
+    ffma2_tflops, _ = pmf.pmf_fp32_peak(packed=True)
+    ffma_tflops, _ = pmf.pmf_fp32_peak(packed=False)
 
     if rank != 0:
         return
@@ -812,7 +816,10 @@ def main():
             "frac_at_sampled_clock": (achieved / (sm_count * 256 * clk["sm_mhz"] * 1e6 / 1e12)
                                       if clk.get("sm_mhz") else None),
             "flops_per_replica_step": flops_per_replica_step(N_BEADS),
-            "launch_ms": chain_launch_ms}
+            "launch_ms": chain_launch_ms,
+            "peak_measured": {"ffma2": ffma2_tflops, "ffma": ffma_tflops, "unit": "TFLOP/s",
+                              "source": "pmf_fp32_peak: 8 independent FMA chains per thread, 4 x 512 threads per SM"},
+            "frac_of_measured": achieved / max(ffma2_tflops, ffma_tflops)}
     ns_per_day = replica_steps * world / (t_step / 1000.0) * run.dt * 86400.0 / 1e3
     line = {"metric": "replica-steps/s", "value": value, "unit": "replica-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,

@@ -355,7 +355,7 @@ pmf_status pmf_final_state(const pmf_run *run, double *pos, double *vel, size_t 
                            size_t *n_written);
 
 /* ---- batching / autotuning ----------------------------------------------
- * Warps per replica CTA of chain `chain` (4, 6 or 8 for FP32; FP64 uses 4);
+ * Warps per replica CTA of chain `chain` (4, 5, 6 or 8 for FP32; FP64 uses 4);
  * the host schedule of the nonbonded phase is rebuilt for the new count.
  * Results are bit-reproducible for a given count; different counts sum the
  * forces in different orders. */
@@ -501,6 +501,17 @@ pmf_status pmf_overlap(const double *mu, const double *log_var, int n, double *o
  * padded bead count).  PMF_EINVAL if capacity < 7 * records. */
 pmf_status pmf_chain_schedule(int N, int NW, int precision, int *out, size_t capacity, size_t *n_written,
                               int *padded);
+
+/* Measured FP32 throughput of this GPU, the peak of the integrator's
+ * roofline (its nonbonded loop is bound by the FP32 FMA pipe): every SM
+ * runs `ctas_per_sm` CTAs of 512 threads (0: 4, i.e. full occupancy), each
+ * thread `iters` iterations of eight independent FMA chains, scalar FFMA
+ * (packed = 0) or packed f32x2 FFMA2 (packed = 1).  One warm-up launch, then
+ * the best of `reps` timed launches (CUDA events on the library stream).
+ * *tflops = flops / time (an FMA counts as two flops); *ms = that launch's
+ * time.  iters >= 1, reps >= 1, else PMF_EINVAL; the probe allocates
+ * 2 KB per CTA of device memory for its results. */
+pmf_status pmf_fp32_peak(int packed, int ctas_per_sm, int iters, int reps, double *tflops, double *ms);
 
 /* Library stream: cudaStream_t passed as void* (NULL = legacy default). */
 pmf_status pmf_set_stream(void *stream);

@@ -1314,7 +1314,7 @@ pmf_status pmf_chain_set_warps(pmf_system *sys, int chain, int warps)
     if (!sys || sys->model != PMF_MODEL_CHAIN || chain < 0 || chain >= (int)sys->chains.size())
         return fail(PMF_EINVAL, "pmf_chain_set_warps: not a chain system / bad chain index");
     cudaError_t e = sys->chains[chain]->set_warps(warps);
-    if (e == cudaErrorInvalidValue) return fail(PMF_EINVAL, "pmf_chain_set_warps: warps must be 4, 6 or 8 (FP64: 4)");
+    if (e == cudaErrorInvalidValue) return fail(PMF_EINVAL, "pmf_chain_set_warps: warps must be 4, 5, 6 or 8 (FP64: 4)");
     if (e != cudaSuccess) return cuda_fail(e, "pmf_chain_set_warps");
     if (sys->chains[chain]->smem_bytes() > 227 * 1024 - 256) {
         sys->chains[chain]->set_warps(4);
@@ -1344,14 +1344,40 @@ pmf_status pmf_chain_get_launch(const pmf_system *sys, int chain, int *warps, in
     return PMF_OK;
 }
 
+pmf_status pmf_fp32_peak(int packed, int ctas_per_sm, int iters, int reps, double *tflops, double *ms)
+{
+    if (iters < 1 || reps < 1 || ctas_per_sm < 0 || ctas_per_sm > 64)
+        return fail(PMF_EINVAL, "pmf_fp32_peak: iters >= 1, reps >= 1, 0 <= ctas_per_sm <= 64");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev), "pmf_fp32_peak");
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "pmf_fp32_peak");
+    const int ctas = (ctas_per_sm > 0 ? ctas_per_sm : 4) * sms;
+    float *out = nullptr;
+    CK(cudaMalloc(&out, sizeof(float) * (size_t)ctas * fp32_peak_threads()), "pmf_fp32_peak alloc");
+    std::unique_ptr<float, cudaError_t (*)(void *)> guard(out, cudaFree);
+    double flops = 0.0;
+    CK(fp32_peak_launch(packed != 0, ctas, iters, out, &flops, g_stream), "pmf_fp32_peak warm-up");
+    double best = 1e300;
+    for (int r = 0; r < reps; ++r) {
+        GpuTimer timer;
+        timer.start();
+        CK(fp32_peak_launch(packed != 0, ctas, iters, out, &flops, g_stream), "pmf_fp32_peak launch");
+        CK(timer.stop(), "pmf_fp32_peak timer");
+        best = std::min(best, timer.ms);
+    }
+    if (tflops) *tflops = flops / (best * 1e-3) / 1e12;
+    if (ms) *ms = best;
+    return PMF_OK;
+}
+
 pmf_status pmf_chain_autotune(pmf_system *sys, const double *lambda, int n_windows, const pmf_run_params *p,
                               int probe_steps, int *best_warps, double *best_ms)
 {
     if (!sys || !lambda || !p || probe_steps < 1) return fail(PMF_EINVAL, "pmf_chain_autotune: bad argument");
     if (sys->model != PMF_MODEL_CHAIN) return fail(PMF_EINVAL, "pmf_chain_autotune: not a chain system");
     ChainModel &m = *sys->chains[p->chain];
-    const int cand_fp32[3] = {4, 6, 8};
-    const int n_cand = m.precision() == PMF_FP64 ? 1 : 3;
+    const int cand_fp32[4] = {4, 5, 6, 8};
+    const int n_cand = m.precision() == PMF_FP64 ? 1 : 4;
     pmf_run_params q = *p;
     q.n_steps = probe_steps + 1;
     q.n_steps_per_window = nullptr;
@@ -1493,8 +1519,8 @@ pmf_status pmf_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint
 pmf_status pmf_chain_schedule(int N, int NW, int precision, int *out, size_t capacity, size_t *n_written,
                               int *padded)
 {
-    if (N < 4 || N > 1024 || (NW != 4 && NW != 6 && NW != 8) || (precision != PMF_FP32 && precision != PMF_FP64))
-        return fail(PMF_EINVAL, "pmf_chain_schedule: N in [4,1024], NW 4, 6 or 8, precision FP32 or FP64");
+    if (N < 4 || N > 1024 || (NW != 4 && NW != 5 && NW != 6 && NW != 8) || (precision != PMF_FP32 && precision != PMF_FP64))
+        return fail(PMF_EINVAL, "pmf_chain_schedule: N in [4,1024], NW 4, 5, 6 or 8, precision FP32 or FP64");
     const auto sched = chain_schedule(N, NW, precision == PMF_FP32);
     size_t n = 0;
     for (const auto &v : sched) n += v.size();

@@ -854,7 +854,7 @@ __device__ long long next_item(const ChainArgs<R> &a)
 }
 
 template <typename R, int NW, bool SMD>
-__global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW == 6 ? 4 : 3)) : 1)
+__global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW == 5 ? 4 : (NW == 6 ? 3 : 2))) : 1)
     chain_kernel(const ChainArgs<R> a)
 // SMD: the constant-velocity pulling variant (a separate instantiation, so
 // the window runs carry none of its per-step work bookkeeping).
@@ -1145,7 +1145,7 @@ unsigned ChainModel::generation() const { return p->generation; }
 
 cudaError_t ChainModel::set_warps(int NW)
 {
-    if (NW != 4 && NW != 6 && NW != 8) return cudaErrorInvalidValue;
+    if (NW != 4 && NW != 5 && NW != 6 && NW != 8) return cudaErrorInvalidValue;
     if (p->precision == 1 && NW != 4) return cudaErrorInvalidValue;
     p->NW = NW;
     ++p->generation;
@@ -1307,6 +1307,7 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
 cudaError_t ChainModel::launch(const RunLaunch &L, cudaStream_t st)
 {
     if (p->precision == 1) return launch_typed<double, 4>(p, p->dd, L, st);
+    if (p->NW == 5) return launch_typed<float, 5>(p, p->df, L, st);
     if (p->NW == 6) return launch_typed<float, 6>(p, p->df, L, st);
     if (p->NW == 8) return launch_typed<float, 8>(p, p->df, L, st);
     return launch_typed<float, 4>(p, p->df, L, st);

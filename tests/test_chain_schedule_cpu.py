@@ -29,7 +29,7 @@ SPLIT = {26}  # quad kinds whose ring steps jump by 10 halfway (t = 1..7, then 1
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("NW", [4, 6, 8])
+@pytest.mark.parametrize("NW", [4, 5, 6, 8])
 @pytest.mark.parametrize("N", NS)
 def test_ring_pieces_cover_pairs_once(N, NW, precision):
     from paper_1105_4840_gb300 import pmf

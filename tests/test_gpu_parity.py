@@ -245,7 +245,7 @@ def test_repeat_launch_is_bit_identical(pmf):
         np.testing.assert_array_equal(u, v)
 
 
-@pytest.mark.parametrize("warps", [4, 6, 8])
+@pytest.mark.parametrize("warps", [4, 5, 6, 8])
 @pytest.mark.parametrize("n", [13, 40, 104, 110, 333])
 def test_forces_other_warp_counts(pmf, n, warps):
     """Same thermal-like states as test_forces_match_oracle (bonds off their
@@ -270,7 +270,7 @@ def test_autotune_picks_a_valid_count_and_runs(pmf):
     lam = inputs.lambda_grid(1.3, 1.6, 4)
     sysh = pmf.pmf_create_system_chain([p], [f32(start)])
     best, ms = pmf.pmf_chain_autotune(sysh, lam, pmf.make_params(run), probe_steps=200)
-    assert best in (4, 6, 8) and ms > 0
+    assert best in (4, 5, 6, 8) and ms > 0
     rr = pmf.pmf_run_windows(sysh, lam, pmf.make_params(run))
     assert np.all(np.isfinite(rr.free_energy()["dF_JE"]))
 
@@ -333,7 +333,7 @@ def test_partials_export_and_shard_merge(pmf):
     _compare_profiles(got, want, run.kT, rel=1e-11)
 
 
-@pytest.mark.parametrize("replicas,warps", [(32, 4), (32, 6), (1024, 4)])
+@pytest.mark.parametrize("replicas,warps", [(32, 4), (32, 5), (32, 6), (1024, 4)])
 def test_full_size_launch_sampled_replicas(pmf, replicas, warps):
     """The 104-bead workload at its full replica counts (21 x 32, and 21 x 1024
     of the precision study) in the benchmark's launch configuration

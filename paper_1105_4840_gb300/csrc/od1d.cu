@@ -3,7 +3,13 @@
 // constant-velocity pulling) on the model
 // H(lambda, x) = a (x^2 - 1)^2 + k/2 (x - lambda)^2 (kT units).
 //   x_{n+1} = x_n + F(x_n) dt / gamma + sqrt(2 kT dt / gamma) xi_n,
-// xi_n = normal (n mod 4) of the Philox block (0, uid, n div 4, 0).
+// F = -dH/dx, xi_n = normal (n mod 4) of the Philox block (0, uid, n div 4, 0).
+// Regrouped, x_{n+1} = x_n (cA x_n^2 + cB) + q_n with cA = -4a dt/gamma,
+// cB = 1 + (4a - k) dt/gamma and q_n = k lambda_n dt/gamma + amp xi_n.  q_n
+// does not depend on the trajectory, so a parallel pre-pass computes it for
+// a block of steps of every simulation; the sequential integration then costs
+// three FP64 operations per step, the rate at which this GPU's FP64 unit
+// retires them bounding a few hundred simulations.
 #include "common.cuh"
 #include "internal.h"
 
@@ -25,27 +31,40 @@ struct Od1dArgs {
     long long window_steps;
     double *wout;               // constant-velocity pulling: work at the records
     double smd_vdt;             //   trap advance per step after the equilibration
-    const double *noise;        // [c1 - c0][n_rep] normals of this launch's steps
+    const double *noise;        // [c1 - c0][n_rep] q_n of this launch's steps
 };
 
-// The normals do not depend on the trajectory, so they are drawn for a block
-// of steps by every thread of the grid at once (one Philox block = four
-// steps of one replica) before the sequential integration reads them.
-__global__ void od1d_noise_kernel(unsigned long long seed, uint32_t uid_base, int n_rep, long long c0, long long c1,
-                                  double *noise)
+// Trap centre during step n of simulation rep: its window's lambda (the
+// window of step n in the sequential protocol), or, when pulled, lambda_1
+// advanced by vdt per step after the equilibration.
+__device__ __forceinline__ double trap_centre(const Od1dArgs &a, int rep, long long n)
 {
-    const long long nb = (c1 - c0 + 3) >> 2;  // c0 is a multiple of 4
+    if (a.wout) {
+        const long long nequil = a.nequil_w[0];
+        return n > nequil ? a.lambda[0] + a.smd_vdt * (double)(n - nequil) : a.lambda[0];
+    }
+    return a.lambda[a.sequential ? (int)(n / a.window_steps) : rep / a.replicas];
+}
+
+// q_n of every simulation for steps [c0, c1), one Philox block (four steps
+// of one simulation) per thread, stored [n - c0][rep].
+__global__ void od1d_noise_kernel(const Od1dArgs a, double *q)
+{
+    const long long nb = (a.c1 - a.c0 + 3) >> 2;  // c0 is a multiple of 4
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= nb * n_rep) return;
-    const int rep = (int)(i % n_rep);
-    const long long blk = i / n_rep;
-    const long long n0 = c0 + 4 * blk;
+    if (i >= nb * a.n_rep) return;
+    const int rep = (int)(i % a.n_rep);
+    const long long blk = i / a.n_rep;
+    const long long n0 = a.c0 + 4 * blk;
     const Normal4<double> z =
-        philox_normals<double>(seed, 0u, uid_base + (uint32_t)rep, (uint32_t)(n0 >> 2), kTagOStep);
+        philox_normals<double>(a.seed, 0u, a.uid_base + (uint32_t)rep, (uint32_t)(n0 >> 2), kTagOStep);
     const double v[4] = {z.n0, z.n1, z.n2, z.n3};
+    const double dtg = a.dt / a.gamma, amp = sqrt(2.0 * a.kT * dtg), ck = a.k * dtg;
 #pragma unroll
-    for (int l = 0; l < 4; ++l)
-        if (n0 + l < c1) noise[(n0 + l - c0) * n_rep + rep] = v[l];
+    for (int l = 0; l < 4; ++l) {
+        const long long n = n0 + l;
+        if (n < a.c1) q[(n - a.c0) * a.n_rep + rep] = fma(amp, v[l], ck * trap_centre(a, rep, n));
+    }
 }
 
 // One thread per simulation, steps [c0, c1): the parallel protocol (window
@@ -72,8 +91,8 @@ __global__ void od1d_kernel(const Od1dArgs a)
     if (a.c0 >= c1) return;
     double x = a.c0 == 0 ? (a.start ? a.start[rep] : a.x0) : a.state[2 * rep];
     double W = a.c0 == 0 ? 0.0 : a.state[2 * rep + 1];
-    const double amp = sqrt(2.0 * a.kT * a.dt / a.gamma);
     const double lam1 = a.lambda[0], dtg = a.dt / a.gamma;
+    const double cA = -4.0 * a.a * dtg, cB = 1.0 + (4.0 * a.a - a.k) * dtg;
     // per-window quantities, refreshed when a sequential run enters a window
     long long origin = a.sequential ? (long long)w * a.window_steps : 0;
     long long win_end = a.sequential ? origin + a.window_steps : c1;
@@ -82,7 +101,7 @@ __global__ void od1d_kernel(const Od1dArgs a)
     long long base = a.off_w[w] + (long long)r * a.tw[w];
     long long next = next_sample(a.c0 - origin, nequil, a.stride);  // in the window's step count
     if (a.wout && a.c0 - 1 > nequil) lam = lam1 + a.smd_vdt * (double)(a.c0 - 1 - nequil);  // pulled so far
-    // normals in blocks of kPre steps, the next block's loads issued before the
+    // q_n in blocks of kPre steps, the next block's loads issued before the
     // current block is integrated (the dependent steps are short; an L2 load
     // per step would otherwise stall every step)
     constexpr int kPre = 8;
@@ -109,14 +128,12 @@ __global__ void od1d_kernel(const Od1dArgs a)
             base = a.off_w[w] + (long long)r * a.tw[w];
             next = next_sample(0, nequil, a.stride);
         }
-        const double xi_c = cur[j];
         if (a.wout && n > nequil) {
             const double lo = lam;
             lam = lam1 + a.smd_vdt * (double)(n - nequil);
             W += 0.5 * a.k * (lam - lo) * (lam + lo - 2.0 * x);
         }
-        const double f = -4.0 * a.a * x * (x * x - 1.0) - a.k * (x - lam);
-        x = x + f * dtg + amp * xi_c;
+        x = fma(x, fma(cA, x * x, cB), cur[j]);
         if (n + 1 - origin == next) {
             const long long at = base + (next - nequil) / a.stride - 1;
             a.xout[at] = (float)x;
@@ -171,16 +188,21 @@ cudaError_t od1d_launch(const Od1dParams &m, const RunLaunch &L, int n_rep, cuda
     a.wout = L.wout;
     a.smd_vdt = L.smd_vdt;
     a.noise = L.noise;
-    const int threads = 128;
+    // few simulations: spread them over the SMs (one warp each) rather than
+    // packing them into a few CTAs; many: 128 threads per CTA
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaGetLastError();
+    const int per_sm = (n_rep + sms - 1) / sms;
+    const int threads = per_sm <= 32 ? 32 : (per_sm <= 64 ? 64 : 128);
     for (long long c0 = L.step_begin; c0 < L.step_end; c0 += L.noise_steps) {
         const long long c1 = c0 + L.noise_steps < L.step_end ? c0 + L.noise_steps : L.step_end;
         const long long cells = ((c1 - c0 + 3) >> 2) * n_rep;
-        od1d_noise_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(L.seed, L.uid_base, n_rep, c0, c1,
-                                                                           L.noise);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
         a.c0 = c0;
         a.c1 = c1;
+        od1d_noise_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(a, L.noise);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
         od1d_kernel<<<(n_rep + threads - 1) / threads, threads, 0, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -162,9 +162,17 @@ def cpu_baseline(budget_s=12.0, n_steps=200):
             uid += cores
             done += sum(f.result() for f in futs)
     el = time.perf_counter() - t0
+    # the same oracle on one thread, for the per-core figure
+    done1, n1 = 0, 0
+    t1 = time.perf_counter()
+    while time.perf_counter() - t1 < min(2.0, budget_s / 4):
+        done1 += one(uid + n1)
+        n1 += 1
+    el1 = time.perf_counter() - t1
     return {"value": done / el, "unit": "replica-steps/s", "cores": cores, "kind": "oracle",
             "sample": f"{uid} replicas x {n_steps} BAOAB steps of the 104-bead chain (FP64, "
-                      f"{cores} threads, {el:.1f} s)"}
+                      f"{cores} threads, {el:.1f} s)",
+            "single_thread": {"value": done1 / el1, "sample": f"{n1} replicas x {n_steps} steps on one thread"}}
 
 
 def run_reference(args, rank, world):

@@ -135,6 +135,23 @@ def _ncu_traffic(warps):
     return t
 
 
+def samples_per_replica(run):
+    """x samples each replica records: every `stride` steps after `n_equil`."""
+    return (run.n_steps - run.n_equil) // run.stride
+
+
+def _reduction_roofline(ms, n_samples, peaks, fp64_tflops):
+    """The FP64 reductions of one step against HBM (4 bytes of x per sample,
+    read once) and beside the measured FP64 rate: one FP64 exp per sample
+    makes them FP64-bound on this GPU."""
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = 4.0 * n_samples / (ms * 1e-3) / 1e9
+    return {"kernels": "partial_kernel, window_kernel, profile_kernel", "ms": ms, "samples": n_samples,
+            "bound": "fp64", "achieved_gbs": gbs, "hbm_peak_gbs": hbm, "hbm_frac": gbs / hbm,
+            "ns_per_sample": ms * 1e6 / n_samples, "fp64_tflops_measured": fp64_tflops,
+            "note": "one FP64 exp per sample; the FP64 rate, not HBM, bounds it"}
+
+
 def cpu_baseline(budget_s=12.0, n_steps=200):
     """The FP64 oracle as it stands, on the host cores: replicas of the
     104-bead chain (windows round-robin), one thread per core."""
@@ -804,6 +821,7 @@ def main():
     # and packed f32x2), the practical ceiling beside the derived peak
     ffma2_tflops, _ = pmf.pmf_fp32_peak(packed=True)
     ffma_tflops, _ = pmf.pmf_fp32_peak(packed=False)
+    dfma_tflops, _ = pmf.pmf_fp64_peak()
 
     if rank != 0:
         return
@@ -843,6 +861,8 @@ def main():
             "roofline": roof,
             "aggregate_ns_per_day": ns_per_day,
             "reduction_ms": sum(red_ms) / len(red_ms),
+            "reduction": _reduction_roofline(sum(red_ms) / len(red_ms), n_rep * world * samples_per_replica(run),
+                                             peaks, dfma_tflops),
             "dF_JE_end": float(res["dF_JE"][-1]), "dF_fluct_end": float(res["dF_fluct"][-1]),
             "dF_com_end": float(res["dF_com"][-1]), "uncertainty_end": float(res["uncertainty"][-1])}
     if not args.no_cpu_baseline:

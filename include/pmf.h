@@ -513,6 +513,12 @@ pmf_status pmf_chain_schedule(int N, int NW, int precision, int *out, size_t cap
  * 2 KB per CTA of device memory for its results. */
 pmf_status pmf_fp32_peak(int packed, int ctas_per_sm, int iters, int reps, double *tflops, double *ms);
 
+/* Measured FP64 FMA throughput (DFMA, same probe shape as pmf_fp32_peak,
+ * 4 KB per CTA of device memory): the ceiling of the FP64 reductions, whose
+ * one exp per sample makes them FP64-bound rather than HBM-bound on a GPU
+ * with GB300's FP64 rate. */
+pmf_status pmf_fp64_peak(int ctas_per_sm, int iters, int reps, double *tflops, double *ms);
+
 /* Library stream: cudaStream_t passed as void* (NULL = legacy default). */
 pmf_status pmf_set_stream(void *stream);
 

@@ -1370,6 +1370,32 @@ pmf_status pmf_fp32_peak(int packed, int ctas_per_sm, int iters, int reps, doubl
     return PMF_OK;
 }
 
+pmf_status pmf_fp64_peak(int ctas_per_sm, int iters, int reps, double *tflops, double *ms)
+{
+    if (iters < 1 || reps < 1 || ctas_per_sm < 0 || ctas_per_sm > 64)
+        return fail(PMF_EINVAL, "pmf_fp64_peak: iters >= 1, reps >= 1, 0 <= ctas_per_sm <= 64");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev), "pmf_fp64_peak");
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "pmf_fp64_peak");
+    const int ctas = (ctas_per_sm > 0 ? ctas_per_sm : 4) * sms;
+    double *out = nullptr;
+    CK(cudaMalloc(&out, sizeof(double) * (size_t)ctas * fp32_peak_threads()), "pmf_fp64_peak alloc");
+    std::unique_ptr<double, cudaError_t (*)(void *)> guard(out, cudaFree);
+    double flops = 0.0;
+    CK(fp64_peak_launch(ctas, iters, out, &flops, g_stream), "pmf_fp64_peak warm-up");
+    double best = 1e300;
+    for (int r = 0; r < reps; ++r) {
+        GpuTimer timer;
+        timer.start();
+        CK(fp64_peak_launch(ctas, iters, out, &flops, g_stream), "pmf_fp64_peak launch");
+        CK(timer.stop(), "pmf_fp64_peak timer");
+        best = std::min(best, timer.ms);
+    }
+    if (tflops) *tflops = flops / (best * 1e-3) / 1e12;
+    if (ms) *ms = best;
+    return PMF_OK;
+}
+
 pmf_status pmf_chain_autotune(pmf_system *sys, const double *lambda, int n_windows, const pmf_run_params *p,
                               int probe_steps, int *best_warps, double *best_ms)
 {

@@ -36,6 +36,7 @@ ChainGeometry chain_geometry(int N);
 // FP32 FMA throughput probe (peak.cu): ctas CTAs of fp32_peak_threads()
 // threads, one float per thread into out; *flops of the launch
 cudaError_t fp32_peak_launch(bool packed, int ctas, int iters, float *out, double *flops, cudaStream_t st);
+cudaError_t fp64_peak_launch(int ctas, int iters, double *out, double *flops, cudaStream_t st);
 int fp32_peak_threads();
 // packed: the FP32 quad pieces (kinds 8, 10, 21..25); else the scalar pieces (0..10)
 std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed);

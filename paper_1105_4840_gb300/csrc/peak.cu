@@ -1,4 +1,5 @@
-// FP32 throughput probe: the denominator of the integrator's roofline.
+// FP32 and FP64 throughput probes: the denominators of the integrator's
+// roofline (FP32) and of the FP64 reductions.
 //
 // The chain integrator is bound by the FP32 FMA pipe, not by memory or the
 // tensor cores, so its peak is the rate at which the SMs retire FP32 fused
@@ -47,7 +48,33 @@ template <bool PACKED> __global__ void __launch_bounds__(kPeakThreads) fma_peak_
     out[tid] = s;  // keeps the chains live
 }
 
+// FP64: the same eight chains per thread with DFMA.
+__global__ void __launch_bounds__(kPeakThreads) dfma_peak_kernel(double *out, int iters, double a, double b)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[kPeakChains];
+#pragma unroll
+    for (int k = 0; k < kPeakChains; ++k) acc[k] = 1e-3 * k + 1e-9 * threadIdx.x;
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kPeakChains; ++k) acc[k] = fma(acc[k], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kPeakChains; ++k) s += acc[k];
+    out[tid] = s;
+}
+
 }  // namespace
+
+cudaError_t fp64_peak_launch(int ctas, int iters, double *out, double *flops, cudaStream_t st)
+{
+    if (ctas < 1 || iters < 1) return cudaErrorInvalidValue;
+    dfma_peak_kernel<<<ctas, kPeakThreads, 0, st>>>(out, iters, 0.999999, 1e-7);
+    *flops = (double)ctas * kPeakThreads * (double)iters * kPeakChains * 2.0;
+    return cudaGetLastError();
+}
 
 // Launches `ctas` CTAs of kPeakThreads threads; out holds ctas x kPeakThreads
 // floats.  Returns the flops one launch performs in *flops.

@@ -140,6 +140,7 @@ def _load():
     L.pmf_chain_get_launch.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.pmf_chain_autotune.argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.c_int, C.POINTER(C.c_int), _D]
     L.pmf_fp32_peak.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _D, _D]
+    L.pmf_fp64_peak.argtypes = [C.c_int, C.c_int, C.c_int, _D, _D]
     L.pmf_set_stream.argtypes = [C.c_void_p]
     L.pmf_last_error.restype = C.c_char_p
     L.pmf_version.restype = C.c_char_p
@@ -152,7 +153,7 @@ def _load():
                  "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_free_energy_noalloc",
                  "pmf_mlp_create", "pmf_mlp_get_params", "pmf_mlp_predict", "pmf_mlp_gradient", "pmf_mlp_train",
                  "pmf_overlap", "pmf_run_adaptive", "pmf_chain_set_warps", "pmf_chain_set_grid", "pmf_chain_get_launch",
-                 "pmf_chain_autotune", "pmf_fp32_peak", "pmf_set_stream"):
+                 "pmf_chain_autotune", "pmf_fp32_peak", "pmf_fp64_peak", "pmf_set_stream"):
         getattr(L, name).restype = C.c_int
     return L
 
@@ -583,6 +584,14 @@ def pmf_fp32_peak(packed=True, ctas_per_sm=0, iters=1 << 16, reps=3):
     and the time of the best launch in ms."""
     tf, ms = C.c_double(), C.c_double()
     _check(lib.pmf_fp32_peak(int(bool(packed)), ctas_per_sm, iters, reps, C.byref(tf), C.byref(ms)), "pmf_fp32_peak")
+    return tf.value, ms.value
+
+
+def pmf_fp64_peak(ctas_per_sm=0, iters=1 << 12, reps=3):
+    """Measured FP64 FMA throughput in TFLOP/s (FMA = 2 flops) and the time
+    of the best launch in ms."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib.pmf_fp64_peak(ctas_per_sm, iters, reps, C.byref(tf), C.byref(ms)), "pmf_fp64_peak")
     return tf.value, ms.value
 
 

@@ -30,3 +30,13 @@ def test_fp32_peak_arguments(pmf):
         with pytest.raises(pmf.PmfError) as e:
             pmf.pmf_fp32_peak(**kw)
         assert e.value.status == pmf.PMF_EINVAL
+
+
+def test_fp64_peak(pmf):
+    """The FP64 probe runs and reports a positive rate below the FP32 one."""
+    fp64, ms = pmf.pmf_fp64_peak(iters=1 << 10, reps=2)
+    fp32, _ = pmf.pmf_fp32_peak(packed=False, iters=1 << 12, reps=2)
+    assert ms > 0 and 0.0 < fp64 < fp32
+    with pytest.raises(pmf.PmfError) as e:
+        pmf.pmf_fp64_peak(iters=0)
+    assert e.value.status == pmf.PMF_EINVAL

@@ -407,6 +407,84 @@ def bench_adaptive(args, pmf, torch):
     print(json.dumps(out), flush=True)
 
 
+def _od1d_exact(lams, a, k, kT):
+    """F(lambda, k) - F(lambda_1, k) of the 1D double well with its trap,
+    -kT ln int exp(-(a (x^2 - 1)^2 + k/2 (x - lambda)^2) / kT) dx, by the
+    trapezoid rule on a fine grid (the reference of the 1D ladder)."""
+    x = np.linspace(-4.0, 4.0, 400001)
+    U = a * (x * x - 1.0) ** 2
+    F = []
+    for lam in lams:
+        e = -(U + 0.5 * k * (x - lam) ** 2) / kT
+        m = e.max()
+        F.append(-kT * (m + np.log(np.trapezoid(np.exp(e - m), x))))
+    F = np.array(F)
+    return F - F[0]
+
+
+def bench_adaptive_1d(args, pmf, torch):
+    """The GPU-seconds-to-0.2-kT comparison on the 1D double well, whose
+    reference is exact (quadrature): the uniform 21-window grid against the
+    learned placement from 11 windows (the chain study's protocol settings),
+    32 replicas per window, a ladder of window lengths, seeds 0..4."""
+    from paper_1105_4840_gb300 import inputs
+
+    w = inputs.od1d_workload()
+    run = w["run"]
+    kT = run.kT
+    lo, hi = float(run.lambdas[0]), float(run.lambdas[-1])
+    exact = float(_od1d_exact([lo, hi], w["a"], run.k, kT)[-1])
+    sysh = pmf.pmf_create_system_1d(w["a"], w["x0"])
+    init = pmf.pack_mlp_params(inputs.mlp_init_params(2))
+    ladder = [250, 500, 1000, 2000, 4000, 8000, 16000, 32000]
+    seeds = list(args.seeds) if args.seeds else [0, 1, 2, 3, 4]
+    rows = {"uniform": [], "adaptive": []}
+    for seed in seeds:
+        for n_steps in ladder:
+            run.replicas, run.n_steps, run.n_equil, run.seed, run.stride = 32, n_steps, n_steps // 10, seed, 10
+            lam = np.linspace(lo, hi, 21)
+            rr = pmf.pmf_run_prepare(sysh, lam, pmf.make_params(run))
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            torch.cuda.synchronize()
+            ev[0].record()
+            rr.launch()
+            rr.reduce()
+            ev[1].record()
+            rr.wait()
+            torch.cuda.synchronize()
+            res = rr.free_energy()
+            rr.close()
+            rows["uniform"].append({"seed": seed, "steps": n_steps, "gpu_s": ev[0].elapsed_time(ev[1]) / 1000.0,
+                                    "windows": 21, "dF": float(res["dF_JE"][-1])})
+            meta, ares = pmf.pmf_run_adaptive(sysh, np.linspace(lo, hi, 11), pmf.make_params(run), init,
+                                              threshold=0.3, max_rounds=3, max_windows=81, mlp_steps=400,
+                                              mlp_batch=512, mlp_lr=3e-3, mlp_seed=5 + seed)
+            rows["adaptive"].append({"seed": seed, "steps": n_steps, "gpu_s": meta["gpu_seconds"],
+                                     "windows": meta["n_windows"], "dF": float(ares["dF_JE"][-1])})
+
+    def summary(rs):
+        per_seed = []
+        for seed in seeds:
+            lad = sorted([r for r in rs if r["seed"] == seed], key=lambda r: r["steps"])
+            ok = [abs(r["dF"] - exact) < 0.2 * kT for r in lad]
+            first = next((i for i in range(len(lad)) if all(ok[i:])), None)
+            per_seed.append(None if first is None else {"steps": lad[first]["steps"], "gpu_s": lad[first]["gpu_s"]})
+        got = [x["gpu_s"] for x in per_seed if x is not None]
+        by_steps = {}
+        for n in ladder:
+            dev = [r["dF"] - exact for r in rs if r["steps"] == n]
+            by_steps[n] = {"mean_dev_kT": float(np.mean(dev)) / kT, "sd_dev_kT": float(np.std(dev)) / kT,
+                           "mean_gpu_s": float(np.mean([r["gpu_s"] for r in rs if r["steps"] == n]))}
+        return {"median_gpu_s": statistics.median(got) if got else None, "seeds_converged": len(got),
+                "per_seed": per_seed, "by_steps": by_steps}
+
+    out = {"workload": "od1d_adaptive_vs_uniform", "criterion_kT": 0.2, "lambda": [lo, hi],
+           "exact_dF": exact, "replicas": 32, "dt": run.dt,
+           "uniform": summary(rows["uniform"]), "adaptive": summary(rows["adaptive"]), "runs": rows}
+    sysh.close()
+    print(json.dumps(out), flush=True)
+
+
 def bench_mlp(args, pmf, torch, stream):
     """Surrogate training throughput: Adam steps of the 1 -> 64 -> 64 -> 2
     network (64 x 64 layer on tcgen05, BF16 operands, FP32 accumulators in
@@ -658,7 +736,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="chain104",
                     choices=["chain104", "batch64", "precision", "adaptive", "mlp", "spp", "histograms", "sweeps",
-                             "smd", "od1d"],
+                             "smd", "od1d", "adaptive1d"],
                     help="chain104: the 104-bead PPP (default); batch64: 64 uneven chains in one graph; "
                          "precision: FP32 vs FP64 integration study")
     ap.add_argument("--replicas", type=int, default=1024, help="replicas per window (precision study)")
@@ -730,6 +808,10 @@ def main():
     if args.workload == "adaptive":
         if world == 1:
             bench_adaptive(args, pmf, torch)
+        return
+    if args.workload == "adaptive1d":
+        if world == 1:
+            bench_adaptive_1d(args, pmf, torch)
         return
     if args.workload == "precision":
         if world == 1:

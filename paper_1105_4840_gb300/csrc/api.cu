@@ -76,7 +76,7 @@ struct pmf_run {
     bool sequential = false;  // sequential protocol: replicas visit the windows in order
     double smd_vdt = 0;       // constant-velocity pulling: trap advance per step
     double *d_w = nullptr;    // constant-velocity pulling: work at the records
-    double *d_noise = nullptr;  // 1D model: normals of a block of steps
+    double *d_noise = nullptr;  // 1D model: q_n (noise and trap term) of a block of steps
     long long noise_steps = 0;
     double k = 0, kT = 1, dt = 0, gamma = 1, timeout_s = 0;
     unsigned long long seed = 0;

@@ -62,7 +62,8 @@ struct RunLaunch {
     // step after the equilibration; accumulated work recorded into wout
     double smd_vdt = 0;
     double *wout = nullptr;
-    // 1D model: buffer for the normals of noise_steps steps of every simulation
+    // 1D model: buffer for the per-step noise-and-trap terms q_n of noise_steps
+    // steps of every simulation
     double *noise = nullptr;
     long long noise_steps = 0;
     long long step_begin = 0, step_end = 0;

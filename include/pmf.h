@@ -437,7 +437,10 @@ pmf_status pmf_mlp_train(pmf_mlp *mlp, const pmf_run *run, int steps, int batch,
  * pmf_free_energy are then evaluated on the merged non-uniform grid.
  * gpu_seconds sums the device time of the simulations, the training, the
  * predictions, the seeding and the reductions (CUDA events on the library
- * stream). */
+ * stream).  Unless the caller set the chain's warp count
+ * (pmf_chain_set_warps or pmf_chain_autotune), each FP32 chain launch of the
+ * protocol uses 8 warps per replica when it has fewer than three replicas
+ * per SM and 4 otherwise; the chain is back at 4 on return. */
 typedef struct {
     double overlap_threshold;   /* e.g. 0.3                                   */
     int max_rounds;             /* insertion rounds (>= 0)                    */

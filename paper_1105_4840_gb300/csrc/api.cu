@@ -54,6 +54,7 @@ template <typename T> cudaError_t upload(T **d, const T *h, size_t n)
 struct pmf_system {
     int model = 0, precision = 0;
     std::vector<std::unique_ptr<ChainModel>> chains;
+    std::vector<char> warps_chosen;  // per chain: warps set by the caller or by autotuning
     Od1dParams od;
 };
 
@@ -1156,12 +1157,45 @@ pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, cons
     if (res->capacity < ap->max_windows) return fail(PMF_EINVAL, "pmf_run_adaptive: result capacity < max_windows");
     std::memset(info, 0, sizeof(*info));
     GpuTimer timer;
+    // Launches with few replicas per SM run faster with more warps per
+    // replica (more resident warps to hide latency): unless the caller chose
+    // the chain's warp count, each launch of an FP32 chain takes 8 warps
+    // below three replicas per SM and 4 otherwise; the default is restored
+    // on return.
+    struct WarpScope {
+        ChainModel *m = nullptr;
+        bool changed = false;
+        ~WarpScope()
+        {
+            if (m && changed) m->set_warps(4);
+        }
+    } wscope;
+    int sms = 1;
+    {
+        int dev = 0;
+        CK(cudaGetDevice(&dev), "pmf_run_adaptive");
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "pmf_run_adaptive");
+    }
+    if (sys->model == PMF_MODEL_CHAIN && sys->chains[p->chain]->precision() != PMF_FP64 &&
+        sys->chains[p->chain]->warps() == 4 &&
+        !(p->chain < (int)sys->warps_chosen.size() && sys->warps_chosen[p->chain]))
+        wscope.m = sys->chains[p->chain].get();
+    auto pick_warps = [&](long long n_rep) -> pmf_status {
+        if (!wscope.m) return PMF_OK;
+        const int nw = n_rep < 3LL * sms ? 8 : 4;
+        if (wscope.m->warps() == nw) return PMF_OK;
+        wscope.changed = true;
+        cudaError_t e = wscope.m->set_warps(nw);
+        if (e == cudaSuccess && wscope.m->smem_bytes() > 227 * 1024 - 256) e = wscope.m->set_warps(4);
+        return e == cudaSuccess ? PMF_OK : cuda_fail(e, "pmf_run_adaptive: warps");
+    };
     std::vector<std::unique_ptr<pmf_run, void (*)(pmf_run *)>> runs;
     auto own = [&](pmf_run *r) { runs.emplace_back(r, pmf_destroy_run); };
     pmf_run *r0 = nullptr;
     pmf_status st = pmf_run_prepare(sys, lambda0, n0, p, &r0);
     if (st != PMF_OK) return st;
     own(r0);
+    if ((st = pick_warps((long long)n0 * p->replicas)) != PMF_OK) return st;
     timer.start();
     if ((st = pmf_run_launch(r0)) != PMF_OK) return st;
     if ((st = pmf_run_wait(r0)) != PMF_OK) return st;
@@ -1271,6 +1305,7 @@ pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, cons
         if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
         cudaFree(d_jobs);
         if (e != cudaSuccess) return cuda_fail(e, "seed");
+        if ((st = pick_warps((long long)new_lam.size() * R)) != PMF_OK) return st;
         if ((st = pmf_run_launch(rn)) != PMF_OK) return st;
         if ((st = pmf_run_wait(rn)) != PMF_OK) return st;
         CK(timer.stop(), "timer");
@@ -1320,6 +1355,8 @@ pmf_status pmf_chain_set_warps(pmf_system *sys, int chain, int warps)
         sys->chains[chain]->set_warps(4);
         return fail(PMF_EINVAL, "pmf_chain_set_warps: shared memory would exceed 227 KB");
     }
+    if (sys->warps_chosen.size() < sys->chains.size()) sys->warps_chosen.resize(sys->chains.size(), 0);
+    sys->warps_chosen[chain] = 1;
     return PMF_OK;
 }
 

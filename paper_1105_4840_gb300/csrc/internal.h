@@ -86,7 +86,7 @@ public:
     size_t state_bytes_per_replica() const;
     size_t smem_bytes() const;
     int warps() const;
-    cudaError_t set_warps(int NW);  // 4, 6 or 8 warps per replica (FP64: 4)
+    cudaError_t set_warps(int NW);  // 4, 5, 6 or 8 warps per replica (FP64: 4)
     // Incremented by every set_warps (which reallocates the work schedule a
     // captured launch points at): a captured graph older than this is stale.
     unsigned generation() const;

@@ -64,6 +64,11 @@ def test_bad_arguments_are_rejected():
     with pytest.raises(pmf.PmfError) as e:
         pmf.pmf_create_system_chain([tiny], [np.zeros((3, 3))])
     assert e.value.status == pmf.PMF_EINVAL
+    # warp counts outside {4, 5, 6, 8} and chain lengths outside [4, 1024]
+    for nw, n in ((7, 104), (3, 104), (4, 3), (4, 1025)):
+        with pytest.raises(pmf.PmfError) as e:
+            pmf.pmf_chain_schedule(n, nw, pmf.PMF_FP32)
+        assert e.value.status == pmf.PMF_EINVAL
 
 
 @pytest.mark.skipif(_has_gpu(), reason="checks the no-device path")

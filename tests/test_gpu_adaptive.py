@@ -100,3 +100,26 @@ def test_adaptive_protocol_on_double_well(pmf):
                     for i in range(lam.size - 1)])
     assert np.median(ovl) > 0.4
     assert meta["gpu_seconds"] > 0
+
+
+def test_adaptive_warp_choice_is_scoped(pmf):
+    """The adaptive protocol may run its sparse launches with more warps per
+    replica; the chain is back at its default afterwards, a warp count the
+    caller chose is kept, and both runs give finite profiles on the same
+    final grid size."""
+    n = 40
+    p = inputs.chain_params(n, 21)
+    start = f32(inputs.chain_start(p, 50, target_x=1.0))
+    run = inputs.RunSettings(k=500.0, kT=inputs.kT_of(300.0), dt=0.001, gamma=5.0, n_steps=400, n_equil=100,
+                             stride=50, replicas=4, seed=3)
+    lam0 = np.linspace(1.0, 1.6, 4)
+    init = pmf.pack_mlp_params(sg.init_params(2))
+    for chosen in (None, 6):
+        sysh = pmf.pmf_create_system_chain([p], [start])
+        if chosen is not None:
+            pmf.pmf_chain_set_warps(sysh, 0, chosen)
+        meta, res = pmf.pmf_run_adaptive(sysh, lam0, pmf.make_params(run), init, threshold=0.3, max_rounds=1,
+                                         max_windows=8, mlp_steps=50, mlp_batch=128, mlp_lr=3e-3, mlp_seed=1)
+        assert pmf.pmf_chain_get_launch(sysh, 0)[0] == (4 if chosen is None else chosen)
+        assert np.all(np.isfinite(res["dF_JE"])) and meta["gpu_seconds"] > 0
+        sysh.close()

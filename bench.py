@@ -152,9 +152,11 @@ def _reduction_roofline(ms, n_samples, peaks, fp64_tflops):
             "note": "one FP64 exp per sample; the FP64 rate, not HBM, bounds it"}
 
 
-def cpu_baseline(budget_s=12.0, n_steps=200):
+def cpu_baseline(budget_s=12.0, n_steps=200, single_thread=True):
     """The FP64 oracle as it stands, on the host cores: replicas of the
-    104-bead chain (windows round-robin), one thread per core."""
+    104-bead chain (windows round-robin), one thread per core; with
+    single_thread, also the same oracle on one thread for the per-core
+    figure."""
     import concurrent.futures as cf
 
     from oracle import _clib
@@ -179,32 +181,44 @@ def cpu_baseline(budget_s=12.0, n_steps=200):
             uid += cores
             done += sum(f.result() for f in futs)
     el = time.perf_counter() - t0
-    # the same oracle on one thread, for the per-core figure
+    out = {"value": done / el, "unit": "replica-steps/s", "cores": cores, "kind": "oracle",
+           "sample": f"{uid} replicas x {n_steps} BAOAB steps of the 104-bead chain (FP64, "
+                     f"{cores} threads, {el:.1f} s)",
+           "replica_steps": done, "seconds": el}
+    if not single_thread:
+        return out
     done1, n1 = 0, 0
     t1 = time.perf_counter()
     while time.perf_counter() - t1 < min(2.0, budget_s / 4):
         done1 += one(uid + n1)
         n1 += 1
     el1 = time.perf_counter() - t1
-    return {"value": done / el, "unit": "replica-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{uid} replicas x {n_steps} BAOAB steps of the 104-bead chain (FP64, "
-                      f"{cores} threads, {el:.1f} s)",
-            "single_thread": {"value": done1 / el1, "sample": f"{n1} replicas x {n_steps} steps on one thread"}}
+    out["single_thread"] = {"value": done1 / el1, "sample": f"{n1} replicas x {n_steps} steps on one thread"}
+    return out
 
 
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
     if rank != 0:
         return
+    # every step is a bounded sample of the workload (about 6 s of oracle
+    # work on all host cores); ms_per_step is the measured time of one such
+    # step and value the replica-steps of all timed steps over their time
     vals = []
     for _ in range(args.warmup):
-        cpu_baseline(budget_s=2.0)
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(budget_s=8.0))
-    v = statistics.median([b["value"] for b in vals])
+        cpu_baseline(budget_s=1.0, single_thread=False)
+    t0 = time.perf_counter()
+    for q in range(args.steps):
+        vals.append(cpu_baseline(budget_s=6.0, single_thread=(q == args.steps - 1)))
+    el = time.perf_counter() - t0
+    work = sum(b["replica_steps"] for b in vals)
+    v = work / sum(b["seconds"] for b in vals)
     line = {"impl": "reference", "metric": "replica-steps/s", "value": v, "unit": "replica-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * 21 * 32 * 400000 / v, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1000.0 * el / max(args.steps, 1), "extrapolated": False,
+            "step_work": f"a bounded sample of {work // max(args.steps, 1)} replica-steps per step "
+                         "(the whole workload is 21 x 32 x 4e5 = 2.69e9 replica-steps)",
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(_workload().get("run"), world),
             "cpu_baseline": {**vals[-1], "value": v},

@@ -38,7 +38,8 @@ typedef enum {
     PMF_ENOMEM = 2,   /* device or host allocation failed                      */
     PMF_ECUDA = 3,    /* CUDA runtime error or no device                       */
     PMF_ENUMERIC = 4, /* a trajectory became non-finite (device error flag)    */
-    PMF_ETIMEOUT = 5, /* the run exceeded pmf_run_params.timeout_s             */
+    PMF_ETIMEOUT = 5, /* the run exceeded pmf_run_params.timeout_s, or a device
+                         wait exceeded pmf_run_params.segment_wait_s           */
     PMF_ESTATE = 6    /* call out of order (e.g. results of an unfinished run) */
 } pmf_status;
 
@@ -117,6 +118,9 @@ typedef struct {
     uint32_t uid_base;          /* first replica uid (sharding across processes) */
     int chain;                  /* chain index of a multi-chain system           */
     double timeout_s;           /* wall-clock limit of pmf_run_wait; 0: none     */
+    double segment_wait_s;      /* persistent chain launches: longest device wait
+                                   for a replica's previous segment (0: 60 s,
+                                   at most 1e6)                                  */
 } pmf_run_params;
 
 /* PPP of Sec. III (ii): allocate the run, upload lambda[n_windows] (strictly
@@ -130,10 +134,20 @@ pmf_status pmf_run_windows(pmf_system *sys, const double *lambda, int n_windows,
 
 /* The three phases of pmf_run_windows.  prepare allocates and uploads (the
  * only host-to-device traffic); launch enqueues the simulation on the
- * library stream and returns at once; wait blocks until it finishes (or
- * timeout_s passes: PMF_ETIMEOUT) and reports PMF_ENUMERIC if the device
- * error flag was raised.  launch may be called again on a finished run to
- * repeat it from x_o with the same streams (identical results). */
+ * library stream and returns at once; wait blocks until it finishes and
+ * reports the device error flags:
+ *   PMF_ENUMERIC  a trajectory became non-finite;
+ *   PMF_ETIMEOUT  a persistent chain launch waited longer than
+ *                 segment_wait_s for a replica's previous segment (the
+ *                 kernel raised the flag and returned by itself).
+ * If timeout_s > 0 and passes first, wait raises a stop flag in host-mapped
+ * memory that the persistent chain launches poll between work items, waits
+ * for the kernels in flight to finish the segment they are on (1D runs and
+ * one-CTA-per-replica launches run their chunk to its end), and returns
+ * PMF_ETIMEOUT.  After either PMF_ETIMEOUT the run's samples are incomplete
+ * and the result calls return PMF_ESTATE until a new launch finishes.
+ * launch may be called again on a finished run to repeat it from x_o with
+ * the same streams (identical results). */
 pmf_status pmf_run_prepare(pmf_system *sys, const double *lambda, int n_windows,
                            const pmf_run_params *p, pmf_run **out);
 pmf_status pmf_run_launch(pmf_run *run);
@@ -465,6 +479,17 @@ pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, cons
                             const pmf_adaptive_params *ap, pmf_adaptive_info *info, pmf_free_energy_result *res);
 
 /* ---- kernel-level entry points used by the parity tests ---------------- */
+
+/* Test hook of the bounded device wait (no counterpart in the paper): the
+ * next launches of this single-item chain run start their persistent work
+ * queue at item first_item (items are segment-major, item = segment x
+ * (n_windows x replicas) + replica) instead of 0; the items before it never
+ * run.  With first_item = n_windows x replicas every replica's second
+ * segment waits for a first segment that never ran, so the launch ends by
+ * itself after segment_wait_s with PMF_ETIMEOUT from pmf_run_wait.  0
+ * restores the normal run.  PMF_EINVAL for other run kinds, PMF_ESTATE while
+ * the run is in flight. */
+pmf_status pmf_run_set_queue_start(pmf_run *run, int64_t first_item);
 
 /* The integrator's Philox4x32-10 and Box-Muller on the GPU: blocks with
  * counters (c0 + i, c1, c2, c3), key (seed lo, seed hi), i < n_blocks.

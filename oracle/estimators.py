@@ -23,6 +23,7 @@ Every function states the passage it follows.  Readings of ambiguous points:
 from __future__ import annotations
 
 import math
+from fractions import Fraction
 
 import numpy as np
 
@@ -226,7 +227,11 @@ def free_energy_from_partials(P, lambdas, k: float, kT: float) -> dict:
         inc["vw"][i] = k * k * d * d * var_x[i]
         inc["n"][i] = n
         if R >= 2:
-            loo_je = [m - kT * math.log(math.fsum(np.delete(E, r).tolist()) / (n - n_r[r])) for r in range(R)]
+            # each leave-one-out sum exact in rational arithmetic, rounded
+            # once (the same value as fsum over the other R - 1 terms)
+            Ef = [Fraction(float(e)) for e in E]
+            tot = sum(Ef, Fraction(0))
+            loo_je = [m - kT * math.log(float(tot - Ef[r]) / (n - n_r[r])) for r in range(R)]
             loo_fl = [-k * d * (a - a_r[r]) / (n - n_r[r]) for r in range(R)]
             inc["jje"][i] = _jackknife_var(loo_je)
             inc["jfl"][i] = _jackknife_var(loo_fl)

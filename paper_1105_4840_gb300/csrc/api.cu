@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/pmf.h"
+#include "common.cuh"
 #include "internal.h"
 
 using namespace pmf;
@@ -79,7 +80,10 @@ struct pmf_run {
     double *d_w = nullptr;    // constant-velocity pulling: work at the records
     double *d_noise = nullptr;  // 1D model: q_n (noise and trap term) of a block of steps
     long long noise_steps = 0;
-    double k = 0, kT = 1, dt = 0, gamma = 1, timeout_s = 0;
+    double k = 0, kT = 1, dt = 0, gamma = 1, timeout_s = 0, segment_wait_s = 0;
+    long long queue_start = 0;  // persistent chain launches: first work item (test hook)
+    int *h_abort = nullptr;     // host-mapped stop flag polled by the persistent chain launches
+    int *d_abort = nullptr;     //   (its device alias)
     unsigned long long seed = 0;
     uint32_t uid_base = 0;
     std::vector<double> lambda;
@@ -116,6 +120,7 @@ struct pmf_run {
         cudaFree(d_done);
         cudaFree(d_w);
         cudaFree(d_noise);
+        if (h_abort) cudaFreeHost(h_abort);
         if (done) cudaEventDestroy(done);
         if (graph) cudaGraphExecDestroy(graph);
         if (cap) cudaStreamDestroy(cap);
@@ -254,6 +259,9 @@ static pmf_status prepare_items(pmf_system *sys, const pmf_batch_item *items, in
     run->dt = p->dt;
     run->gamma = p->gamma;
     run->timeout_s = p->timeout_s;
+    if (!(p->segment_wait_s >= 0) || !std::isfinite(p->segment_wait_s) || p->segment_wait_s > 1e6)
+        return fail(PMF_EINVAL, "segment_wait_s must be in [0, 1e6]");
+    run->segment_wait_s = p->segment_wait_s;
     run->seed = p->seed;
     run->uid_base = p->uid_base;
     size_t state_off = 0;
@@ -307,6 +315,11 @@ static pmf_status prepare_items(pmf_system *sys, const pmf_batch_item *items, in
         const long long sims = sequential ? p->replicas : (long long)n_windows * p->replicas;
         run->noise_steps = od1d_noise_steps((int)std::min<long long>(sims, 1 << 30));
         CK(cudaMalloc(&run->d_noise, sizeof(double) * (size_t)run->noise_steps * sims), "alloc noise");
+    }
+    if (sys->model == PMF_MODEL_CHAIN) {
+        CK(cudaHostAlloc(&run->h_abort, sizeof(int), cudaHostAllocMapped), "alloc stop flag");
+        *(volatile int *)run->h_abort = 0;
+        CK(cudaHostGetDevicePointer(&run->d_abort, run->h_abort, 0), "map stop flag");
     }
     if (n_items == 1 && sys->model == PMF_MODEL_CHAIN) {
         CK(cudaMalloc(&run->d_queue, sizeof(unsigned long long)), "alloc queue");
@@ -375,6 +388,9 @@ static cudaError_t enqueue_item(pmf_run *run, const RunItem &ri, cudaStream_t st
     L.start = run->d_start;
     L.queue = run->d_queue;  // set for single-item chain runs only
     L.done = run->d_done;
+    L.queue_start = run->queue_start;
+    L.wait_ns = (unsigned long long)(run->segment_wait_s * 1e9);
+    L.abort = run->d_abort;
     L.wout = run->d_w;       // set for pulled runs only
     L.smd_vdt = run->smd_vdt;
     // 1D runs: this item's block of the noise buffer
@@ -479,6 +495,7 @@ pmf_status pmf_run_launch(pmf_run *run)
         if (e != cudaSuccess) return cuda_fail(e, "instantiate graph");
         run->graph_gen = gen;
     }
+    if (run->h_abort) *(volatile int *)run->h_abort = 0;
     CK(cudaGraphLaunch(run->graph, g_stream), "graph launch");
     CK(cudaEventRecord(run->done, g_stream), "record");
     run->launched = true;
@@ -497,14 +514,29 @@ pmf_status pmf_run_wait(pmf_run *run)
         if (q != cudaErrorNotReady) return cuda_fail(q, "run");
         if (run->timeout_s > 0) {
             const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-            if (el > run->timeout_s) return fail(PMF_ETIMEOUT, "run exceeded timeout_s");
+            if (el > run->timeout_s) {
+                // ask the persistent chain launches to stop at their next
+                // work item, then wait for the kernels in flight to drain so
+                // that no kernel of this run still uses its buffers
+                if (run->h_abort) *(volatile int *)run->h_abort = 1;
+                cudaError_t e = cudaEventSynchronize(run->done);
+                if (e != cudaSuccess) return cuda_fail(e, "run (stopping after timeout_s)");
+                run->finished = false;
+                return fail(PMF_ETIMEOUT, "run exceeded timeout_s and was stopped (its samples are incomplete)");
+            }
         }
         std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
     int err = 0;
     CK(cudaMemcpy(&err, run->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read flag");
     run->finished = true;
-    if (err) return fail(PMF_ENUMERIC, "a trajectory became non-finite");
+    if (err & kErrTimeout) {
+        run->finished = false;
+        return fail(PMF_ETIMEOUT, "a persistent segment waited longer than segment_wait_s for the replica's "
+                                  "previous segment (the run stopped; its samples are incomplete)");
+    }
+    if (err & kErrNonFinite) return fail(PMF_ENUMERIC, "a trajectory became non-finite");
+    if (err) return fail(PMF_ECUDA, "device error flag " + std::to_string(err));
     return PMF_OK;
 }
 
@@ -698,6 +730,22 @@ pmf_status pmf_free_energy_item(const pmf_run *run, int item, pmf_free_energy_re
     CK(cudaMemcpyAsync(h.data(), run->d_res, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g_stream), "copy");
     CK(cudaStreamSynchronize(g_stream), "sync");
     return copy_result(h.data(), nw, res);
+}
+
+pmf_status pmf_run_set_queue_start(pmf_run *run, int64_t first_item)
+{
+    if (!run) return fail(PMF_EINVAL, "null run");
+    if (!run->d_queue || run->sequential || run->items.size() != 1)
+        return fail(PMF_EINVAL, "pmf_run_set_queue_start: single-item chain runs with the persistent launch only");
+    if (first_item < 0) return fail(PMF_EINVAL, "pmf_run_set_queue_start: first_item must be >= 0");
+    if (run->launched && !run->finished && cudaEventQuery(run->done) == cudaErrorNotReady)
+        return fail(PMF_ESTATE, "pmf_run_set_queue_start: the run is still in flight");
+    run->queue_start = first_item;
+    if (run->graph) {  // the offset is a kernel argument: capture the launches again
+        cudaGraphExecDestroy(run->graph);
+        run->graph = nullptr;
+    }
+    return PMF_OK;
 }
 
 pmf_status pmf_run_reduce(pmf_run *run)

@@ -58,6 +58,9 @@ template <typename R> struct ChainArgs {
     unsigned long long *queue; // persistent mode: next work item (zeroed before the launch)
     int *done;                 // persistent mode: [n_rep] segments finished (zeroed)
     long long n_items;         // persistent mode: n_rep x segments
+    long long queue_start;     // persistent mode: first item taken (0; > 0 only to test the bounded wait)
+    unsigned long long wait_ns;  // persistent mode: longest wait for a replica's previous segment
+    const volatile int *abort;   // host-mapped flag: non-zero asks every CTA to stop at its next item
     int n_rep, seg_steps, persistent;
     double *wout;              // constant-velocity pulling: accumulated work at the records
     int smd;                   // constant-velocity pulling: the trap advances smd_vdt per step
@@ -824,26 +827,32 @@ __device__ __forceinline__ unsigned long long global_ns()
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Longest wait for a replica's previous segment before the kernel gives up
-// (flags kErrTimeout and returns); a segment normally takes milliseconds.
-constexpr unsigned long long kSegmentWaitNs = 60ull * 1000000000ull;
+// The host asked the run to stop (pmf_run_wait's wall-clock limit), or a
+// CTA of this run raised an error flag.
+template <typename R> __device__ __forceinline__ bool stop_requested(const ChainArgs<R> &a)
+{
+    return *((volatile int *)a.err) != 0 || (a.abort != nullptr && *a.abort != 0);
+}
 
 // Persistent mode, thread 0: the next work item (segment-major: item =
 // segment x n_rep + replica) once the replica's previous segment is done;
-// -1 when the queue is empty or the run was aborted.
+// -1 when the queue is empty or the run was stopped.  The wait for the
+// previous segment is bounded by a.wait_ns of %globaltimer; when it runs out
+// the kernel raises kErrTimeout (reported as PMF_ETIMEOUT) and every CTA
+// returns at its next item.
 template <typename R>
 __device__ long long next_item(const ChainArgs<R> &a)
 {
-    if (*((volatile int *)a.err) != 0) return -1;
-    const unsigned long long it = atomicAdd(a.queue, 1ull);
+    if (stop_requested(a)) return -1;
+    const unsigned long long it = atomicAdd(a.queue, 1ull) + (unsigned long long)a.queue_start;
     if (it >= (unsigned long long)a.n_items) return -1;
     const int rep = (int)(it % (unsigned long long)a.n_rep);
     const int seg = (int)(it / (unsigned long long)a.n_rep);
     if (seg > 0 && ld_acquire(a.done + rep) < seg) {
         const unsigned long long t0 = global_ns();
         while (ld_acquire(a.done + rep) < seg) {
-            if (*((volatile int *)a.err) != 0) return -1;
-            if (global_ns() - t0 > kSegmentWaitNs) {
+            if (stop_requested(a)) return -1;
+            if (global_ns() - t0 > a.wait_ns) {
                 atomicOr(a.err, kErrTimeout);
                 return -1;
             }
@@ -916,7 +925,7 @@ __global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW =
             if (a.persistent) {
                 s0 += seg * a.seg_steps;
                 s1 = s0 + a.seg_steps < a.step_end ? s0 + a.seg_steps : a.step_end;
-            } else if (*((volatile int *)a.err) != 0) {
+            } else if (stop_requested(a)) {
                 return;
             }
             const long long nsteps = a.nsteps_w[w];
@@ -1254,6 +1263,9 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
         a.seg_steps = (int)((L.window_steps + subs - 1) / subs);
     }
     a.n_items = 0;
+    a.queue_start = L.queue_start;
+    a.wait_ns = L.wait_ns > 0 ? L.wait_ns : kDefaultSegmentWaitNs;
+    a.abort = L.abort;
     const size_t smem = chain_smem_bytes<R>(m->geo, NW);
     void (*kern)(const ChainArgs<R>) = a.smd ? chain_kernel<R, NW, true> : chain_kernel<R, NW, false>;
     // The attribute is the kernel's upper limit, shared by every chain that

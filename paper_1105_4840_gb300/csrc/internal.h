@@ -17,6 +17,9 @@ struct ChainHost {
 };
 
 constexpr int kMaxRunWindows = 4096;
+// Longest wait of a persistent chain launch for a replica's previous segment
+// unless the run sets its own (a segment normally takes milliseconds).
+constexpr unsigned long long kDefaultSegmentWaitNs = 60ull * 1000000000ull;
 constexpr int kMaxBranches = 64;  // concurrent item branches of a batched run's graph
 
 // Tiling of N beads into 32-bead tiles; the last tile has width 8, 16 or 32.
@@ -54,6 +57,9 @@ struct RunLaunch {
     // per-replica segment counters, both zeroed by the launch itself
     unsigned long long *queue = nullptr;
     int *done = nullptr;
+    long long queue_start = 0;         // first item taken (> 0 only to test the bounded wait)
+    unsigned long long wait_ns = 0;    // longest wait for a previous segment (0: kDefaultSegmentWaitNs)
+    const volatile int *abort = nullptr;  // host-mapped stop flag, polled between items
     // sequential protocol: n_blocks simulations each visit every window for
     // window_steps steps (steps [0, n_windows x window_steps)); persistent only
     bool sequential = false;

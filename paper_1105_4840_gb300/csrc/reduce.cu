@@ -117,11 +117,67 @@ constexpr int kWindowThreads = 256;
 // shared memory; larger ones recompute them in the jackknife loops.
 constexpr int kWindowSmemReplicas = 16384;
 
+// Error-free sum of two doubles: s + e == a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
+{
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Block-wide sum of compensated pairs (s, c) (each thread's Neumaier sum):
+// the pairs are merged with TwoSum so the result hi + lo keeps the
+// compensation; hi is the correctly rounded total up to O(n eps^2).
+template <int NT> __device__ void block_sum_pair(double s, double c, double *red, double &hi, double &lo)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const double s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        double t, e;
+        two_sum(s, s2, t, e);
+        s = t;
+        c = c + c2 + e;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) {
+        red[2 * warp] = s;
+        red[2 * warp + 1] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ts = red[0], tc = red[1];
+        for (int q = 1; q < NT / 32; ++q) {
+            double t, e;
+            two_sum(ts, red[2 * q], t, e);
+            ts = t;
+            tc = tc + red[2 * q + 1] + e;
+        }
+        const double h = ts + tc;
+        red[2 * (NT / 32)] = h;
+        red[2 * (NT / 32) + 1] = tc - (h - ts);
+    }
+    __syncthreads();
+    hi = red[2 * (NT / 32)];
+    lo = red[2 * (NT / 32) + 1];
+}
+
+// Sum of the replicas' exponential sums without replica r, from the
+// compensated total hi + lo of all of them: (hi - e_r) + lo.  The terms are
+// non-negative, so the only cancellation is e_r close to the total, and then
+// hi - e_r is exact (Sterbenz: e_r >= hi / 2) and the result carries the
+// total's own accuracy; otherwise hi - e_r >= hi / 2 rounds once.  O(1) per
+// replica instead of re-summing the other R - 1 terms.
+__device__ __forceinline__ double sum_without(double hi, double lo, double e_r)
+{
+    const double v = (hi - e_r) + lo;
+    return v > 0.0 ? v : 0.0;
+}
+
 template <bool SMEM>
 __global__ void __launch_bounds__(kWindowThreads) window_kernel(const ReduceLayout L, const Partial *P, WindowOut *wo)
 {
     extern __shared__ double E[];  // [replicas] when SMEM
-    __shared__ double red[kWindowThreads / 32 + 1];
+    __shared__ double red[2 * (kWindowThreads / 32 + 1)];
     const int w = blockIdx.x, R = L.replicas;
     const Partial *p = P + (size_t)w * R;
     const double li = L.lambda[w];
@@ -131,16 +187,20 @@ __global__ void __launch_bounds__(kWindowThreads) window_kernel(const ReduceLayo
     for (int r = threadIdx.x; r < R; r += kWindowThreads)
         if (p[r].n > 0) m = fmin(m, p[r].m);
     m = block_min<kWindowThreads>(m, red);
+    // replica r's exponential sum brought to the window's common shift m
+    auto e_of = [&](int r) { return p[r].n > 0 ? p[r].S * exp(-(p[r].m - m) / L.kT) : 0.0; };
     double se = 0, ce = 0, sn = 0, s1 = 0, c1 = 0, s2 = 0, c2 = 0;
     for (int r = threadIdx.x; r < R; r += kWindowThreads) {
-        const double e = p[r].n > 0 ? p[r].S * exp(-(p[r].m - m) / L.kT) : 0.0;
+        const double e = e_of(r);
         if (SMEM) E[r] = e;
         neumaier(se, ce, e);
         sn += p[r].n;
         neumaier(s1, c1, p[r].sdx);
         neumaier(s2, c2, p[r].sdx2);
     }
-    const double S = block_sum<kWindowThreads>(se + ce, red);
+    double Shi, Slo;
+    block_sum_pair<kWindowThreads>(se, ce, red, Shi, Slo);
+    const double S = Shi + Slo;
     const double n = block_sum<kWindowThreads>(sn, red);
     const double sdx = block_sum<kWindowThreads>(s1 + c1, red);
     const double sdx2 = block_sum<kWindowThreads>(s2 + c2, red);
@@ -150,16 +210,15 @@ __global__ void __launch_bounds__(kWindowThreads) window_kernel(const ReduceLayo
     const double var = sdx2 / n - mdx * mdx;
     const double fl = -L.k * d * mdx;
     const double g2 = L.k * var / L.kT;
-    // delete-one-replica jackknife
+    // delete-one-replica jackknife, O(R): the leave-one-out exponential sum
+    // from the compensated total (sum_without), the Eq. (14) mean from sdx
     double vje = 0, vfl = 0;
     const bool jk = R >= 2;
     if (jk) {
         for (int r = threadIdx.x; r < R; r += kWindowThreads) {
-            double sm = 0, cm = 0;
-            for (int q = 0; q < R; ++q)
-                if (q != r) neumaier(sm, cm, SMEM ? E[q] : (p[q].n > 0 ? p[q].S * exp(-(p[q].m - m) / L.kT) : 0.0));
+            const double sm = sum_without(Shi, Slo, SMEM ? E[r] : e_of(r));
             const double nm = n - p[r].n;
-            vje += m - L.kT * log((sm + cm) / nm);
+            vje += m - L.kT * log(sm / nm);
             vfl += -L.k * d * (sdx - p[r].sdx) / nm;
         }
     }
@@ -168,11 +227,9 @@ __global__ void __launch_bounds__(kWindowThreads) window_kernel(const ReduceLayo
     double qje = 0, qfl = 0;
     if (jk) {
         for (int r = threadIdx.x; r < R; r += kWindowThreads) {
-            double sm = 0, cm = 0;
-            for (int q = 0; q < R; ++q)
-                if (q != r) neumaier(sm, cm, SMEM ? E[q] : (p[q].n > 0 ? p[q].S * exp(-(p[q].m - m) / L.kT) : 0.0));
+            const double sm = sum_without(Shi, Slo, SMEM ? E[r] : e_of(r));
             const double nm = n - p[r].n;
-            const double a = m - L.kT * log((sm + cm) / nm) - mje;
+            const double a = m - L.kT * log(sm / nm) - mje;
             const double b = -L.k * d * (sdx - p[r].sdx) / nm - mfl;
             qje += a * a;
             qfl += b * b;
@@ -379,10 +436,41 @@ constexpr size_t kNoAllocBytes = kNoAllocPartialBytes + kNoAllocWindowBytes + kN
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Host side: the array's name is only a host stand-in; its device address is
-// looked up once per device (with that device current) and cached.
+// looked up with that device current and cached per device, together with
+// the unique id of the CUDA context it was looked up in.  A later call in
+// another context of the same device (after cudaDeviceReset, the module and
+// its array are loaded again, maybe elsewhere) looks the address up again.
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 void *g_noalloc_addr[kMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kMaxDevices] = {};
+
+// Unique id of the calling thread's current context (driver entry points
+// cuCtxGetCurrent / cuCtxGetId, reached through the runtime so the library
+// links no driver library); 0 if it cannot be had.
+unsigned long long current_context_id()
+{
+    using GetCurrent = int (*)(void **);
+    using GetId = int (*)(void *, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+    return 0;
+}
 
 cudaError_t noalloc_scratch(void **out)
 {
@@ -391,11 +479,15 @@ cudaError_t noalloc_scratch(void **out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (g_noalloc_addr[dev] == nullptr) {
+    const unsigned long long ctx = current_context_id();
+    if (g_noalloc_addr[dev] == nullptr || ctx == 0 || ctx != g_noalloc_ctx[dev]) {
+        // (the lookup makes the device's primary context current if no
+        // runtime call has done so yet; the id is read again after it)
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_noalloc_addr[dev] = p;
+        g_noalloc_ctx[dev] = current_context_id();
     }
     *out = g_noalloc_addr[dev];
     return cudaSuccess;

@@ -45,7 +45,8 @@ class RunParams(C.Structure):
     _fields_ = [("k", C.c_double), ("kT", C.c_double), ("dt", C.c_double), ("gamma", C.c_double),
                 ("n_steps", C.c_int64), ("n_steps_per_window", _I64), ("n_equil", C.c_int64),
                 ("sample_stride", C.c_int), ("replicas", C.c_int), ("seed", C.c_uint64),
-                ("uid_base", C.c_uint32), ("chain", C.c_int), ("timeout_s", C.c_double)]
+                ("uid_base", C.c_uint32), ("chain", C.c_int), ("timeout_s", C.c_double),
+                ("segment_wait_s", C.c_double)]
 
 
 MAX_RUN_WINDOWS = 4096  # PMF_MAX_RUN_WINDOWS
@@ -123,6 +124,7 @@ def _load():
     L.pmf_chain_schedule.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_size_t,
                                      C.POINTER(C.c_size_t), C.POINTER(C.c_int)]
     L.pmf_run_reduce.argtypes = [P]
+    L.pmf_run_set_queue_start.argtypes = [P, C.c_int64]
     L.pmf_free_energy_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64,
                                           C.c_double, C.c_double, C.c_void_p]
     L.pmf_mlp_create.argtypes = [_F, C.c_double, C.c_double, C.POINTER(P)]
@@ -150,7 +152,7 @@ def _load():
                  "pmf_run_wait", "pmf_get_run_info", "pmf_x_samples", "pmf_work_samples",
                  "pmf_free_energy", "pmf_free_energy_from_samples", "pmf_final_state",
                  "pmf_run_partials", "pmf_free_energy_from_partials", "pmf_work_distributions", "pmf_philox",
-                 "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_free_energy_noalloc",
+                 "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_run_set_queue_start", "pmf_free_energy_noalloc",
                  "pmf_mlp_create", "pmf_mlp_get_params", "pmf_mlp_predict", "pmf_mlp_gradient", "pmf_mlp_train",
                  "pmf_overlap", "pmf_run_adaptive", "pmf_chain_set_warps", "pmf_chain_set_grid", "pmf_chain_get_launch",
                  "pmf_chain_autotune", "pmf_fp32_peak", "pmf_fp64_peak", "pmf_set_stream"):
@@ -228,7 +230,7 @@ def pmf_create_system_1d(a=2.0, x0=-1.0) -> System:
     return System(h, None)
 
 
-def make_params(run, chain=0, n_steps_per_window=None, timeout_s=0.0, uid_base=0):
+def make_params(run, chain=0, n_steps_per_window=None, timeout_s=0.0, uid_base=0, segment_wait_s=0.0):
     """RunParams from an inputs.RunSettings."""
     arr = None
     if n_steps_per_window is not None:
@@ -236,7 +238,8 @@ def make_params(run, chain=0, n_steps_per_window=None, timeout_s=0.0, uid_base=0
     p = RunParams(k=run.k, kT=run.kT, dt=run.dt, gamma=run.gamma, n_steps=run.n_steps,
                   n_steps_per_window=arr.ctypes.data_as(_I64) if arr is not None else None,
                   n_equil=run.n_equil, sample_stride=run.stride, replicas=run.replicas,
-                  seed=run.seed, uid_base=uid_base, chain=chain, timeout_s=timeout_s)
+                  seed=run.seed, uid_base=uid_base, chain=chain, timeout_s=timeout_s,
+                  segment_wait_s=segment_wait_s)
     return p, arr
 
 
@@ -267,6 +270,10 @@ class Run:
 
     def reduce(self):
         _check(lib.pmf_run_reduce(self.handle), "pmf_run_reduce")
+
+    def set_queue_start(self, first_item):
+        """Test hook of the bounded device wait (pmf_run_set_queue_start)."""
+        _check(lib.pmf_run_set_queue_start(self.handle, int(first_item)), "pmf_run_set_queue_start")
 
     def info(self):
         inf = RunInfo()

@@ -120,6 +120,29 @@ def test_reduction_parity(pmf, s, R, T):
     _compare_profiles(g, o, kT)
 
 
+@pytest.mark.parametrize("R", [300, 16384, 20000])
+def test_combination_many_replicas(pmf, R):
+    """The per-window combination and its delete-one-replica jackknife on
+    synthetic per-replica partials with one replica dominating the
+    exponential sums (the leave-one-out sum then cancels almost all of the
+    total): 16384 replicas keep their sums in shared memory, 20000 take the
+    other branch.  Against the oracle's combination of the same partials."""
+    s, k, kT = 3, 500.0, inputs.kT_of(300.0)
+    lam = np.array([1.3, 1.4, 1.55])
+    g = np.random.default_rng(R)
+    P = np.zeros((s, R, 5))
+    T = 50.0
+    P[:, :, 0] = 1.0 + 0.5 * g.standard_normal((s, R))      # min w
+    P[:, :, 1] = 1.0 + 10.0 * g.random((s, R))               # shifted exponential sum
+    P[:, :, 2] = T
+    P[:, :, 3] = T * 0.02 * g.standard_normal((s, R))        # sum (x - lambda)
+    P[:, :, 4] = T * 0.003 + np.abs(P[:, :, 3]) ** 2 / T     # sum (x - lambda)^2
+    P[0, R // 3, 0] -= 40.0 * kT                             # this replica's weight dominates window 0
+    got = pmf.pmf_free_energy_from_partials(P, lam, k, kT)
+    want = est.free_energy_from_partials(P, lam, k, kT)
+    _compare_profiles(got, want, kT)
+
+
 def test_reduction_ragged_and_device_pointer(pmf):
     torch = pytest.importorskip("torch")
     lam = np.array([-1.5, -1.2, -1.0, -0.2, 0.4, 1.5])

@@ -64,6 +64,33 @@ def test_noalloc_matches_regular_entry_point_twice():
     assert not np.array_equal(results[0]["dF_JE"], results[1]["dF_JE"])
 
 
+@pytest.mark.parametrize("s,R", [(4, 16384), (2, 32768)])
+def test_noalloc_at_its_size_limits(s, R):
+    """n_windows x replicas = 65536 fills the partials part of the fixed
+    scratch; 16384 replicas keep the per-replica sums of the combination
+    step in shared memory, 32768 take its other branch.  Two calls in a
+    row, each against the regular entry point."""
+    torch = pytest.importorskip("torch")
+    from paper_1105_4840_gb300 import pmf
+
+    T = 4
+    lam = inputs.lambda_grid(1.3, 1.6, s)
+    k, kT = 500.0, inputs.kT_of(300.0)
+    for seed in (21, 22):
+        x = inputs.gaussian_x_samples(lam, k, kT, R, T, seed=seed)
+        want = pmf.pmf_free_energy_from_samples(x.ravel(), lam, R, [T] * s, k, kT)
+        x_dev = torch.from_numpy(x.ravel()).cuda()
+        lam_dev = torch.from_numpy(lam.copy()).cuda()
+        out_dev = torch.full((14 * s,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        pmf.pmf_set_stream(torch.cuda.current_stream().cuda_stream)
+        pmf.pmf_free_energy_noalloc(x_dev.data_ptr(), lam_dev.data_ptr(), s, R, T, k, kT, out_dev.data_ptr())
+        torch.cuda.synchronize()
+        pmf.pmf_set_stream(0)
+        got_flat = out_dev.cpu().numpy()
+        _close({key: got_flat[q * s:(q + 1) * s] for q, key in enumerate(FIELDS)}, want, kT)
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     torch = pytest.importorskip("torch")
     from paper_1105_4840_gb300 import pmf

@@ -455,6 +455,32 @@ pmf_status pmf_mlp_train(pmf_mlp *mlp, const pmf_run *run, int steps, int batch,
  * (pmf_chain_set_warps or pmf_chain_autotune), each FP32 chain launch of the
  * protocol uses 8 warps per replica when it has fewer than three replicas
  * per SM and 4 otherwise; the chain is back at 4 on return. */
+/* Optional record of the protocol's decisions (caller-owned host arrays;
+ * a NULL array is not filled).  Round q (q < max_rounds) stores, for the
+ * n_windows[q] windows it started from (path order):
+ *   lambda, mu, log_var  [q][max_windows]: centres and the surrogate's
+ *                        prediction there;
+ *   ovl                  [q][max_windows]: OVL of windows i and i + 1;
+ * and for the n_inserted[q] windows it inserted (path order):
+ *   inserted, target     [q][max_windows]: centres and the predicted mean x
+ *                        there (the seeding target);
+ *   cand_x               [q][max_windows][2 replicas]: final x of each seeding
+ *                        candidate (c < replicas: replica c of the left
+ *                        neighbour, else replica c - replicas of the right);
+ *   seed                 [q][max_windows][replicas]: the candidate each replica
+ *                        of the inserted window started from.
+ * rounds receives the number of rounds recorded (the last one may insert
+ * nothing).  max_windows must be >= pmf_adaptive_params.max_windows and
+ * replicas = pmf_run_params.replicas (<= 2048), else PMF_EINVAL. */
+typedef struct {
+    int max_rounds, max_windows, replicas;
+    int rounds;
+    int *n_windows, *n_inserted;
+    double *lambda, *mu, *log_var, *ovl;
+    double *inserted, *target, *cand_x;
+    int *seed;
+} pmf_adaptive_trace;
+
 typedef struct {
     double overlap_threshold;   /* e.g. 0.3                                   */
     int max_rounds;             /* insertion rounds (>= 0)                    */
@@ -463,6 +489,7 @@ typedef struct {
     double mlp_lr;
     uint64_t mlp_seed;
     const float *mlp_init;      /* PMF_MLP_PARAMS initial weights (host)      */
+    pmf_adaptive_trace *trace;  /* optional decision record (NULL: none)      */
 } pmf_adaptive_params;
 
 typedef struct {

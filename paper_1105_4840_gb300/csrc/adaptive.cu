@@ -51,7 +51,8 @@ cudaError_t overlap_launch(const double *mu, const double *log_var, int n, doubl
 // neighbouring windows); replica r starts from the candidate of rank r mod M
 // when candidates are ordered by |x_final - target_q| (ties by index).
 template <typename R>
-__global__ void seed_kernel(const SeedJob *jobs, int N, int Np, int replicas, double *start)
+__global__ void seed_kernel(const SeedJob *jobs, int N, int Np, int replicas, int max_cand, double *start,
+                            int *choice, double *cand_x)
 {
     extern __shared__ double dist[];  // [M]
     const SeedJob &J = jobs[blockIdx.x];
@@ -68,12 +69,14 @@ __global__ void seed_kernel(const SeedJob *jobs, int N, int Np, int replicas, do
             x = *reinterpret_cast<const double *>(J.cand[c]);
         }
         dist[c] = fabs(x - J.target);
+        if (cand_x) cand_x[(size_t)blockIdx.x * max_cand + c] = x;
     }
     __syncthreads();
     for (int c = threadIdx.x; c < M; c += blockDim.x) {
         int rank = 0;
         for (int d = 0; d < M; ++d) rank += (dist[d] < dist[c]) || (dist[d] == dist[c] && d < c);
         for (int r = rank; r < replicas; r += M) {
+            if (choice) choice[(size_t)blockIdx.x * replicas + r] = c;
             double *out = start + ((size_t)blockIdx.x * replicas + r) * (N > 0 ? 3 * (size_t)N : 1);
             if (N > 0) {
                 const R *p = reinterpret_cast<const R *>(J.cand[c]);
@@ -87,12 +90,14 @@ __global__ void seed_kernel(const SeedJob *jobs, int N, int Np, int replicas, do
 }
 
 cudaError_t seed_launch(const SeedJob *jobs, int n_jobs, int max_cand, int N, int Np, int replicas, bool fp64,
-                        double *start, cudaStream_t st)
+                        double *start, int *choice, double *cand_x, cudaStream_t st)
 {
     if (n_jobs == 0) return cudaSuccess;
     const size_t smem = sizeof(double) * (size_t)max_cand;
-    if (fp64 || N == 0) seed_kernel<double><<<n_jobs, 128, smem, st>>>(jobs, N, Np, replicas, start);
-    else seed_kernel<float><<<n_jobs, 128, smem, st>>>(jobs, N, Np, replicas, start);
+    if (fp64 || N == 0)
+        seed_kernel<double><<<n_jobs, 128, smem, st>>>(jobs, N, Np, replicas, max_cand, start, choice, cand_x);
+    else
+        seed_kernel<float><<<n_jobs, 128, smem, st>>>(jobs, N, Np, replicas, max_cand, start, choice, cand_x);
     return cudaGetLastError();
 }
 

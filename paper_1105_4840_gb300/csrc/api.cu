@@ -1203,6 +1203,14 @@ pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, cons
         ap->overlap_threshold > 1 || ap->mlp_steps < 0 || ap->mlp_batch < 1 || !(ap->mlp_lr > 0))
         return fail(PMF_EINVAL, "pmf_run_adaptive: bad adaptive parameters");
     if (res->capacity < ap->max_windows) return fail(PMF_EINVAL, "pmf_run_adaptive: result capacity < max_windows");
+    pmf_adaptive_trace *tr = ap->trace;
+    if (tr) {
+        if (tr->max_rounds < 0 || tr->max_windows < ap->max_windows || tr->replicas != p->replicas ||
+            p->replicas > kMaxSeedCandidates / 2)
+            return fail(PMF_EINVAL, "pmf_run_adaptive: trace needs max_windows >= the protocol's, "
+                                    "replicas = the run's (<= 2048)");
+        tr->rounds = 0;
+    }
     std::memset(info, 0, sizeof(*info));
     GpuTimer timer;
     // Launches with few replicas per SM run faster with more warps per
@@ -1318,6 +1326,23 @@ pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, cons
         std::vector<int> pick;
         for (size_t i = 0; i < mids.size(); ++i)
             if (ovl[i] < ap->overlap_threshold && (int)(win.size() + pick.size()) < ap->max_windows) pick.push_back((int)i);
+        const bool rec = tr && round < tr->max_rounds;
+        if (rec) {
+            const size_t o = (size_t)round * tr->max_windows;
+            if (tr->n_windows) tr->n_windows[round] = m.n;
+            if (tr->n_inserted) tr->n_inserted[round] = (int)pick.size();
+            for (int i = 0; i < m.n; ++i) {
+                if (tr->lambda) tr->lambda[o + i] = lam[i];
+                if (tr->mu) tr->mu[o + i] = mu[i];
+                if (tr->log_var) tr->log_var[o + i] = lv[i];
+                if (tr->ovl && i + 1 < m.n) tr->ovl[o + i] = ovl[i];
+            }
+            for (size_t q = 0; q < pick.size(); ++q) {
+                if (tr->inserted) tr->inserted[o + q] = mids[pick[q]];
+                if (tr->target) tr->target[o + q] = mu_mid[pick[q]];
+            }
+            tr->rounds = round + 1;
+        }
         if (pick.empty()) break;
         // seed jobs: candidates = end states of the two neighbours
         std::vector<SeedJob> jobs(pick.size());
@@ -1349,8 +1374,29 @@ pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, cons
         CK(upload(&d_jobs, jobs.data(), jobs.size()), "upload seed jobs");
         const size_t per = chain ? 3 * (size_t)N : 1;
         cudaError_t e = cudaMalloc(&rn->d_start, sizeof(double) * per * R * new_lam.size());
-        if (e == cudaSuccess) e = seed_launch(d_jobs, (int)jobs.size(), max_cand, N, Np, R, fp64, rn->d_start, g_stream);
+        int *d_choice = nullptr;
+        double *d_cx = nullptr;
+        if (rec && e == cudaSuccess && (tr->seed || tr->cand_x)) {
+            e = cudaMalloc(&d_choice, sizeof(int) * R * jobs.size());
+            if (e == cudaSuccess) e = cudaMalloc(&d_cx, sizeof(double) * max_cand * jobs.size());
+        }
+        if (e == cudaSuccess)
+            e = seed_launch(d_jobs, (int)jobs.size(), max_cand, N, Np, R, fp64, rn->d_start, d_choice, d_cx, g_stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+        if (e == cudaSuccess && d_choice) {
+            std::vector<int> hc((size_t)R * jobs.size());
+            std::vector<double> hx((size_t)max_cand * jobs.size());
+            e = cudaMemcpy(hc.data(), d_choice, sizeof(int) * hc.size(), cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(hx.data(), d_cx, sizeof(double) * hx.size(), cudaMemcpyDeviceToHost);
+            const size_t o = (size_t)round * tr->max_windows;
+            for (size_t q = 0; e == cudaSuccess && q < jobs.size(); ++q) {
+                for (int r = 0; r < R && tr->seed; ++r) tr->seed[(o + q) * R + r] = hc[q * R + r];
+                for (int c = 0; c < 2 * R && tr->cand_x; ++c)
+                    tr->cand_x[(o + q) * 2 * R + c] = c < jobs[q].n_cand ? hx[q * max_cand + c] : NAN;
+            }
+        }
+        cudaFree(d_choice);
+        cudaFree(d_cx);
         cudaFree(d_jobs);
         if (e != cudaSuccess) return cuda_fail(e, "seed");
         if ((st = pick_warps((long long)new_lam.size() * R)) != PMF_OK) return st;

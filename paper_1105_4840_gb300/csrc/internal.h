@@ -185,8 +185,10 @@ struct SeedJob {
     int n_cand;                            // candidates (end states of the neighbours)
     const void *cand[kMaxSeedCandidates];  // positions (chain: 4 values per bead) or x (1D)
 };
+// choice (optional, [n_jobs][replicas]): candidate each replica took;
+// cand_x (optional, [n_jobs][max_cand]): each candidate's final x
 cudaError_t seed_launch(const SeedJob *jobs, int n_jobs, int max_cand, int N, int Np, int replicas, bool fp64,
-                        double *start, cudaStream_t st);
+                        double *start, int *choice, double *cand_x, cudaStream_t st);
 
 // Work distributions of App. C (histogram.cu)
 struct HistStep {

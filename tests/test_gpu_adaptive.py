@@ -123,3 +123,64 @@ def test_adaptive_warp_choice_is_scoped(pmf):
         assert pmf.pmf_chain_get_launch(sysh, 0)[0] == (4 if chosen is None else chosen)
         assert np.all(np.isfinite(res["dF_JE"])) and meta["gpu_seconds"] > 0
         sysh.close()
+
+
+def _check_decisions(meta, threshold, max_windows, R):
+    """Every round's inserted centres are the oracle's insert_windows on the
+    round's own windows and surrogate predictions (its OVL values are the
+    oracle's closed form to 1e-10), the next round starts from the union,
+    and every replica of an inserted window started from the candidate the
+    oracle's seed_order ranks at r mod (2 R)."""
+    tr = meta["trace"]
+    assert len(tr) >= 1
+    for q, rd in enumerate(tr):
+        lam, mu, lv = rd["lambdas"], rd["mu"], rd["log_var"]
+        sd = np.exp(0.5 * lv)
+        ovl_o = np.array([sg.gaussian_overlap(mu[i], sd[i], mu[i + 1], sd[i + 1]) for i in range(lam.size - 1)])
+        np.testing.assert_allclose(rd["ovl"], ovl_o, rtol=0, atol=1e-10)
+        want = sg.insert_windows(lam, mu, lv, threshold)[: max(0, max_windows - lam.size)]
+        np.testing.assert_array_equal(rd["inserted"], want)
+        for j, lam_new in enumerate(rd["inserted"]):
+            i = int(np.searchsorted(lam, lam_new))  # between windows i - 1 and i
+            assert lam[i - 1] < lam_new < lam[i]
+            order = sg.seed_order(rd["cand_x"][j], rd["target"][j])
+            np.testing.assert_array_equal(rd["seed"][j], order[np.arange(R) % order.size])
+        if q + 1 < len(tr):
+            np.testing.assert_array_equal(tr[q + 1]["lambdas"], np.sort(np.concatenate([lam, rd["inserted"]])))
+    assert meta["inserted"] == sum(rd["inserted"].size for rd in tr)
+
+
+def test_adaptive_decisions_match_oracle_1d(pmf):
+    w = inputs.od1d_workload()
+    run = w["run"]
+    lam0 = np.linspace(-1.5, 1.5, 6)
+    sysh = pmf.pmf_create_system_1d(w["a"], w["x0"])
+    init = pmf.pack_mlp_params(sg.init_params(2))
+    meta, _ = pmf.pmf_run_adaptive(sysh, lam0, pmf.make_params(run), init, threshold=0.5, max_rounds=4,
+                                   max_windows=64, mlp_steps=400, mlp_batch=512, mlp_lr=3e-3, mlp_seed=5,
+                                   trace=True)
+    assert meta["inserted"] > 0
+    _check_decisions(meta, 0.5, 64, run.replicas)
+    # the final grid is the last round's windows plus its insertions
+    last = meta["trace"][-1]
+    np.testing.assert_array_equal(meta["lambdas"], np.sort(np.concatenate([last["lambdas"], last["inserted"]])))
+
+
+def test_adaptive_decisions_match_oracle_chain(pmf):
+    """A 40-bead chain on a coarse grid (and a window cap that bites): the
+    seeding candidates are chain end states, their x the end-to-end
+    distances."""
+    n = 40
+    p = inputs.chain_params(n, 21)
+    start = f32(inputs.chain_start(p, 50, target_x=1.0))
+    run = inputs.RunSettings(k=500.0, kT=inputs.kT_of(300.0), dt=0.001, gamma=5.0, n_steps=2000, n_equil=200,
+                             stride=50, replicas=6, seed=3)
+    lam0 = np.linspace(1.0, 1.9, 4)
+    sysh = pmf.pmf_create_system_chain([p], [start])
+    init = pmf.pack_mlp_params(sg.init_params(2))
+    meta, res = pmf.pmf_run_adaptive(sysh, lam0, pmf.make_params(run), init, threshold=0.3, max_rounds=2,
+                                     max_windows=9, mlp_steps=300, mlp_batch=256, mlp_lr=3e-3, mlp_seed=2,
+                                     trace=True)
+    assert meta["inserted"] > 0
+    _check_decisions(meta, 0.3, 9, run.replicas)
+    assert np.all(np.isfinite(res["dF_JE"]))

@@ -211,6 +211,29 @@ def test_chain_free_energy_within_two_se_of_oracle(pmf):
         assert np.all(np.abs(g[key] - o[key])[1:] <= 2.0 * se[1:] + 1e-9), (key, g[key], o[key], se)
 
 
+def test_chain_full_path_within_two_se_of_oracle(pmf):
+    """The 104-bead workload's whole path (21 windows, 1.3 -> 3.3 nm) at 16
+    replicas x 2e4 steps per window, same Philox streams on both sides: the
+    FP32 GPU run's dF^JE(lambda_s) and dF_fluct(lambda_s) within 2 combined
+    jackknife standard errors of the FP64 oracle's (trajectories decorrelate
+    within a few thousand steps, so the comparison is statistical); every
+    other profile point within 3."""
+    w = inputs.chain_workload(n_steps=20000, replicas=16)
+    p, start, run = w["params"], w["start"], w["run"]
+    lam = run.lambdas
+    assert lam.size == 21
+    _, rr = _run_chain(pmf, p, f32(start), run, lam)
+    g = rr.free_energy()
+    xo = oracle_chain_samples(p, start, lam, run)
+    o = est.free_energy_profile(xo, lam, run.k, run.kT)
+    for key, sek in (("dF_JE", "se_JE"), ("dF_fluct", "se_fluct")):
+        se = np.hypot(g[sek], o[sek])
+        z = (g[key] - o[key])[1:] / se[1:]
+        print(key, "end", g[key][-1], o[key][-1], "z", np.round(z, 2))
+        assert abs(z[-1]) <= 2.0, (key, g[key][-1], o[key][-1], se[-1])
+        assert np.all(np.abs(z) <= 3.0), (key, z)
+
+
 def test_gaussian_chain_matches_radial_quadrature(pmf):
     """Bond-only chain (r0 = 0): <x> in each window equals the radial
     quadrature of the Gaussian end-to-end distribution in the trap."""

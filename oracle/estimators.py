@@ -255,3 +255,53 @@ def free_energy_from_partials(P, lambdas, k: float, kT: float) -> dict:
     out["gamma2"] = k * var_x / kT
     out["lambda"] = lam.copy()
     return out
+
+
+def turn_on_free_energy(x_first, lam1: float, k: float, kT: float) -> float:
+    """Eq. (5): the free energy of turning the trap on at lambda_1,
+    dF(lambda_1, k) = F(lambda_1, k) - F_0 = kT ln < exp(k/2 (x_1 - lambda_1)^2 / kT) >
+    over the trapped ensemble (the samples of the first window), evaluated as
+    M + kT ln((1/n) sum exp((u - M)/kT)) with u = k/2 (x_1 - lambda_1)^2,
+    M = max u and an exactly rounded sum."""
+    x = np.asarray(x_first, dtype=np.float64).ravel()
+    if x.size == 0:
+        return math.nan
+    u = 0.5 * k * (x - lam1) ** 2
+    M = float(u.max())
+    return M + kT * math.log(math.fsum(np.exp((u - M) / kT).tolist()) / x.size)
+
+
+def state_free_energy(samples, lambdas, k: float, kT: float) -> dict:
+    """Eq. (15): the state free energy G(lambda_j, lambda_1) =
+    dF^JE(lambda_j, lambda_1, k) - dF(lambda_1, k) for every profile point j
+    (dF^JE of Eq. (12) as in free_energy_profile, dF(lambda_1, k) of Eq. (5)
+    on the first window's samples), so G(lambda_1, lambda_1) = -dF(lambda_1, k).
+    Standard error: delete-one-replica jackknife.  The first window's samples
+    enter both its JE increment and the turn-on average, so replica r of that
+    window is left out of both together; the jackknife variances of the other
+    windows' JE increments are added.  Returns {"G", "se_G", "dF_turn_on"}."""
+    lam = np.asarray(lambdas, dtype=np.float64)
+    s = lam.size
+    xs = []
+    for i in range(s):
+        x = np.asarray(samples[i], dtype=np.float64)
+        xs.append(x[None, :] if x.ndim == 1 else x)
+    prof = free_energy_profile(xs, lam, k, kT)
+    on = turn_on_free_energy(xs[0], lam[0], k, kT)
+    G = prof["dF_JE"] - on
+    se = np.full(s, math.nan)
+
+    def je_inc(x, i):
+        return je_increment(work_increment(x, lam[i], lam[i + 1], k), kT)
+
+    def loo(x):
+        return [np.delete(x, r, axis=0) for r in range(x.shape[0])]
+
+    if xs[0].shape[0] >= 2:
+        jk = [_jackknife_var([je_inc(x, i) for x in loo(xs[i])]) for i in range(1, s - 1)]
+        se[0] = math.sqrt(_jackknife_var([turn_on_free_energy(x, lam[0], k, kT) for x in loo(xs[0])]))
+        if s > 1:
+            v0 = _jackknife_var([je_inc(x, 0) - turn_on_free_energy(x, lam[0], k, kT) for x in loo(xs[0])])
+            for j in range(1, s):
+                se[j] = math.sqrt(v0 + math.fsum(jk[: j - 1]))
+    return {"G": G, "se_G": se, "dF_turn_on": on}

@@ -106,11 +106,17 @@ template <typename R> struct Smem {
     Vec4<R> *bslot;  // [4][Np]
     R *noise;        // [2][4 * n_blocks] normals of an O-step (by step parity), dof d = 3 b + axis
     Vec2<R> *mass;   // [Np] (1/m, c2 sqrt(kT/m)) of the O-step, per run
+    Vec4<R> *dih;    // [N] dihedral constants (copied once per CTA)
+    int4 *units;     // [NW][max_units] this CTA's copy of the nonbonded schedule
+    int *ucount;     // [NW]
     // FP32 packed path: entry p of tile T pairs ring positions p and p + D
-    // (D = pair_offset(W)): posp[2(64T + p)] = (x_p, x_{p+D}, y_p, y_{p+D}),
-    // posp[2(64T + p) + 1] = (z_p, z_{p+D}, s_p, s_{p+D}),
-    // eqp[64T + p] = (e_p, e_{p+D}, q_p, q_{p+D}), p < 2W.
-    float4 *posp;
+    // (D = pair_offset(W)): posa[64T + p] = (x_p, x_{p+D}, y_p, y_{p+D}),
+    // posb[64T + p] = (z_p, z_{p+D}, s_p, s_{p+D}),
+    // eqp[64T + p] = (e_p, e_{p+D}, q_p, q_{p+D}), p < 2W.  Each is a
+    // contiguous float4 array, so a warp reading consecutive entries takes the
+    // minimum four shared-memory wavefronts.
+    float4 *posa;
+    float4 *posb;
     float4 *eqp;
     int *flag;
 };
@@ -148,12 +154,12 @@ __device__ __forceinline__ void pack_tile(const Smem<float> &s, int t, int lane,
     const float qz = __shfl_sync(0xffffffffu, p.z, src);
     const float qs = __shfl_sync(0xffffffffu, sig, src);
     if (lane < W) {
-        float4 *base = s.posp + 2 * 64 * t;
+        float4 *pa = s.posa + 64 * t, *pb = s.posb + 64 * t;
         const float4 lo = make_float4(p.x, qx, p.y, qy), hi = make_float4(p.z, qz, sig, qs);
-        base[2 * lane] = lo;
-        base[2 * lane + 1] = hi;
-        base[2 * (lane + W)] = lo;
-        base[2 * (lane + W) + 1] = hi;
+        pa[lane] = lo;
+        pb[lane] = hi;
+        pa[lane + W] = lo;
+        pb[lane + W] = hi;
     }
 }
 
@@ -303,7 +309,7 @@ __device__ __forceinline__ void quad_piece(const Smem<float> &s, Vec4<float> *fw
     const float2 two = f2(2.f, 2.f), mone = f2(-1.f, -1.f);
     float2 f1x = f2(0.f, 0.f), f1y = f1x, f1z = f1x, f2x = f1x, f2y = f1x, f2z = f1x;
     float2 fjx = f1x, fjy = f1x, fjz = f1x;
-    const float4 *A = s.posp + 2 * (64 * J + lr);
+    const float4 *PA = s.posa + 64 * J + lr, *PB = s.posb + 64 * J + lr;
     const float4 *E = s.eqp + 64 * J + lr;
     const int src = (lane & ~(W - 1)) | ((lr + 2) & (W - 1));
     const int src_jump = (lane & ~(W - 1)) | ((lr + 10) & (W - 1));
@@ -313,7 +319,7 @@ __device__ __forceinline__ void quad_piece(const Smem<float> &s, Vec4<float> *fw
 #pragma unroll
     for (int k = 0; k < NST; ++k) {
         const int t = TB + 2 * k + ((SPLIT && 2 * k >= NST) ? 8 : 0);
-        const float4 a = A[2 * t], b = A[2 * t + 1], e = E[t];
+        const float4 a = PA[t], b = PB[t], e = E[t];
         const float2 xj = f2(a.x, a.y), yj = f2(a.z, a.w), zj = f2(b.x, b.y), sj = f2(b.z, b.w);
         const float2 ej = f2(e.x, e.y), cj = f2(e.z, e.w);
         // pairs of i1 with (j_a, j_b)
@@ -511,7 +517,7 @@ __device__ __forceinline__ R bonded_owner(const ChainArgs<R> &a, const Smem<R> &
             f1 = sub(f1, scl(add(ga, gc), pref));
         }
         if (a.has_dih && t + 3 < N) {
-            const Vec4<R> K = a.dih[t];
+            const Vec4<R> K = s.dih[t];
             if (K.w != R(0)) {
                 const V3<R> pc = pos_of(s, t + 2), pd = pos_of(s, t + 3);
                 const V3<R> b1 = sub(pb, pa), b2 = sub(pc, pb), b3 = sub(pd, pc);
@@ -598,7 +604,10 @@ __device__ __forceinline__ void work_set(const Smem<double> &s, double W) { s.ve
 
 template <typename R, int NW, bool SMD>
 __device__ __forceinline__ void force_phase(const ChainArgs<R> &a, const Smem<R> &s, R lam, long long done,
-                                            long long nequil, long long sample_base, bool first, uint32_t uid)
+                                            long long nequil, long long sample_base, bool first, uint32_t uid,
+                                            long long rec)
+// rec: index of the x record taken at this force evaluation (the state after
+// `done` steps), or -1 (records are every `stride` steps after nequil).
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     gen_noise<R>(a, s, uid, done, first ? 0 : early_noise_blocks(a.N, a.n_tiles, NW), (3 * a.N + 3) >> 2,
@@ -619,16 +628,16 @@ __device__ __forceinline__ void force_phase(const ChainArgs<R> &a, const Smem<R>
                     work_set(s, W);
                 }
             }
-            if (!first && done > nequil && (done - nequil) % a.stride == 0) {
-                a.xout[sample_base + (done - nequil) / a.stride - 1] = (float)x;
-                if constexpr (SMD) a.wout[sample_base + (done - nequil) / a.stride - 1] = W;
+            if (rec >= 0) {
+                a.xout[sample_base + rec] = (float)x;
+                if constexpr (SMD) a.wout[sample_base + rec] = W;
             }
         }
     }
     if (a.nonbonded) {
         Vec4<R> *fw_mine = s.fw + warp * a.Np;
-        const int cnt = a.unit_count[warp];
-        const int4 *u = a.units + warp * a.max_units;
+        const int cnt = s.ucount[warp];
+        const int4 *u = s.units + warp * a.max_units;
         for (int q = 0; q < cnt; ++q) {
             const int4 e = u[q];  // (I1, I2 or -1, J, kind | near1 << 8 | near2 << 9)
             const int kind = e.w & 0xff;
@@ -724,8 +733,8 @@ __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s
             if (i >= 2 * W) continue;
             const Vec4<R> p0 = s.posd[t * 64 + (i & (W - 1))], p1 = s.posd[t * 64 + ((i + D) & (W - 1))];
             const Vec2<R> q0 = s.eqd[t * 64 + (i & (W - 1))], q1 = s.eqd[t * 64 + ((i + D) & (W - 1))];
-            s.posp[2 * e] = make_float4(p0.x, p1.x, p0.y, p1.y);
-            s.posp[2 * e + 1] = make_float4(p0.z, p1.z, p0.w, p1.w);
+            s.posa[e] = make_float4(p0.x, p1.x, p0.y, p1.y);
+            s.posb[e] = make_float4(p0.z, p1.z, p0.w, p1.w);
             s.eqp[e] = make_float4(q0.x, q1.x, q0.y, q1.y);
         }
         __syncthreads();
@@ -733,8 +742,13 @@ __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s
     const long long nequil = origin + a.nequil_w[w];  // equilibration counts from the window's first step
     const long long sample_base = a.off_w[w] + (long long)r * a.tw[w];
     force_phase<R, NW, SMD>(a, s, SMD ? (R)smd_lambda(a.lambda[0], a.smd_vdt, s0, nequil) : lam, s0, nequil,
-                            sample_base, true, uid);
+                            sample_base, true, uid, -1);
     __syncthreads();
+    // record q is taken after nequil + (q + 1) stride steps: the first one
+    // after s0 and the step it falls on (one division per segment instead
+    // of a 64-bit remainder per step)
+    long long rec_q = s0 >= nequil ? (s0 - nequil) / a.stride : 0;
+    long long rec_step = nequil + (rec_q + 1) * a.stride;
 
     const int warp = tid >> 5, lane = tid & 31;
     for (long long step = s0;; ++step) {
@@ -794,8 +808,13 @@ __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s
                          (NW - a.n_tiles) * 32);
         if (step >= s1) break;
         __syncthreads();
+        long long rec = -1;
+        if (step + 1 == rec_step) {
+            rec = rec_q++;
+            rec_step += a.stride;
+        }
         force_phase<R, NW, SMD>(a, s, SMD ? (R)smd_lambda(a.lambda[0], a.smd_vdt, step + 1, nequil) : lam,
-                                step + 1, nequil, sample_base, false, uid);
+                                step + 1, nequil, sample_base, false, uid, rec);
         __syncthreads();
         if (*s.flag) {
             if (tid == 0) atomicOr(a.err, kErrNonFinite);
@@ -890,14 +909,23 @@ __global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW =
         s.bslot = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * 4;
         s.noise = reinterpret_cast<R *>(p); p += 2 * sizeof(Vec4<R>) * ((3 * a.N + 3) >> 2);
         s.mass = reinterpret_cast<Vec2<R> *>(p); p += sizeof(Vec2<R>) * a.Np;
-        s.posp = nullptr;
+        s.posa = nullptr;
+        s.posb = nullptr;
         s.eqp = nullptr;
         if constexpr (kPacked<R>) {
-            s.posp = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 2 * 64 * a.n_tiles;
+            s.posa = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 64 * a.n_tiles;
+            s.posb = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 64 * a.n_tiles;
             s.eqp = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 64 * a.n_tiles;
         }
+        s.dih = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.N;
+        s.units = reinterpret_cast<int4 *>(p); p += sizeof(int4) * NW * a.max_units;
+        s.ucount = reinterpret_cast<int *>(p); p += sizeof(int) * NW;
         s.flag = reinterpret_cast<int *>(p);
     }
+    // static per-CTA data: the nonbonded schedule and the dihedral constants
+    for (int e = threadIdx.x; e < NW * a.max_units; e += NW * 32) s.units[e] = a.units[e];
+    for (int e = threadIdx.x; e < NW; e += NW * 32) s.ucount[e] = a.unit_count[e];
+    for (int b = threadIdx.x; b < a.N; b += NW * 32) s.dih[b] = a.dih[b];
     // one call site of simulate() for both modes keeps the kernel compact;
     // the item survives the segment in shared memory, not in registers
     for (long long iter = 0;; ++iter) {
@@ -1042,11 +1070,12 @@ std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed)
     return per;
 }
 
-template <typename R> size_t chain_smem_bytes(const ChainGeometry &g, int NW)
+template <typename R> size_t chain_smem_bytes(const ChainGeometry &g, int NW, int max_units)
 {
     size_t b = sizeof(Vec4<R>) * g.n_tiles * 64 + sizeof(Vec2<R>) * g.n_tiles * 64 + sizeof(Vec4<R>) * g.Np * (1 + NW + 4) +
                2 * sizeof(Vec4<R>) * ((3 * g.N + 3) / 4) + sizeof(Vec2<R>) * g.Np + 16;
     if (kPacked<R>) b += sizeof(float4) * 3 * 64 * g.n_tiles;
+    b += sizeof(Vec4<R>) * g.N + sizeof(int4) * NW * max_units + sizeof(int) * NW;
     return b;
 }
 
@@ -1187,7 +1216,8 @@ cudaError_t ChainModel::set_warps(int NW)
 int ChainModel::n_beads() const { return p->geo.N; }
 size_t ChainModel::smem_bytes() const
 {
-    return p->precision == 1 ? chain_smem_bytes<double>(p->geo, p->NW) : chain_smem_bytes<float>(p->geo, p->NW);
+    return p->precision == 1 ? chain_smem_bytes<double>(p->geo, p->NW, p->max_units)
+                             : chain_smem_bytes<float>(p->geo, p->NW, p->max_units);
 }
 int ChainModel::n_padded() const { return p->geo.Np; }
 int ChainModel::precision() const { return p->precision; }
@@ -1266,7 +1296,7 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     a.queue_start = L.queue_start;
     a.wait_ns = L.wait_ns > 0 ? L.wait_ns : kDefaultSegmentWaitNs;
     a.abort = L.abort;
-    const size_t smem = chain_smem_bytes<R>(m->geo, NW);
+    const size_t smem = chain_smem_bytes<R>(m->geo, NW, m->max_units);
     void (*kern)(const ChainArgs<R>) = a.smd ? chain_kernel<R, NW, true> : chain_kernel<R, NW, false>;
     // The attribute is the kernel's upper limit, shared by every chain that
     // launches it: raise it to the device's opt-in maximum rather than to this

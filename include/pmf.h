@@ -330,6 +330,27 @@ typedef struct {
 pmf_status pmf_work_distributions(const pmf_run *run, const pmf_hist_params *hp, double *omega,
                                   size_t omega_capacity, double *dF_JE, double *var_ZW, double *lost);
 
+/* State free energy of Eq. (15): G(lambda_j, lambda_1) = dF^JE(lambda_j,
+ * lambda_1, k) - dF(lambda_1, k) at every profile point j (so the value at
+ * lambda_1 is -dF(lambda_1, k)), where dF(lambda_1, k) = F(lambda_1, k) - F_0
+ * is the free energy of turning the trap on, from Eq. (5):
+ * kT ln <exp(k/2 (x_1 - lambda_1)^2 / kT)> over the first window's samples
+ * (max-shifted log-sum-exp, compensated sums, FP64 on the GPU).  se_G: the
+ * delete-one-replica jackknife (the first window's replica r is left out of
+ * its JE increment and of the turn-on average together; the other windows'
+ * JE variances are added).  G and se_G (host) hold >= n_windows values (may
+ * be NULL), *dF_turn_on (host, may be NULL) receives dF(lambda_1, k).  Eq. (5)
+ * converges only when the trapped first window samples the whole support of
+ * the unbiased ensemble (a soft trap); with a stiff trap the turn-on term is
+ * biased low.  The run must be finished and a single-path window run
+ * (PMF_EINVAL for batches and pulled runs); capacity >= n_windows. */
+pmf_status pmf_state_free_energy(pmf_run *run, double *G, double *se_G, double *dF_turn_on, int capacity);
+/* The same on caller-supplied samples (arguments as for
+ * pmf_free_energy_from_samples; 1 <= n_windows <= 1024). */
+pmf_status pmf_state_free_energy_from_samples(const float *x, int x_on_device, const double *lambda, int n_windows,
+                                              int replicas, const int64_t *samples_per_window, double k, double kT,
+                                              double *G, double *se_G, double *dF_turn_on);
+
 /* The same reduction on caller-supplied samples x (layout of pmf_run_info
  * with `replicas` and samples_per_window[n_windows]); x is a host pointer
  * (x_on_device = 0) or a device pointer (x_on_device = 1). */

@@ -883,6 +883,90 @@ pmf_status pmf_run_partials(const pmf_run *run, double *out, size_t capacity, si
     return PMF_OK;
 }
 
+// Eq. (5) / Eq. (15) on a filled reduction layout (device pointers); the
+// caller's G, se_G (n_windows each) and dF_turn_on (one value), host.
+static pmf_status state_common(const ReduceLayout &L, void *scratch, double *G, double *se_G, double *dF_turn_on)
+{
+    struct Tmp {
+        void *pt = nullptr;
+        double *out = nullptr;
+        ~Tmp() { cudaFree(pt); cudaFree(out); }
+    } t;
+    const int s = L.n_windows;
+    CK(cudaMalloc(&t.pt, partial_bytes(1, L.replicas)), "alloc turn-on partials");
+    CK(cudaMalloc(&t.out, sizeof(double) * (2 * (size_t)s + 1)), "alloc state results");
+    cudaError_t e = state_launch(L, scratch, t.pt, t.out, g_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "state free energy");
+    std::vector<double> h(2 * (size_t)s + 1);
+    CK(cudaMemcpyAsync(h.data(), t.out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g_stream), "copy");
+    CK(cudaStreamSynchronize(g_stream), "sync");
+    if (G) std::memcpy(G, h.data(), sizeof(double) * s);
+    if (se_G) std::memcpy(se_G, h.data() + s, sizeof(double) * s);
+    if (dF_turn_on) *dF_turn_on = h[2 * (size_t)s];
+    return PMF_OK;
+}
+
+pmf_status pmf_state_free_energy(pmf_run *run, double *G, double *se_G, double *dF_turn_on, int capacity)
+{
+    if (pmf_status s = need_finished(run)) return s;
+    if (run->items.size() != 1 || run->d_w) return fail(PMF_EINVAL, "pmf_state_free_energy: single-path window runs only");
+    if (capacity < run->n_windows) return fail(PMF_EINVAL, "pmf_state_free_energy: capacity smaller than n_windows");
+    const ReduceLayout L = layout_of(run);
+    cudaError_t e = reduce_launch(L, run->d_scratch, run->d_res, g_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce");
+    run->reduced = true;
+    return state_common(L, run->d_scratch, G, se_G, dF_turn_on);
+}
+
+pmf_status pmf_state_free_energy_from_samples(const float *x, int x_on_device, const double *lambda, int n_windows,
+                                              int replicas, const int64_t *samples_per_window, double k, double kT,
+                                              double *G, double *se_G, double *dF_turn_on)
+{
+    if (!x || !lambda || !samples_per_window) return fail(PMF_EINVAL, "null argument");
+    if (pmf_status s = need_device()) return s;
+    if (n_windows < 1 || n_windows > 1024 || replicas < 1 || replicas > 65535)
+        return fail(PMF_EINVAL, "bad window / replica count");
+    if (!(k > 0) || !(kT > 0)) return fail(PMF_EINVAL, "need k > 0, kT > 0");
+    std::vector<long long> off(n_windows), tw(n_windows);
+    long long total = 0;
+    for (int i = 0; i < n_windows; ++i) {
+        if (samples_per_window[i] < 1) return fail(PMF_EINVAL, "each window needs at least one sample");
+        tw[i] = samples_per_window[i];
+        off[i] = total;
+        total += tw[i] * replicas;
+    }
+    struct Tmp {
+        double *lam = nullptr;
+        long long *off = nullptr, *tw = nullptr;
+        float *x = nullptr;
+        void *scratch = nullptr;
+        double *res = nullptr;
+        ~Tmp() { cudaFree(lam); cudaFree(off); cudaFree(tw); cudaFree(x); cudaFree(scratch); cudaFree(res); }
+    } t;
+    CK(upload(&t.lam, lambda, n_windows), "upload lambda");
+    CK(upload(&t.off, off.data(), n_windows), "upload offsets");
+    CK(upload(&t.tw, tw.data(), n_windows), "upload counts");
+    const float *dx = x;
+    if (!x_on_device) {
+        CK(upload(&t.x, x, (size_t)total), "upload samples");
+        dx = t.x;
+    }
+    CK(cudaMalloc(&t.scratch, reduce_scratch_bytes(n_windows, replicas)), "alloc scratch");
+    CK(cudaMalloc(&t.res, sizeof(double) * kResFields * n_windows), "alloc result");
+    ReduceLayout L;
+    L.x = dx;
+    L.lambda = t.lam;
+    L.off_w = t.off;
+    L.tw = t.tw;
+    L.n_windows = n_windows;
+    L.replicas = replicas;
+    L.k = k;
+    L.kT = kT;
+    cudaError_t e = reduce_launch(L, t.scratch, t.res, g_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce");
+    return state_common(L, t.scratch, G, se_G, dF_turn_on);
+}
+
 pmf_status pmf_free_energy_from_partials(const double *partials, const double *lambda, int n_windows, int replicas,
                                          double k, double kT, pmf_free_energy_result *res)
 {

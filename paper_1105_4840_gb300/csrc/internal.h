@@ -151,6 +151,10 @@ constexpr int kNoAllocMaxWindows = 1024;
 constexpr long long kNoAllocMaxWindowReplicas = 65536;  // n_windows * replicas
 cudaError_t reduce_noalloc_launch(const float *x, const double *lambda, int n_windows, int replicas,
                                   long long samples_per_window, double k, double kT, double *out, cudaStream_t st);
+// Eq. (5) / Eq. (15) after reduce_launch filled `scratch`: out[2 s + 1] =
+// G(lambda_j, lambda_1) [s], its standard error [s], dF(lambda_1, k);
+// turn_partials: device buffer of partial_bytes(1, replicas).
+cudaError_t state_launch(const ReduceLayout &L, void *scratch, void *turn_partials, double *out, cudaStream_t st);
 cudaError_t work_samples_launch(const ReduceLayout &L, int mode, long long samples_per_replica, double *out,
                                 cudaStream_t st);
 

@@ -290,6 +290,125 @@ __global__ void profile_kernel(const ReduceLayout L, const WindowOut *wo, double
     }
 }
 
+// ---------------------------------------------------------------------------
+// Eq. (5) and Eq. (15).  The free energy of turning the trap on at lambda_1,
+// dF(lambda_1, k) = kT ln < exp(u / kT) >, u = k/2 (x_1 - lambda_1)^2, over the
+// first window's samples, and the state free energy
+// G(lambda_j, lambda_1) = dF^JE(lambda_j, lambda_1, k) - dF(lambda_1, k).
+// Stage 1 (one CTA per replica of the first window): the replica's
+// max-shifted sum in the form of the JE partials with w = -u:
+// m = min w = -max u, S = sum exp(-(w - m)/kT) = sum exp((u - max u)/kT).
+// Stage 2 (one CTA): the turn-on estimate, G at every profile point, and the
+// delete-one-replica jackknife (the first window's replica r is left out of
+// its JE increment and of the turn-on average together; the other windows'
+// jackknife variances of their increments are added).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPartialThreads) turn_on_partial_kernel(const ReduceLayout L, Partial *out)
+{
+    __shared__ double red[kPartialThreads / 32 + 1];
+    const int r = blockIdx.x;
+    const long long T = L.tw[0];
+    const float *x = L.x + L.off_w[0] + (long long)r * T;
+    const double l1 = L.lambda[0], hk = 0.5 * L.k, beta = 1.0 / L.kT;
+    double m = INFINITY, S = 0;
+    for (long long t = threadIdx.x; t < T; t += kPartialThreads) {
+        const double d = (double)x[t] - l1;
+        const double wv = -hk * d * d;
+        if (wv < m) {
+            S = (m == INFINITY ? 0.0 : S * exp((wv - m) * beta)) + 1.0;
+            m = wv;
+        } else {
+            S += exp((m - wv) * beta);
+        }
+    }
+    const double mb = block_min<kPartialThreads>(m, red);
+    const double St = m == INFINITY ? 0.0 : S * exp((mb - m) * beta);
+    const double Sb = block_sum<kPartialThreads>(St, red);
+    if (threadIdx.x == 0) out[r] = Partial{mb, Sb, (double)T, 0.0, 0.0};
+}
+
+// The window's exponential sums of the replicas on a common shift: the
+// shift (minimum of the replicas' minima) and the compensated total.
+template <int NT>
+__device__ void common_shift_sum(const Partial *p, int R, double kT, double *red, double &m, double &hi, double &lo,
+                                 double &n)
+{
+    double mm = INFINITY;
+    for (int r = threadIdx.x; r < R; r += NT)
+        if (p[r].n > 0) mm = fmin(mm, p[r].m);
+    m = block_min<NT>(mm, red);
+    double se = 0, ce = 0, sn = 0;
+    for (int r = threadIdx.x; r < R; r += NT) {
+        neumaier(se, ce, p[r].n > 0 ? p[r].S * exp(-(p[r].m - m) / kT) : 0.0);
+        sn += p[r].n;
+    }
+    block_sum_pair<NT>(se, ce, red, hi, lo);
+    n = block_sum<NT>(sn, red);
+}
+
+__global__ void __launch_bounds__(kWindowThreads) state_kernel(const ReduceLayout L, const Partial *P, const Partial *Pt,
+                                                               const WindowOut *wo, double *out)
+{
+    __shared__ double red[2 * (kWindowThreads / 32 + 1)];
+    const int R = L.replicas, s = L.n_windows;
+    const double kT = L.kT;
+    double m0, S0h, S0l, n, mt, Sth, Stl, nt;
+    common_shift_sum<kWindowThreads>(P, R, kT, red, m0, S0h, S0l, n);   // first window, Eq. (12)
+    common_shift_sum<kWindowThreads>(Pt, R, kT, red, mt, Sth, Stl, nt);  // first window, Eq. (5)
+    const double on = kT * log((Sth + Stl) / nt) - mt;
+    // leave-one-out values of the first window: its JE increment minus the
+    // turn-on estimate (g), and the turn-on estimate alone (t)
+    auto e_of = [&](const Partial &q, double mm) { return q.n > 0 ? q.S * exp(-(q.m - mm) / kT) : 0.0; };
+    double vg = 0, vt = 0;
+    const bool jk = R >= 2;
+    if (jk) {
+        for (int r = threadIdx.x; r < R; r += kWindowThreads) {
+            const double nm = n - P[r].n;
+            const double t = kT * log(sum_without(Sth, Stl, e_of(Pt[r], mt)) / nm) - mt;
+            const double je = m0 - kT * log(sum_without(S0h, S0l, e_of(P[r], m0)) / nm);
+            vg += je - t;
+            vt += t;
+        }
+    }
+    const double mg = block_sum<kWindowThreads>(vg, red) / R;
+    const double mtt = block_sum<kWindowThreads>(vt, red) / R;
+    double qg = 0, qt = 0;
+    if (jk) {
+        for (int r = threadIdx.x; r < R; r += kWindowThreads) {
+            const double nm = n - P[r].n;
+            const double t = kT * log(sum_without(Sth, Stl, e_of(Pt[r], mt)) / nm) - mt;
+            const double je = m0 - kT * log(sum_without(S0h, S0l, e_of(P[r], m0)) / nm);
+            qg += (je - t - mg) * (je - t - mg);
+            qt += (t - mtt) * (t - mtt);
+        }
+    }
+    const double var_g = (R - 1.0) / R * block_sum<kWindowThreads>(qg, red);
+    const double var_t = (R - 1.0) / R * block_sum<kWindowThreads>(qt, red);
+    if (threadIdx.x == 0) {
+        double je = 0, v = var_g;
+        for (int j = 0; j < s; ++j) {
+            if (j > 0) je += wo[j - 1].je;
+            if (j > 1) v += wo[j - 1].jk_je;
+            out[j] = je - on;                                              // G(lambda_j, lambda_1)
+            out[s + j] = jk ? sqrt(j == 0 ? var_t : v) : NAN;              // its standard error
+        }
+        out[2 * s] = on;                                                   // dF(lambda_1, k), Eq. (5)
+    }
+}
+
+cudaError_t state_launch(const ReduceLayout &L, void *scratch, void *turn_partials, double *out, cudaStream_t st)
+{
+    const Partial *P = static_cast<const Partial *>(scratch);
+    const WindowOut *wo =
+        reinterpret_cast<const WindowOut *>(static_cast<const char *>(scratch) + partial_bytes(L.n_windows, L.replicas));
+    Partial *Pt = static_cast<Partial *>(turn_partials);
+    turn_on_partial_kernel<<<L.replicas, kPartialThreads, 0, st>>>(L, Pt);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    state_kernel<<<1, kWindowThreads, 0, st>>>(L, P, Pt, wo, out);
+    return cudaGetLastError();
+}
+
 size_t reduce_scratch_bytes(int n_windows, int replicas)
 {
     return sizeof(Partial) * (size_t)n_windows * replicas + sizeof(WindowOut) * (size_t)n_windows + 256;

@@ -134,6 +134,9 @@ def _load():
                                      C.POINTER(C.c_size_t), C.POINTER(C.c_int)]
     L.pmf_run_reduce.argtypes = [P]
     L.pmf_run_set_queue_start.argtypes = [P, C.c_int64]
+    L.pmf_state_free_energy.argtypes = [P, _D, _D, _D, C.c_int]
+    L.pmf_state_free_energy_from_samples.argtypes = [C.c_void_p, C.c_int, _D, C.c_int, C.c_int, _I64, C.c_double,
+                                                     C.c_double, _D, _D, _D]
     L.pmf_free_energy_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int64,
                                           C.c_double, C.c_double, C.c_void_p]
     L.pmf_mlp_create.argtypes = [_F, C.c_double, C.c_double, C.POINTER(P)]
@@ -161,7 +164,8 @@ def _load():
                  "pmf_run_wait", "pmf_get_run_info", "pmf_x_samples", "pmf_work_samples",
                  "pmf_free_energy", "pmf_free_energy_from_samples", "pmf_final_state",
                  "pmf_run_partials", "pmf_free_energy_from_partials", "pmf_work_distributions", "pmf_philox",
-                 "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_run_set_queue_start", "pmf_free_energy_noalloc",
+                 "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_run_set_queue_start", "pmf_state_free_energy",
+                 "pmf_state_free_energy_from_samples", "pmf_free_energy_noalloc",
                  "pmf_mlp_create", "pmf_mlp_get_params", "pmf_mlp_predict", "pmf_mlp_gradient", "pmf_mlp_train",
                  "pmf_overlap", "pmf_run_adaptive", "pmf_chain_set_warps", "pmf_chain_set_grid", "pmf_chain_get_launch",
                  "pmf_chain_autotune", "pmf_fp32_peak", "pmf_fp64_peak", "pmf_set_stream"):
@@ -329,6 +333,13 @@ class Run:
                "pmf_work_distributions")
         return {"omega": om, "dF_JE": dF, "var_ZW": var, "lost": lost}
 
+    def state_free_energy(self):
+        """Eq. (15): dict with G and se_G per profile point and dF_turn_on (Eq. (5))."""
+        s = self.lambdas.size
+        G, se, on = np.zeros(s), np.zeros(s), C.c_double()
+        _check(lib.pmf_state_free_energy(self.handle, _dp(G), _dp(se), C.byref(on), s), "pmf_state_free_energy")
+        return {"G": G, "se_G": se, "dF_turn_on": on.value}
+
     def smd_work(self):
         """Accumulated work [replicas, records] of a pulled run."""
         n = C.c_size_t()
@@ -457,6 +468,22 @@ def pmf_free_energy_from_samples(x, lambdas, replicas, samples_per_window, k, kT
                                                                  replicas, spw.ctypes.data_as(_I64), k, kT,
                                                                  C.byref(res)),
                     lam.size, "pmf_free_energy_from_samples")
+
+
+def pmf_state_free_energy_from_samples(x, lambdas, replicas, samples_per_window, k, kT, x_on_device=False):
+    """Eq. (15) on caller samples (layout of pmf_free_energy_from_samples)."""
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    spw = np.ascontiguousarray(samples_per_window, dtype=np.int64)
+    if x_on_device:
+        xp = C.c_void_p(int(x))
+    else:
+        xa = np.ascontiguousarray(x, dtype=np.float32)
+        xp = xa.ctypes.data_as(C.c_void_p)
+    G, se, on = np.zeros(lam.size), np.zeros(lam.size), C.c_double()
+    _check(lib.pmf_state_free_energy_from_samples(xp, int(bool(x_on_device)), _dp(lam), lam.size, replicas,
+                                                  spw.ctypes.data_as(_I64), k, kT, _dp(G), _dp(se), C.byref(on)),
+           "pmf_state_free_energy_from_samples")
+    return {"G": G, "se_G": se, "dF_turn_on": on.value}
 
 
 def pmf_philox(seed, c0, c1, c2, c3, n_blocks):

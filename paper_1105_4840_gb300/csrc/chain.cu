@@ -75,6 +75,7 @@ template <typename R> struct ChainArgs {
     R k, kT, dt, gamma;
     R kb, r0, kth, th0;
     int has_angles, has_dih, nonbonded;
+    int static_in_smem;        // copy the schedule and the dihedral constants into shared memory
 };
 
 template <typename R> __device__ __forceinline__ R rsqrt_r(R v);
@@ -106,9 +107,11 @@ template <typename R> struct Smem {
     Vec4<R> *bslot;  // [4][Np]
     R *noise;        // [2][4 * n_blocks] normals of an O-step (by step parity), dof d = 3 b + axis
     Vec2<R> *mass;   // [Np] (1/m, c2 sqrt(kT/m)) of the O-step, per run
-    Vec4<R> *dih;    // [N] dihedral constants (copied once per CTA)
-    int4 *units;     // [NW][max_units] this CTA's copy of the nonbonded schedule
-    int *ucount;     // [NW]
+    const Vec4<R> *dih;  // [N] dihedral constants
+    const int4 *units;   // [NW][max_units] the nonbonded schedule
+    const int *ucount;   // [NW]
+    // (shared-memory copies made once per CTA when the chain leaves room for
+    // them, else the arguments' global arrays)
     // FP32 packed path: entry p of tile T pairs ring positions p and p + D
     // (D = pair_offset(W)): posa[64T + p] = (x_p, x_{p+D}, y_p, y_{p+D}),
     // posb[64T + p] = (z_p, z_{p+D}, s_p, s_{p+D}),
@@ -917,15 +920,23 @@ __global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW =
             s.posb = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 64 * a.n_tiles;
             s.eqp = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 64 * a.n_tiles;
         }
-        s.dih = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.N;
-        s.units = reinterpret_cast<int4 *>(p); p += sizeof(int4) * NW * a.max_units;
-        s.ucount = reinterpret_cast<int *>(p); p += sizeof(int) * NW;
-        s.flag = reinterpret_cast<int *>(p);
+        s.flag = reinterpret_cast<int *>(p); p += 32;  // keeps what follows 32-byte aligned
+        s.dih = a.dih;
+        s.units = a.units;
+        s.ucount = a.unit_count;
+        if (a.static_in_smem) {
+            // static per-CTA data: the nonbonded schedule and the dihedral constants
+            Vec4<R> *dih = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.N;
+            int4 *units = reinterpret_cast<int4 *>(p); p += sizeof(int4) * NW * a.max_units;
+            int *ucount = reinterpret_cast<int *>(p);
+            for (int e = threadIdx.x; e < NW * a.max_units; e += NW * 32) units[e] = a.units[e];
+            for (int e = threadIdx.x; e < NW; e += NW * 32) ucount[e] = a.unit_count[e];
+            for (int b = threadIdx.x; b < a.N; b += NW * 32) dih[b] = a.dih[b];
+            s.dih = dih;
+            s.units = units;
+            s.ucount = ucount;
+        }
     }
-    // static per-CTA data: the nonbonded schedule and the dihedral constants
-    for (int e = threadIdx.x; e < NW * a.max_units; e += NW * 32) s.units[e] = a.units[e];
-    for (int e = threadIdx.x; e < NW; e += NW * 32) s.ucount[e] = a.unit_count[e];
-    for (int b = threadIdx.x; b < a.N; b += NW * 32) s.dih[b] = a.dih[b];
     // one call site of simulate() for both modes keeps the kernel compact;
     // the item survives the segment in shared memory, not in registers
     for (long long iter = 0;; ++iter) {
@@ -1070,13 +1081,18 @@ std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed)
     return per;
 }
 
-template <typename R> size_t chain_smem_bytes(const ChainGeometry &g, int NW, int max_units)
+// Shared memory of one replica CTA; `extras`: the schedule and dihedral
+// copies (taken only when the total stays within kChainSmemLimit).
+constexpr size_t kChainSmemLimit = 227 * 1024 - 256;
+template <typename R> size_t chain_smem_bytes(const ChainGeometry &g, int NW, int max_units, bool *extras = nullptr)
 {
     size_t b = sizeof(Vec4<R>) * g.n_tiles * 64 + sizeof(Vec2<R>) * g.n_tiles * 64 + sizeof(Vec4<R>) * g.Np * (1 + NW + 4) +
-               2 * sizeof(Vec4<R>) * ((3 * g.N + 3) / 4) + sizeof(Vec2<R>) * g.Np + 16;
+               2 * sizeof(Vec4<R>) * ((3 * g.N + 3) / 4) + sizeof(Vec2<R>) * g.Np + 32;
     if (kPacked<R>) b += sizeof(float4) * 3 * 64 * g.n_tiles;
-    b += sizeof(Vec4<R>) * g.N + sizeof(int4) * NW * max_units + sizeof(int) * NW;
-    return b;
+    const size_t x = sizeof(Vec4<R>) * g.N + sizeof(int4) * NW * max_units + sizeof(int) * NW;
+    const bool fit = b + x <= kChainSmemLimit;
+    if (extras) *extras = fit;
+    return fit ? b + x : b;
 }
 
 // Device copy of one chain in precision R.
@@ -1296,7 +1312,9 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     a.queue_start = L.queue_start;
     a.wait_ns = L.wait_ns > 0 ? L.wait_ns : kDefaultSegmentWaitNs;
     a.abort = L.abort;
-    const size_t smem = chain_smem_bytes<R>(m->geo, NW, m->max_units);
+    bool extras = false;
+    const size_t smem = chain_smem_bytes<R>(m->geo, NW, m->max_units, &extras);
+    a.static_in_smem = extras ? 1 : 0;
     void (*kern)(const ChainArgs<R>) = a.smd ? chain_kernel<R, NW, true> : chain_kernel<R, NW, false>;
     // The attribute is the kernel's upper limit, shared by every chain that
     // launches it: raise it to the device's opt-in maximum rather than to this

@@ -948,7 +948,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(run, world),
             "launch": {"warps_per_replica": warps, "ctas": "auto" if grid_ctas == 0 else grid_ctas,
-                       "segment_steps": seg_steps, "mode": "persistent"},
+                       "segment_steps": seg_steps, "mode": "persistent",
+                       "schedule_variant": pmf.pmf_chain_get_schedule(sysh, 0)},
             "e2e": {"value": e2e_value, "unit": "replica-steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * (chunks + 3),

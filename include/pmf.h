@@ -409,6 +409,11 @@ pmf_status pmf_chain_set_warps(pmf_system *sys, int chain, int warps);
  * the whole integrator state between segments).  Default: ctas = 0,
  * seg_steps = 1000.  Batched runs always use one CTA per replica. */
 pmf_status pmf_chain_set_grid(pmf_system *sys, int chain, int ctas, int seg_steps);
+/* Schedule cost model of chain `chain` (see pmf_chain_schedule_variant; the
+ * work schedule is rebuilt, results are bit-reproducible for a given
+ * variant and warp count).  PMF_EINVAL for a variant out of range. */
+pmf_status pmf_chain_set_schedule(pmf_system *sys, int chain, int variant);
+pmf_status pmf_chain_get_schedule(const pmf_system *sys, int chain, int *variant);
 /* The current warps per replica, ctas and seg_steps of chain `chain` (as set
  * by the calls above or chosen by pmf_chain_autotune); NULL outputs skipped. */
 pmf_status pmf_chain_get_launch(const pmf_system *sys, int chain, int *warps, int *ctas, int *seg_steps);
@@ -417,8 +422,10 @@ pmf_status pmf_chain_get_launch(const pmf_system *sys, int chain, int *warps, in
  * thousand steps so the persistent segments dominate the launch tail) for
  * each warp count and each of two persistent
  * launch shapes (ctas = 0 and ctas = one per replica, see
- * pmf_chain_set_grid) and keep the fastest; *best_warps and *best_ms (may
- * be NULL) report the warp count chosen and its probe time. */
+ * pmf_chain_set_grid), keep the fastest, then, for FP32, time each schedule
+ * cost model that gives a different schedule for that shape and keep the
+ * fastest; *best_warps and *best_ms (may be NULL) report the warp count
+ * chosen and its probe time. */
 pmf_status pmf_chain_autotune(pmf_system *sys, const double *lambda, int n_windows, const pmf_run_params *p,
                               int probe_steps, int *best_warps, double *best_ms);
 
@@ -577,6 +584,16 @@ pmf_status pmf_overlap(const double *mu, const double *log_var, int n, double *o
  * padded bead count).  PMF_EINVAL if capacity < 7 * records. */
 pmf_status pmf_chain_schedule(int N, int NW, int precision, int *out, size_t capacity, size_t *n_written,
                               int *padded);
+/* The same for cost model `variant` of the FP32 schedule (0 ..
+ * pmf_chain_schedule_variants() - 1; pmf_chain_schedule is variant 0).  The
+ * FP32 pieces are dealt longest-first to the least loaded warp under an
+ * estimated cost per ring step, per piece, per bonded pass and per noise
+ * pass; the variants weight these differently (the bonded and noise passes
+ * are latency-bound, so their true cost depends on the chain and the warp
+ * count).  FP64 schedules do not depend on the variant. */
+int pmf_chain_schedule_variants(void);
+pmf_status pmf_chain_schedule_variant(int N, int NW, int precision, int variant, int *out, size_t capacity,
+                                      size_t *n_written, int *padded);
 
 /* Measured FP32 throughput of this GPU, the peak of the integrator's
  * roofline (its nonbonded loop is bound by the FP32 FMA pipe): every SM

@@ -1548,6 +1548,24 @@ pmf_status pmf_chain_set_grid(pmf_system *sys, int chain, int ctas, int seg_step
     return PMF_OK;
 }
 
+pmf_status pmf_chain_set_schedule(pmf_system *sys, int chain, int variant)
+{
+    if (!sys || sys->model != PMF_MODEL_CHAIN || chain < 0 || chain >= (int)sys->chains.size())
+        return fail(PMF_EINVAL, "pmf_chain_set_schedule: not a chain system / bad chain index");
+    cudaError_t e = sys->chains[chain]->set_schedule_variant(variant);
+    if (e == cudaErrorInvalidValue) return fail(PMF_EINVAL, "pmf_chain_set_schedule: variant out of range");
+    if (e != cudaSuccess) return cuda_fail(e, "pmf_chain_set_schedule");
+    return PMF_OK;
+}
+
+pmf_status pmf_chain_get_schedule(const pmf_system *sys, int chain, int *variant)
+{
+    if (!sys || sys->model != PMF_MODEL_CHAIN || chain < 0 || chain >= (int)sys->chains.size() || !variant)
+        return fail(PMF_EINVAL, "pmf_chain_get_schedule: not a chain system / bad chain index / null output");
+    *variant = sys->chains[chain]->schedule_variant();
+    return PMF_OK;
+}
+
 pmf_status pmf_chain_get_launch(const pmf_system *sys, int chain, int *warps, int *ctas, int *seg_steps)
 {
     if (!sys || sys->model != PMF_MODEL_CHAIN || chain < 0 || chain >= (int)sys->chains.size())
@@ -1660,6 +1678,47 @@ pmf_status pmf_chain_autotune(pmf_system *sys, const double *lambda, int n_windo
     }
     if (pmf_status s = pmf_chain_set_warps(sys, p->chain, best)) return s;
     if (m.set_grid(best_grid, seg) != cudaSuccess) return fail(PMF_EINVAL, "pmf_chain_autotune: grid");
+    // then the cost models of the FP32 schedule for that shape: each one
+    // that gives a schedule not timed yet is probed the same way
+    int best_v = m.schedule_variant();
+    if (m.precision() != PMF_FP64) {
+        std::vector<std::vector<std::vector<UnitDesc>>> seen;
+        auto key = [&](int v) { return chain_schedule(m.n_beads(), best, true, v); };
+        auto same = [](const std::vector<std::vector<UnitDesc>> &a, const std::vector<std::vector<UnitDesc>> &b) {
+            if (a.size() != b.size()) return false;
+            for (size_t w = 0; w < a.size(); ++w) {
+                if (a[w].size() != b[w].size()) return false;
+                for (size_t q = 0; q < a[w].size(); ++q)
+                    if (std::memcmp(&a[w][q], &b[w][q], sizeof(UnitDesc)) != 0) return false;
+            }
+            return true;
+        };
+        seen.push_back(key(best_v));  // timed above
+        for (int v = 0; v < kSchedVariants; ++v) {
+            const auto sv = key(v);
+            bool dup = false;
+            for (const auto &o : seen) dup = dup || same(o, sv);
+            if (dup) continue;
+            seen.push_back(sv);
+            if (m.set_schedule_variant(v) != cudaSuccess) continue;
+            if (pmf_status s = pmf_run_launch(run)) return s;
+            if (pmf_status s = pmf_run_wait(run)) return s;
+            double t = 1e300;
+            for (int rep = 0; rep < 2; ++rep) {
+                const double before = timer.ms;
+                timer.start();
+                if (pmf_status s = pmf_run_launch(run)) return s;
+                CK(timer.stop(), "autotune timer");
+                if (pmf_status s = pmf_run_wait(run)) return s;
+                t = std::min(t, timer.ms - before);
+            }
+            if (t < best_t) {
+                best_t = t;
+                best_v = v;
+            }
+        }
+        if (m.set_schedule_variant(best_v) != cudaSuccess) return fail(PMF_EINVAL, "pmf_chain_autotune: schedule");
+    }
     if (best_warps) *best_warps = best;
     if (best_ms) *best_ms = best_t;
     return PMF_OK;
@@ -1760,9 +1819,18 @@ pmf_status pmf_philox(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint
 pmf_status pmf_chain_schedule(int N, int NW, int precision, int *out, size_t capacity, size_t *n_written,
                               int *padded)
 {
+    return pmf_chain_schedule_variant(N, NW, precision, 0, out, capacity, n_written, padded);
+}
+
+int pmf_chain_schedule_variants(void) { return kSchedVariants; }
+
+pmf_status pmf_chain_schedule_variant(int N, int NW, int precision, int variant, int *out, size_t capacity,
+                                      size_t *n_written, int *padded)
+{
     if (N < 4 || N > 1024 || (NW != 4 && NW != 5 && NW != 6 && NW != 8) || (precision != PMF_FP32 && precision != PMF_FP64))
         return fail(PMF_EINVAL, "pmf_chain_schedule: N in [4,1024], NW 4, 5, 6 or 8, precision FP32 or FP64");
-    const auto sched = chain_schedule(N, NW, precision == PMF_FP32);
+    if (variant < 0 || variant >= kSchedVariants) return fail(PMF_EINVAL, "pmf_chain_schedule: bad variant");
+    const auto sched = chain_schedule(N, NW, precision == PMF_FP32, variant);
     size_t n = 0;
     for (const auto &v : sched) n += v.size();
     if (n_written) *n_written = n;

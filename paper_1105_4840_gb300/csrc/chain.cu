@@ -1008,9 +1008,21 @@ ChainGeometry chain_geometry(int N)
 // piece.  Pieces are spread over the NW warps longest-first onto the least
 // loaded warp; the bonded owners and the noise generators load warps
 // 0..ceil(N/32)-1 first.
-std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed)
+// Cost models of the FP32 schedule's longest-first assignment, in units of
+// about one warp instruction: ring step, per-piece setup and flush, bonded
+// pass, noise pass.  Which model balances the warps best depends on the
+// chain and the warp count (the bonded and noise passes are latency-bound),
+// so pmf_chain_autotune times the distinct schedules they give.
+struct SchedWeights {
+    double step, piece, bonded, noise;
+};
+constexpr SchedWeights kSchedWeights[kSchedVariants] = {
+    {75, 60, 400, 250}, {75, 60, 250, 150}, {75, 60, 550, 350}, {75, 120, 400, 250}, {75, 60, 700, 400}, {75, 60, 400, 600}};
+
+std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed, int variant)
 {
     const ChainGeometry g = chain_geometry(N);
+    const SchedWeights sw = kSchedWeights[(variant >= 0 && variant < kSchedVariants) ? variant : 0];
     struct P {
         UnitDesc u;
         double cost;
@@ -1019,17 +1031,17 @@ std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed)
     for (int J = 0; packed && J < g.n_tiles; ++J) {
         // packed FP32 quad pieces: 4 steps x 4 pairs per lane for a W 32 ring half
         const int W = J == g.n_tiles - 1 ? g.w_last : 32;
-        if (W == 32) all.push_back(P{UnitDesc{J, -1, J, 23, 1, 0}, 4 * 75.0 + 60.0});
+        if (W == 32) all.push_back(P{UnitDesc{J, -1, J, 23, 1, 0}, 4 * sw.step + sw.piece});
         else if (W == 16) all.push_back(P{UnitDesc{J, -1, J, 8, 1, 0}, 8 * 30.0 + 20.0});
         else all.push_back(P{UnitDesc{J, -1, J, 10, 1, 0}, 4 * 30.0 + 20.0});
         for (int I = 0; I < J; ++I) {
             const int nr = J - I == 1 ? 1 : 0;
             if (W == 32) {
-                all.push_back(P{UnitDesc{I, -1, J, 26, nr, 0}, 8 * 75.0 + 60.0});
+                all.push_back(P{UnitDesc{I, -1, J, 26, nr, 0}, 8 * sw.step + sw.piece});
             } else if (W == 16) {
-                all.push_back(P{UnitDesc{I, -1, J, 24, nr, 0}, 4 * 75.0 + 70.0});
+                all.push_back(P{UnitDesc{I, -1, J, 24, nr, 0}, 4 * sw.step + sw.piece + 10.0});
             } else {
-                all.push_back(P{UnitDesc{I, -1, J, 25, nr, 0}, 2 * 75.0 + 80.0});
+                all.push_back(P{UnitDesc{I, -1, J, 25, nr, 0}, 2 * sw.step + sw.piece + 20.0});
             }
         }
     }
@@ -1065,10 +1077,10 @@ std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed)
         // nt-1 downwards
         const int nblk = (3 * N + 3) / 4 - early_noise_blocks(N, g.n_tiles, NW);
         for (int pass = 0; pass * nt < N; ++pass)
-            if (w * 32 < N - pass * nt) load[w] += 400.0;
+            if (w * 32 < N - pass * nt) load[w] += packed ? sw.bonded : 400.0;
         for (int pass = 0; pass * nt < nblk; ++pass) {
             const int lo = nt - (nblk - pass * nt);  // lowest thread with a block in this pass
-            if ((w + 1) * 32 > lo) load[w] += 250.0;
+            if ((w + 1) * 32 > lo) load[w] += packed ? sw.noise : 250.0;
         }
     }
     for (const P &p : all) {
@@ -1159,6 +1171,7 @@ struct ChainModel::Impl {
     int *unit_count = nullptr;
     int max_units = 0;
     unsigned generation = 0;
+    int variant = 0;         // cost model of the FP32 schedule (kSchedWeights)
     int grid_ctas = 0;       // persistent CTAs: 0 = auto, < 0 = one CTA per replica
     int seg_steps = 1000;    // steps per persistent work item
 };
@@ -1184,6 +1197,13 @@ cudaError_t ChainModel::init(const ChainHost &h, int precision)
 }
 
 int ChainModel::warps() const { return p->NW; }
+int ChainModel::schedule_variant() const { return p->variant; }
+cudaError_t ChainModel::set_schedule_variant(int v)
+{
+    if (v < 0 || v >= kSchedVariants) return cudaErrorInvalidValue;
+    p->variant = v;
+    return set_warps(p->NW);  // rebuilds the schedule (and bumps the generation)
+}
 
 cudaError_t ChainModel::set_grid(int ctas, int seg_steps)
 {
@@ -1208,7 +1228,7 @@ cudaError_t ChainModel::set_warps(int NW)
     p->units = nullptr;
     p->unit_count = nullptr;
     cudaError_t e;
-    const auto sched = chain_schedule(p->host.N, p->NW, p->precision != 1);
+    const auto sched = chain_schedule(p->host.N, p->NW, p->precision != 1, p->variant);
     int mx = 1;
     for (const auto &v : sched) mx = std::max<int>(mx, (int)v.size());
     std::vector<int4> flat((size_t)p->NW * mx, int4{0, 0, 0, 0});

@@ -41,8 +41,10 @@ ChainGeometry chain_geometry(int N);
 cudaError_t fp32_peak_launch(bool packed, int ctas, int iters, float *out, double *flops, cudaStream_t st);
 cudaError_t fp64_peak_launch(int ctas, int iters, double *out, double *flops, cudaStream_t st);
 int fp32_peak_threads();
-// packed: the FP32 quad pieces (kinds 8, 10, 21..25); else the scalar pieces (0..10)
-std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed);
+// packed: the FP32 quad pieces (kinds 8, 10, 21..26); else the scalar pieces
+// (0..10); variant: the cost model of the FP32 assignment (0 .. kSchedVariants-1)
+constexpr int kSchedVariants = 6;
+std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed, int variant = 0);
 
 // Everything one launch of a simulation kernel needs about the run.
 struct RunLaunch {
@@ -93,6 +95,9 @@ public:
     size_t smem_bytes() const;
     int warps() const;
     cudaError_t set_warps(int NW);  // 4, 5, 6 or 8 warps per replica (FP64: 4)
+    // cost model of the FP32 schedule (0 .. kSchedVariants-1); rebuilds it
+    cudaError_t set_schedule_variant(int v);
+    int schedule_variant() const;
     // Incremented by every set_warps (which reallocates the work schedule a
     // captured launch points at): a captured graph older than this is stale.
     unsigned generation() const;

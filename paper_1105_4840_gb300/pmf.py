@@ -152,6 +152,11 @@ def _load():
     L.pmf_chain_set_warps.argtypes = [P, C.c_int, C.c_int]
     L.pmf_chain_set_grid.argtypes = [P, C.c_int, C.c_int, C.c_int]
     L.pmf_chain_get_launch.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.pmf_chain_set_schedule.argtypes = [P, C.c_int, C.c_int]
+    L.pmf_chain_get_schedule.argtypes = [P, C.c_int, C.POINTER(C.c_int)]
+    L.pmf_chain_schedule_variants.restype = C.c_int
+    L.pmf_chain_schedule_variant.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_size_t,
+                                             C.POINTER(C.c_size_t), C.POINTER(C.c_int)]
     L.pmf_chain_autotune.argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.c_int, C.POINTER(C.c_int), _D]
     L.pmf_fp32_peak.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _D, _D]
     L.pmf_fp64_peak.argtypes = [C.c_int, C.c_int, C.c_int, _D, _D]
@@ -168,6 +173,7 @@ def _load():
                  "pmf_state_free_energy_from_samples", "pmf_free_energy_noalloc",
                  "pmf_mlp_create", "pmf_mlp_get_params", "pmf_mlp_predict", "pmf_mlp_gradient", "pmf_mlp_train",
                  "pmf_overlap", "pmf_run_adaptive", "pmf_chain_set_warps", "pmf_chain_set_grid", "pmf_chain_get_launch",
+                 "pmf_chain_set_schedule", "pmf_chain_get_schedule", "pmf_chain_schedule_variant",
                  "pmf_chain_autotune", "pmf_fp32_peak", "pmf_fp64_peak", "pmf_set_stream"):
         getattr(L, name).restype = C.c_int
     return L
@@ -501,15 +507,29 @@ def pmf_chain_forces(system: System, chain, pos, lam, k):
     return f
 
 
-def pmf_chain_schedule(N, NW=4, precision=PMF_FP32):
+def pmf_chain_schedule(N, NW=4, precision=PMF_FP32, variant=0):
     """Host schedule: int array [pieces, 7] (warp, I1, I2, J, kind, near1, near2), padded N."""
     n = C.c_size_t()
     pad = C.c_int()
-    lib.pmf_chain_schedule(N, NW, precision, None, 0, C.byref(n), C.byref(pad))
+    lib.pmf_chain_schedule_variant(N, NW, precision, variant, None, 0, C.byref(n), C.byref(pad))
     out = np.zeros(7 * n.value, dtype=np.int32)
-    _check(lib.pmf_chain_schedule(N, NW, precision, out.ctypes.data_as(C.POINTER(C.c_int)), out.size,
-                                  C.byref(n), C.byref(pad)), "pmf_chain_schedule")
+    _check(lib.pmf_chain_schedule_variant(N, NW, precision, variant, out.ctypes.data_as(C.POINTER(C.c_int)),
+                                          out.size, C.byref(n), C.byref(pad)), "pmf_chain_schedule_variant")
     return out.reshape(-1, 7), pad.value
+
+
+def pmf_chain_schedule_variants():
+    return lib.pmf_chain_schedule_variants()
+
+
+def pmf_chain_set_schedule(system: System, chain, variant):
+    _check(lib.pmf_chain_set_schedule(system.handle, chain, variant), "pmf_chain_set_schedule")
+
+
+def pmf_chain_get_schedule(system: System, chain=0):
+    v = C.c_int()
+    _check(lib.pmf_chain_get_schedule(system.handle, chain, C.byref(v)), "pmf_chain_get_schedule")
+    return v.value
 
 
 def pmf_free_energy_noalloc(x_dev, lambda_dev, n_windows, replicas, samples_per_window, k, kT, out_dev):

@@ -28,13 +28,17 @@ KINDS = {0: (32, 0, 8, 0, 0), 1: (32, 8, 8, 0, 0), 2: (32, 16, 8, 0, 0), 3: (32,
 SPLIT = {26}  # quad kinds whose ring steps jump by 10 halfway (t = 1..7, then 17..23)
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("NW", [4, 5, 6, 8])
 @pytest.mark.parametrize("N", NS)
-def test_ring_pieces_cover_pairs_once(N, NW, precision):
+def test_ring_pieces_cover_pairs_once(N, NW, precision, variant):
     from paper_1105_4840_gb300 import pmf
 
-    units, Np = pmf.pmf_chain_schedule(N, NW, precision)
+    if precision == 1 and variant:
+        pytest.skip("FP64 schedules do not depend on the cost model")
+    assert pmf.pmf_chain_schedule_variants() == 6
+    units, Np = pmf.pmf_chain_schedule(N, NW, precision, variant)
     n_tiles = (N + 31) // 32
     rem = N % 32
     w_last = 32 if rem == 0 else (8 if rem <= 8 else (16 if rem <= 16 else 32))

@@ -58,6 +58,23 @@ def test_forces_match_oracle(pmf, n):
     assert np.linalg.norm(f64 - fo) / np.linalg.norm(fo) <= 1e-12
 
 
+@pytest.mark.parametrize("variant", range(6))
+@pytest.mark.parametrize("n", [40, 104, 200])
+def test_forces_every_schedule_variant(pmf, n, variant):
+    """Every cost model of the FP32 schedule gives the oracle's forces (the
+    variants only move pieces between warps)."""
+    p = inputs.chain_params(n, 300 + n)
+    r = f32(inputs.chain_start(p, 9 + n) + np.random.default_rng(n + variant).normal(0, 0.005, (n, 3)))
+    sysh = pmf.pmf_create_system_chain([p], [r])
+    pmf.pmf_chain_set_schedule(sysh, 0, variant)
+    assert pmf.pmf_chain_get_schedule(sysh, 0) == variant
+    fg = pmf.pmf_chain_forces(sysh, 0, r, 1.7, 500.0)
+    fo = _clib.Chain(p).forces(r, 1.7, 500.0)
+    assert np.linalg.norm(fg - fo) / np.linalg.norm(fo) <= 1e-5
+    with pytest.raises(pmf.PmfError):
+        pmf.pmf_chain_set_schedule(sysh, 0, 6)
+
+
 def test_forces_without_nonbonded_and_angles(pmf):
     n = 37
     p = inputs.gaussian_chain_params(n, 80.0)

@@ -228,14 +228,18 @@ def run_reference(args, rank, world):
 
 def bench_batch(args, pmf, torch, stream):
     """Many uneven paths at once: 64 chains (40-400 beads), 21-61 windows
-    each, 16 replicas, one CUDA graph of concurrent per-chain launches, then
-    the per-chain FP64 reductions.  Single GPU, rank 0 only."""
+    each, 16 replicas, in the launch the batch autotuner picks (by default
+    one packed persistent launch per chunk for the whole batch, else a CUDA
+    graph of per-chain launches), then the per-chain FP64 reductions.
+    Single GPU, rank 0 only."""
     from paper_1105_4840_gb300 import inputs
 
     bw = inputs.batch_workload(n_steps=args.md_steps)
     run, params, lams = bw["run"], bw["params"], bw["lambdas"]
     sysh = pmf.pmf_create_system_chain(params, bw["starts"])
     rr = pmf.pmf_run_batch_prepare(sysh, list(enumerate(lams)), pmf.make_params(run))
+    tune_ms = rr.batch_autotune(min(run.n_steps, 1000))  # untimed setup
+    binfo = rr.batch_launch()
     R = run.replicas
     replica_steps = sum(l.size for l in lams) * R * run.n_steps
     flops = sum(flops_per_replica_step(p.n) * l.size * R * run.n_steps for p, l in zip(params, lams))
@@ -276,8 +280,10 @@ def bench_batch(args, pmf, torch, stream):
     peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
     sim = statistics.mean(sim_ms)
     achieved = flops / (sim / 1000.0) / 1e12
-    chunks = sum(math.ceil(run.n_steps / 100000) for _ in lams)
+    packed = binfo["mode"] == pmf.PMF_BATCH_PACKED
+    chunks = math.ceil(run.n_steps / 100000) if packed else sum(math.ceil(run.n_steps / 100000) for _ in lams)
     n = [p.n for p in params]
+    teams = {int(g): int(np.sum(binfo["teams"] == g)) for g in sorted(set(binfo["teams"].tolist()))}
     line = {"metric": "replica-steps/s", "value": replica_steps / (t_step / 1000.0), "unit": "replica-steps/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -285,12 +291,17 @@ def bench_batch(args, pmf, torch, stream):
             "config": {"workload": "batch64_uneven", "chains": len(params), "beads_min": min(n),
                        "beads_max": max(n), "beads_total": sum(n), "windows_total": sum(l.size for l in lams),
                        "replicas_per_window": R, "md_steps_per_window": run.n_steps,
-                       "launch": "one CUDA graph, one branch per chain", "l2": "256 MB flush between timed steps"},
+                       "launch": ("one packed persistent launch per 1e5-step chunk: %d CTAs of 16 warps, %d packs, "
+                                  "policy %d, chains per team size %s" % (binfo["ctas"], binfo["packs"],
+                                                                          binfo["policy"], teams))
+                       if packed else "one CUDA graph, one branch per chain",
+                       "autotune_probe_ms": tune_ms, "l2": "256 MB flush between timed steps"},
             "gpu_launches": args.steps * (chunks + 3 * len(lams)),
             "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                        "reasons": clk.get("reasons")},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "chain_kernel<float,4> (64 launches)",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "chain_pack_kernel<float>" if packed else "chain_kernel<float,4> (64 launches)",
                          "launch_ms": sim},
             "simulation_ms": sim, "reduction_ms": statistics.mean(red_ms)}
     print(json.dumps(line), flush=True)

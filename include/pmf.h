@@ -200,6 +200,37 @@ typedef struct {
 pmf_status pmf_run_batch_prepare(pmf_system *sys, const pmf_batch_item *items, int n_items,
                                  const pmf_run_params *p, pmf_run **out);
 
+/* Launch of a batched run (more than one item).  PMF_BATCH_PACKED (the
+ * default for FP32 chain batches): one persistent launch per 1e5-step chunk
+ * for the whole batch; each CTA (16 warps, one per SM) takes (segment, pack)
+ * work items from a device queue, a pack being up to 16 / G replicas of one
+ * item simulated side by side by teams of G warps (G = 2, 4, 8 or 16: the
+ * smallest allowed team size whose 16 / G replicas fit the CTA's shared
+ * memory, allowed being G >= 4 under packing policy `shift` = 0 (the
+ * default), G >= 2 under 1 and G >= 8 under 2; chains too long for a full
+ * CTA at any allowed size take the size that keeps the most warps busy,
+ * 16 if it fits); packs are
+ * queued costliest first, segment-major, and a pack's segment waits
+ * (bounded, as for single runs) for its previous one.  Every replica then
+ * runs the force schedule of G warps, so its trajectory is bit-identical to
+ * a per-item launch with G warps per replica.  PMF_BATCH_GRAPH: the
+ * per-item launches of pmf_run_batch_prepare's graph (FP64 batches always).
+ * PMF_EINVAL for a packed launch of an FP64 chain, a chain too long to fit,
+ * or a non-window run; PMF_ESTATE while the run is in flight.
+ * pmf_run_get_batch_launch reports the mode, shift, the number of packs and
+ * CTAs (0 in graph mode) and the team size of each item (teams[capacity],
+ * may be NULL; 0 in graph mode).
+ * pmf_run_batch_autotune times probe_steps steps of the whole batch (a
+ * warm-up and the best of two launches) in graph mode and in packed mode for
+ * every policy that gives different team sizes, and keeps the fastest; the
+ * probes overwrite the run's samples, so call it before the real launch.
+ * The paper runs one path at a time; packing many is this library's. */
+enum { PMF_BATCH_GRAPH = 0, PMF_BATCH_PACKED = 1 };
+pmf_status pmf_run_set_batch_launch(pmf_run *run, int mode, int shift);
+pmf_status pmf_run_get_batch_launch(pmf_run *run, int *mode, int *shift, int *packs, int *ctas, int *teams,
+                                    int capacity);
+pmf_status pmf_run_batch_autotune(pmf_run *run, int64_t probe_steps, double *best_ms);
+
 /* Constant-velocity pulling, the steered-MD comparator the paper measures
  * against (Sec. I, the work -v k int (x - lambda_1 - v t) dt): p->replicas
  * simulations start from x_o with the trap at lambda1, relax p->n_equil

@@ -43,6 +43,33 @@ pmf_status need_device()
     return PMF_OK;
 }
 
+// Device time of the work enqueued between start() and stop() on the
+// library stream, accumulated over calls.
+struct GpuTimer {
+    double ms = 0.0;
+    cudaEvent_t a = nullptr, b = nullptr;
+    GpuTimer()
+    {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+    ~GpuTimer()
+    {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+    void start() { cudaEventRecord(a, g_stream); }
+    cudaError_t stop()
+    {
+        cudaEventRecord(b, g_stream);
+        cudaError_t e = cudaEventSynchronize(b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        ms += t;
+        return e;
+    }
+};
+
 template <typename T> cudaError_t upload(T **d, const T *h, size_t n)
 {
     cudaError_t e = cudaMalloc(d, sizeof(T) * (n ? n : 1));
@@ -82,6 +109,11 @@ struct pmf_run {
     long long noise_steps = 0;
     double k = 0, kT = 1, dt = 0, gamma = 1, timeout_s = 0, segment_wait_s = 0;
     long long queue_start = 0;  // persistent chain launches: first work item (test hook)
+    // batched FP32 chain runs: one packed persistent launch per chunk (mode 1)
+    // or a graph of per-item launches (mode 0); team shift of the packing
+    int batch_mode = 0, pack_shift = 0;
+    PackPlan *pack = nullptr;
+    long long probe_steps = 0;  // > 0: launches stop after this many steps (autotuning probes)
     int *h_abort = nullptr;     // host-mapped stop flag polled by the persistent chain launches
     int *d_abort = nullptr;     //   (its device alias)
     unsigned long long seed = 0;
@@ -121,6 +153,7 @@ struct pmf_run {
         cudaFree(d_w);
         cudaFree(d_noise);
         if (h_abort) cudaFreeHost(h_abort);
+        pack_plan_destroy(pack);
         if (done) cudaEventDestroy(done);
         if (graph) cudaGraphExecDestroy(graph);
         if (cap) cudaStreamDestroy(cap);
@@ -325,6 +358,13 @@ static pmf_status prepare_items(pmf_system *sys, const pmf_batch_item *items, in
         CK(cudaMalloc(&run->d_queue, sizeof(unsigned long long)), "alloc queue");
         CK(cudaMalloc(&run->d_done, sizeof(int) * (size_t)n_windows * p->replicas), "alloc segment counters");
     }
+    if (n_items > 1 && sys->model == PMF_MODEL_CHAIN && !sequential) {
+        bool packable = true;
+        for (const RunItem &ri : run->items)
+            packable = packable && sys->chains[ri.chain]->precision() != PMF_FP64 &&
+                       pack_team_choice(*sys->chains[ri.chain], 0) > 0;
+        run->batch_mode = packable ? 1 : 0;
+    }
     const int n_branch = std::min(n_items, kMaxBranches);
     if (n_branch > 1) {
         run->fork_ev.assign(1 + n_branch, nullptr);
@@ -374,7 +414,8 @@ static double item_cost(const pmf_run *run, const RunItem &ri)
 // Enqueue every launch of one item on stream st: one launch per 1e5-step
 // chunk (chain model) over the item's nw x replicas CTAs; state carries over
 // between chunks in device memory.
-static cudaError_t enqueue_item(pmf_run *run, const RunItem &ri, cudaStream_t st)
+// The launch fields of one item of the run (one-CTA-per-replica form).
+static RunLaunch item_launch(const pmf_run *run, const RunItem &ri)
 {
     RunLaunch L;
     L.state = static_cast<char *>(run->d_state) + ri.state_off;
@@ -404,6 +445,16 @@ static cudaError_t enqueue_item(pmf_run *run, const RunItem &ri, cudaStream_t st
     L.kT = run->kT;
     L.dt = run->dt;
     L.gamma = run->gamma;
+    L.n_blocks = ri.nw * run->replicas;
+    return L;
+}
+
+// Enqueue every launch of one item on stream st: one launch per 1e5-step
+// chunk (chain model) over the item's nw x replicas CTAs; state carries over
+// between chunks in device memory.
+static cudaError_t enqueue_item(pmf_run *run, const RunItem &ri, cudaStream_t st)
+{
+    RunLaunch L = item_launch(run, ri);
     if (run->sequential) {
         // one launch: each replica visits every window, nsteps[0] steps each
         L.sequential = true;
@@ -419,6 +470,7 @@ static cudaError_t enqueue_item(pmf_run *run, const RunItem &ri, cudaStream_t st
     L.n_blocks = n_rep;
     long long max_steps = 0;
     for (int w = ri.w0; w < ri.w0 + ri.nw; ++w) max_steps = std::max(max_steps, run->nsteps[w]);
+    if (run->probe_steps > 0) max_steps = std::min(max_steps, run->probe_steps);
     const long long chunk = run->sys->model == PMF_MODEL_CHAIN ? 100000 : (1LL << 40);
     for (long long s0 = 0; s0 < max_steps; s0 += chunk) {
         L.step_begin = s0;
@@ -430,8 +482,28 @@ static cudaError_t enqueue_item(pmf_run *run, const RunItem &ri, cudaStream_t st
     return cudaSuccess;
 }
 
+// The packed launch plan of a batched FP32 chain run (team sizes from the
+// run's shift), built on first use.
+static cudaError_t ensure_pack(pmf_run *run)
+{
+    if (run->pack) return cudaSuccess;
+    std::vector<PackItemSpec> specs;
+    std::vector<int> teams;
+    int seg = 1000;
+    for (const RunItem &ri : run->items) {
+        ChainModel *m = run->sys->chains[ri.chain].get();
+        const int G = pack_team_choice(*m, run->pack_shift);
+        if (G < 0) return cudaErrorInvalidValue;
+        specs.push_back(PackItemSpec{m, item_launch(run, ri)});
+        teams.push_back(G);
+        seg = m->seg_steps();
+    }
+    return pack_plan_create(specs, teams, seg, &run->pack);
+}
+
 // Enqueue the run's whole launch sequence on stream st (the capture stream).
-// A batch forks into independent branches, one chain of launches per item,
+// A packed batch is one persistent launch per chunk.  Otherwise a batch
+// forks into independent branches, one chain of launches per item,
 // so that the items' kernels run concurrently and the block scheduler fills
 // the SMs; items are issued costliest first (longest CTAs start first) and
 // dealt to branches by least accumulated cost.
@@ -439,6 +511,15 @@ static cudaError_t enqueue_run(pmf_run *run, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(run->d_err, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
+    if (run->batch_mode == 1) {
+        // one packed persistent launch per 1e5-step chunk for the whole batch
+        if ((e = ensure_pack(run)) != cudaSuccess) return e;
+        long long max_steps = run->max_steps;
+        if (run->probe_steps > 0) max_steps = std::min(max_steps, run->probe_steps);
+        for (long long s0 = 0; s0 < max_steps; s0 += 100000)
+            if ((e = pack_plan_launch(run->pack, s0, std::min(max_steps, s0 + 100000), st)) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
     if (run->branch.empty()) {
         for (const RunItem &ri : run->items)
             if ((e = enqueue_item(run, ri, st)) != cudaSuccess) return e;
@@ -480,6 +561,10 @@ pmf_status pmf_run_launch(pmf_run *run)
         if (run->graph) {
             cudaGraphExecDestroy(run->graph);
             run->graph = nullptr;
+        }
+        if (run->pack && gen != run->graph_gen) {  // a schedule was rebuilt: so is the plan
+            pack_plan_destroy(run->pack);
+            run->pack = nullptr;
         }
         CK(cudaStreamBeginCapture(run->cap, cudaStreamCaptureModeRelaxed), "begin capture");
         cudaError_t e = enqueue_run(run, run->cap);
@@ -730,6 +815,124 @@ pmf_status pmf_free_energy_item(const pmf_run *run, int item, pmf_free_energy_re
     CK(cudaMemcpyAsync(h.data(), run->d_res, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g_stream), "copy");
     CK(cudaStreamSynchronize(g_stream), "sync");
     return copy_result(h.data(), nw, res);
+}
+
+pmf_status pmf_run_set_batch_launch(pmf_run *run, int mode, int shift)
+{
+    if (!run) return fail(PMF_EINVAL, "null run");
+    if (mode != PMF_BATCH_GRAPH && mode != PMF_BATCH_PACKED) return fail(PMF_EINVAL, "unknown batch mode");
+    if (shift < 0 || shift > 2) return fail(PMF_EINVAL, "packing policy must be 0, 1 or 2");
+    if (run->launched && !run->finished && cudaEventQuery(run->done) == cudaErrorNotReady)
+        return fail(PMF_ESTATE, "pmf_run_set_batch_launch: the run is still in flight");
+    if (mode == PMF_BATCH_PACKED) {
+        if (run->sys->model != PMF_MODEL_CHAIN || run->sequential || run->d_w || run->d_start)
+            return fail(PMF_EINVAL, "packed launches: chain window runs only");
+        for (const RunItem &ri : run->items) {
+            const ChainModel &m = *run->sys->chains[ri.chain];
+            if (m.precision() == PMF_FP64 || pack_team_choice(m, shift) < 0)
+                return fail(PMF_EINVAL, "packed launches: FP32 chains that fit a packed CTA only");
+        }
+    }
+    if (mode != run->batch_mode || shift != run->pack_shift) {
+        run->batch_mode = mode;
+        run->pack_shift = shift;
+        pack_plan_destroy(run->pack);
+        run->pack = nullptr;
+        if (run->graph) {
+            cudaGraphExecDestroy(run->graph);
+            run->graph = nullptr;
+        }
+    }
+    return PMF_OK;
+}
+
+pmf_status pmf_run_get_batch_launch(pmf_run *run, int *mode, int *shift, int *packs, int *ctas, int *teams,
+                                    int capacity)
+{
+    if (!run) return fail(PMF_EINVAL, "null run");
+    if (mode) *mode = run->batch_mode;
+    if (shift) *shift = run->pack_shift;
+    if (run->batch_mode == PMF_BATCH_PACKED) {
+        cudaError_t e = ensure_pack(run);
+        if (e != cudaSuccess) return cuda_fail(e, "pmf_run_get_batch_launch");
+    }
+    if (packs) *packs = pack_plan_packs(run->pack);
+    if (ctas) *ctas = pack_plan_grid(run->pack);
+    if (teams) {
+        if (capacity < (int)run->items.size()) return fail(PMF_EINVAL, "teams capacity smaller than the items");
+        for (size_t m = 0; m < run->items.size(); ++m)
+            teams[m] = run->batch_mode == PMF_BATCH_PACKED
+                           ? pack_team_choice(*run->sys->chains[run->items[m].chain], run->pack_shift)
+                           : 0;
+    }
+    return PMF_OK;
+}
+
+pmf_status pmf_run_batch_autotune(pmf_run *run, int64_t probe_steps, double *best_ms)
+{
+    if (!run || probe_steps < 1) return fail(PMF_EINVAL, "pmf_run_batch_autotune: bad argument");
+    if (run->items.size() < 2 || run->sys->model != PMF_MODEL_CHAIN)
+        return fail(PMF_EINVAL, "pmf_run_batch_autotune: batched chain runs only");
+    struct Cand {
+        int mode, shift;
+    };
+    std::vector<Cand> cands = {{PMF_BATCH_GRAPH, 0}};
+    for (int sh = 0; sh <= 2; ++sh) {
+        bool ok = true;
+        for (const RunItem &ri : run->items) {
+            const ChainModel &m = *run->sys->chains[ri.chain];
+            ok = ok && m.precision() != PMF_FP64 && pack_team_choice(m, sh) > 0;
+        }
+        if (!ok) continue;
+        bool dup = false;
+        for (const Cand &c : cands) {
+            if (c.mode != PMF_BATCH_PACKED) continue;
+            bool same = true;
+            for (const RunItem &ri : run->items) {
+                const ChainModel &m = *run->sys->chains[ri.chain];
+                same = same && pack_team_choice(m, sh) == pack_team_choice(m, c.shift);
+            }
+            dup = dup || same;
+        }
+        if (!dup) cands.push_back(Cand{PMF_BATCH_PACKED, sh});
+    }
+    const int mode0 = run->batch_mode, shift0 = run->pack_shift;
+    Cand best{mode0, shift0};
+    double best_t = 1e300;
+    GpuTimer timer;
+    run->probe_steps = probe_steps;
+    pmf_status st = PMF_OK;
+    for (const Cand &c : cands) {
+        if ((st = pmf_run_set_batch_launch(run, c.mode, c.shift)) != PMF_OK) break;
+        if ((st = pmf_run_launch(run)) != PMF_OK || (st = pmf_run_wait(run)) != PMF_OK) break;  // warm-up, capture
+        double t = 1e300;
+        for (int rep = 0; rep < 2 && st == PMF_OK; ++rep) {
+            const double before = timer.ms;
+            timer.start();
+            if ((st = pmf_run_launch(run)) != PMF_OK) break;
+            cudaError_t e = timer.stop();
+            if (e != cudaSuccess) { st = cuda_fail(e, "autotune timer"); break; }
+            if ((st = pmf_run_wait(run)) != PMF_OK) break;
+            t = std::min(t, timer.ms - before);
+        }
+        if (st != PMF_OK) break;
+        if (t < best_t) {
+            best_t = t;
+            best = c;
+        }
+    }
+    run->probe_steps = 0;
+    // the probes overwrote the run's samples and states: the next launch
+    // starts from x_o again; the captured probe launches are dropped
+    if (run->graph) {
+        cudaGraphExecDestroy(run->graph);
+        run->graph = nullptr;
+    }
+    run->finished = false;
+    if (st != PMF_OK) return st;
+    if (pmf_status s2 = pmf_run_set_batch_launch(run, best.mode, best.shift)) return s2;
+    if (best_ms) *best_ms = best_t;
+    return PMF_OK;
 }
 
 pmf_status pmf_run_set_queue_start(pmf_run *run, int64_t first_item)
@@ -1209,30 +1412,6 @@ pmf_status pmf_mlp_train(pmf_mlp *mlp, const pmf_run *run, int steps, int batch,
 
 namespace {
 
-struct GpuTimer {
-    double ms = 0.0;
-    cudaEvent_t a = nullptr, b = nullptr;
-    GpuTimer()
-    {
-        cudaEventCreate(&a);
-        cudaEventCreate(&b);
-    }
-    ~GpuTimer()
-    {
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
-    }
-    void start() { cudaEventRecord(a, g_stream); }
-    cudaError_t stop()
-    {
-        cudaEventRecord(b, g_stream);
-        cudaError_t e = cudaEventSynchronize(b);
-        float t = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
-        ms += t;
-        return e;
-    }
-};
 
 struct Window {
     double lam;

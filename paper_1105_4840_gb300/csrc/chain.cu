@@ -23,6 +23,7 @@
 //    thread owning their first bead, written to per-owner slots and gathered;
 //  * BAOAB with Philox4x32-10 noise, counter (bead, uid, step, 0).
 #include <algorithm>
+#include <memory>
 #include <cmath>
 #include <vector>
 
@@ -605,14 +606,25 @@ __device__ __forceinline__ void work_set(const Smem<float> &s, double W)
 __device__ __forceinline__ double work_get(const Smem<double> &s) { return s.vel[0].w; }
 __device__ __forceinline__ void work_set(const Smem<double> &s, double W) { s.vel[0].w = W; }
 
+// The threads that simulate one replica: a whole CTA (barrier 0) or a group
+// of warps of a packed CTA (named barrier `bar`, counted over its own
+// threads), with the thread's index inside the team.
+struct Team {
+    int tid, bar, nthreads;
+    __device__ __forceinline__ void sync() const
+    {
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
+    }
+};
+
 template <typename R, int NW, bool SMD>
 __device__ __forceinline__ void force_phase(const ChainArgs<R> &a, const Smem<R> &s, R lam, long long done,
                                             long long nequil, long long sample_base, bool first, uint32_t uid,
-                                            long long rec)
+                                            long long rec, const Team &tm)
 // rec: index of the x record taken at this force evaluation (the state after
 // `done` steps), or -1 (records are every `stride` steps after nequil).
 {
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = tm.tid, warp = tid >> 5, lane = tid & 31;
     gen_noise<R>(a, s, uid, done, first ? 0 : early_noise_blocks(a.N, a.n_tiles, NW), (3 * a.N + 3) >> 2,
                  NW * 32 - 1 - tid, NW * 32);
     for (int t = tid; t < a.N; t += NW * 32) {
@@ -680,10 +692,10 @@ template <> __device__ __forceinline__ Vec4<double> load_cg<double>(const Vec4<d
 // Returns false when the run was aborted (non-finite state).
 template <typename R, int NW, bool SMD>
 __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s, int rep, int w, int r,
-                                         long long s0, long long s1, long long origin)
+                                         long long s0, long long s1, long long origin, const Team &tm)
 {
     const uint32_t uid = a.uid_base + (uint32_t)rep;
-    const int tid = threadIdx.x;
+    const int tid = tm.tid;
     const R lam = (R)a.lambda[w];
     const R hdt = R(0.5) * a.dt;
     const R c1 = exp(-a.gamma * a.dt);
@@ -729,7 +741,7 @@ __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s
         const int t = e >> 6, i = e & 63, W = tile_width(t, a.n_tiles, a.w_last);
         if (i < 2 * W) s.eqd[e] = a.bead_eq[t * 32 + (i & (W - 1))];
     }
-    __syncthreads();
+    tm.sync();
     if constexpr (kPacked<R>) {
         for (int e = tid; e < a.n_tiles * 64; e += NW * 32) {
             const int t = e >> 6, i = e & 63, W = tile_width(t, a.n_tiles, a.w_last), D = pair_offset(W);
@@ -740,13 +752,13 @@ __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s
             s.posb[e] = make_float4(p0.z, p1.z, p0.w, p1.w);
             s.eqp[e] = make_float4(q0.x, q1.x, q0.y, q1.y);
         }
-        __syncthreads();
+        tm.sync();
     }
     const long long nequil = origin + a.nequil_w[w];  // equilibration counts from the window's first step
     const long long sample_base = a.off_w[w] + (long long)r * a.tw[w];
     force_phase<R, NW, SMD>(a, s, SMD ? (R)smd_lambda(a.lambda[0], a.smd_vdt, s0, nequil) : lam, s0, nequil,
-                            sample_base, true, uid, -1);
-    __syncthreads();
+                            sample_base, true, uid, -1, tm);
+    tm.sync();
     // record q is taken after nequil + (q + 1) stride steps: the first one
     // after s0 and the step it falls on (one division per segment instead
     // of a 64-bit remainder per step)
@@ -810,21 +822,21 @@ __device__ __forceinline__ bool simulate(const ChainArgs<R> &a, const Smem<R> &s
             gen_noise<R>(a, s, uid, step + 1, 0, early_noise_blocks(a.N, a.n_tiles, NW), tid - a.n_tiles * 32,
                          (NW - a.n_tiles) * 32);
         if (step >= s1) break;
-        __syncthreads();
+        tm.sync();
         long long rec = -1;
         if (step + 1 == rec_step) {
             rec = rec_q++;
             rec_step += a.stride;
         }
         force_phase<R, NW, SMD>(a, s, SMD ? (R)smd_lambda(a.lambda[0], a.smd_vdt, step + 1, nequil) : lam,
-                                step + 1, nequil, sample_base, false, uid, rec);
-        __syncthreads();
+                                step + 1, nequil, sample_base, false, uid, rec, tm);
+        tm.sync();
         if (*s.flag) {
             if (tid == 0) atomicOr(a.err, kErrNonFinite);
             return false;
         }
     }
-    __syncthreads();
+    tm.sync();
     for (int b = tid; b < a.Np; b += NW * 32) {
         const V3<R> p = pos_of(s, b);
         st[b] = Vec4<R>{p.x, p.y, p.z, R(0)};
@@ -884,6 +896,37 @@ __device__ long long next_item(const ChainArgs<R> &a)
     return (long long)it;
 }
 
+// Shared-memory views of one replica starting at p (the layout counted by
+// chain_smem_bytes); *tail receives the first byte after them.  The
+// schedule and the dihedral constants are read from the arguments' global
+// arrays unless the caller copies them behind.
+template <typename R, int NW>
+__device__ __forceinline__ Smem<R> carve_smem(unsigned char *p, const ChainArgs<R> &a, unsigned char **tail)
+{
+    Smem<R> s;
+    s.posd = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.n_tiles * 64;
+    s.eqd = reinterpret_cast<Vec2<R> *>(p); p += sizeof(Vec2<R>) * a.n_tiles * 64;
+    s.vel = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np;
+    s.fw = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * NW;
+    s.bslot = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * 4;
+    s.noise = reinterpret_cast<R *>(p); p += 2 * sizeof(Vec4<R>) * ((3 * a.N + 3) >> 2);
+    s.mass = reinterpret_cast<Vec2<R> *>(p); p += sizeof(Vec2<R>) * a.Np;
+    s.posa = nullptr;
+    s.posb = nullptr;
+    s.eqp = nullptr;
+    if constexpr (kPacked<R>) {
+        s.posa = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 64 * a.n_tiles;
+        s.posb = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 64 * a.n_tiles;
+        s.eqp = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 64 * a.n_tiles;
+    }
+    s.flag = reinterpret_cast<int *>(p); p += 32;  // keeps what follows 32-byte aligned
+    s.dih = a.dih;
+    s.units = a.units;
+    s.ucount = a.unit_count;
+    *tail = p;
+    return s;
+}
+
 template <typename R, int NW, bool SMD>
 __global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW == 5 ? 4 : (NW == 6 ? 3 : 2))) : 1)
     chain_kernel(const ChainArgs<R> a)
@@ -902,40 +945,20 @@ __global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW =
 {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ long long s_item;
-    Smem<R> s;
-    {
-        unsigned char *p = smem_raw;
-        s.posd = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.n_tiles * 64;
-        s.eqd = reinterpret_cast<Vec2<R> *>(p); p += sizeof(Vec2<R>) * a.n_tiles * 64;
-        s.vel = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np;
-        s.fw = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * NW;
-        s.bslot = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.Np * 4;
-        s.noise = reinterpret_cast<R *>(p); p += 2 * sizeof(Vec4<R>) * ((3 * a.N + 3) >> 2);
-        s.mass = reinterpret_cast<Vec2<R> *>(p); p += sizeof(Vec2<R>) * a.Np;
-        s.posa = nullptr;
-        s.posb = nullptr;
-        s.eqp = nullptr;
-        if constexpr (kPacked<R>) {
-            s.posa = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 64 * a.n_tiles;
-            s.posb = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 64 * a.n_tiles;
-            s.eqp = reinterpret_cast<float4 *>(p); p += sizeof(float4) * 64 * a.n_tiles;
-        }
-        s.flag = reinterpret_cast<int *>(p); p += 32;  // keeps what follows 32-byte aligned
-        s.dih = a.dih;
-        s.units = a.units;
-        s.ucount = a.unit_count;
-        if (a.static_in_smem) {
-            // static per-CTA data: the nonbonded schedule and the dihedral constants
-            Vec4<R> *dih = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.N;
-            int4 *units = reinterpret_cast<int4 *>(p); p += sizeof(int4) * NW * a.max_units;
-            int *ucount = reinterpret_cast<int *>(p);
-            for (int e = threadIdx.x; e < NW * a.max_units; e += NW * 32) units[e] = a.units[e];
-            for (int e = threadIdx.x; e < NW; e += NW * 32) ucount[e] = a.unit_count[e];
-            for (int b = threadIdx.x; b < a.N; b += NW * 32) dih[b] = a.dih[b];
-            s.dih = dih;
-            s.units = units;
-            s.ucount = ucount;
-        }
+    unsigned char *tail = nullptr;
+    Smem<R> s = carve_smem<R, NW>(smem_raw, a, &tail);
+    if (a.static_in_smem) {
+        // static per-CTA data: the nonbonded schedule and the dihedral constants
+        unsigned char *p = tail;
+        Vec4<R> *dih = reinterpret_cast<Vec4<R> *>(p); p += sizeof(Vec4<R>) * a.N;
+        int4 *units = reinterpret_cast<int4 *>(p); p += sizeof(int4) * NW * a.max_units;
+        int *ucount = reinterpret_cast<int *>(p);
+        for (int e = threadIdx.x; e < NW * a.max_units; e += NW * 32) units[e] = a.units[e];
+        for (int e = threadIdx.x; e < NW; e += NW * 32) ucount[e] = a.unit_count[e];
+        for (int b = threadIdx.x; b < a.N; b += NW * 32) dih[b] = a.dih[b];
+        s.dih = dih;
+        s.units = units;
+        s.ucount = ucount;
     }
     // one call site of simulate() for both modes keeps the kernel compact;
     // the item survives the segment in shared memory, not in registers
@@ -970,7 +993,8 @@ __global__ void __launch_bounds__(NW * 32, sizeof(R) == 4 ? (NW == 4 ? 5 : (NW =
             const long long nsteps = a.nsteps_w[w];
             s1 = s1 < nsteps ? s1 : nsteps;
         }
-        if ((s0 < s1 || a.force_out != nullptr) && !simulate<R, NW, SMD>(a, s, rep, w, r, s0, s1, origin)) return;
+        const Team tm{(int)threadIdx.x, 0, NW * 32};
+        if ((s0 < s1 || a.force_out != nullptr) && !simulate<R, NW, SMD>(a, s, rep, w, r, s0, s1, origin, tm)) return;
         if (a.persistent) {
             __syncthreads();  // the replica's state record is written
             if (threadIdx.x == 0) {
@@ -1096,11 +1120,17 @@ std::vector<std::vector<UnitDesc>> chain_schedule(int N, int NW, bool packed, in
 // Shared memory of one replica CTA; `extras`: the schedule and dihedral
 // copies (taken only when the total stays within kChainSmemLimit).
 constexpr size_t kChainSmemLimit = 227 * 1024 - 256;
-template <typename R> size_t chain_smem_bytes(const ChainGeometry &g, int NW, int max_units, bool *extras = nullptr)
+// Shared memory of one replica CTA without the static copies.
+template <typename R> size_t chain_base_smem_bytes(const ChainGeometry &g, int NW)
 {
     size_t b = sizeof(Vec4<R>) * g.n_tiles * 64 + sizeof(Vec2<R>) * g.n_tiles * 64 + sizeof(Vec4<R>) * g.Np * (1 + NW + 4) +
                2 * sizeof(Vec4<R>) * ((3 * g.N + 3) / 4) + sizeof(Vec2<R>) * g.Np + 32;
     if (kPacked<R>) b += sizeof(float4) * 3 * 64 * g.n_tiles;
+    return b;
+}
+template <typename R> size_t chain_smem_bytes(const ChainGeometry &g, int NW, int max_units, bool *extras = nullptr)
+{
+    const size_t b = chain_base_smem_bytes<R>(g, NW);
     const size_t x = sizeof(Vec4<R>) * g.N + sizeof(int4) * NW * max_units + sizeof(int) * NW;
     const bool fit = b + x <= kChainSmemLimit;
     if (extras) *extras = fit;
@@ -1174,6 +1204,13 @@ struct ChainModel::Impl {
     int variant = 0;         // cost model of the FP32 schedule (kSchedWeights)
     int grid_ctas = 0;       // persistent CTAs: 0 = auto, < 0 = one CTA per replica
     int seg_steps = 1000;    // steps per persistent work item
+    // schedules of the packed batch launch, per team size (warps per replica)
+    struct TeamSched {
+        int4 *units = nullptr;
+        int *count = nullptr;
+        int max_units = 0, variant = -1;
+    };
+    TeamSched team[17];
 };
 
 ChainModel::ChainModel() : p(new Impl) {}
@@ -1183,6 +1220,10 @@ ChainModel::~ChainModel()
     free_chain(p->dd);
     cudaFree(p->units);
     cudaFree(p->unit_count);
+    for (auto &t : p->team) {
+        cudaFree(t.units);
+        cudaFree(t.count);
+    }
     delete p;
 }
 
@@ -1263,8 +1304,9 @@ size_t ChainModel::state_bytes_per_replica() const
     return (p->precision == 1 ? sizeof(Vec4<double>) : sizeof(Vec4<float>)) * 2 * p->geo.Np;
 }
 
-template <typename R, int NW>
-static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, const RunLaunch &L, cudaStream_t st)
+template <typename R>
+static ChainArgs<R> fill_args(const ChainModel::Impl *m, const ChainDevice<R> &d, const RunLaunch &L,
+                              const int4 *units, const int *unit_count, int max_units)
 {
     ChainArgs<R> a{};
     a.bead_pos0 = d.pos0;
@@ -1278,8 +1320,8 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     a.nequil_w = L.nequil_w;
     a.off_w = L.off_w;
     a.tw = L.tw;
-    a.units = m->units;
-    a.unit_count = m->unit_count;
+    a.units = units;
+    a.unit_count = unit_count;
     a.err = L.err;
     a.force_out = L.force_out;
     a.start = L.start;
@@ -1290,7 +1332,7 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     a.n_tiles = m->geo.n_tiles;
     a.w_last = m->geo.w_last;
     a.replicas = L.replicas;
-    a.max_units = m->max_units;
+    a.max_units = max_units;
     a.stride = L.stride;
     a.uid_base = L.uid_base;
     a.seed = L.seed;
@@ -1314,7 +1356,6 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     a.n_rep = L.n_blocks;
     a.seg_steps = m->seg_steps;
     a.wout = L.wout;
-    if (L.smd_vdt != 0.0 && L.wout == nullptr) return cudaErrorInvalidValue;  // a pulled run records its work
     a.smd = L.wout != nullptr ? 1 : 0;
     a.smd_vdt = L.smd_vdt;
     a.persistent = 0;
@@ -1332,6 +1373,15 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     a.queue_start = L.queue_start;
     a.wait_ns = L.wait_ns > 0 ? L.wait_ns : kDefaultSegmentWaitNs;
     a.abort = L.abort;
+    a.static_in_smem = 0;
+    return a;
+}
+
+template <typename R, int NW>
+static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, const RunLaunch &L, cudaStream_t st)
+{
+    if (L.smd_vdt != 0.0 && L.wout == nullptr) return cudaErrorInvalidValue;  // a pulled run records its work
+    ChainArgs<R> a = fill_args<R>(m, d, L, m->units, m->unit_count, m->max_units);
     bool extras = false;
     const size_t smem = chain_smem_bytes<R>(m->geo, NW, m->max_units, &extras);
     a.static_in_smem = extras ? 1 : 0;
@@ -1383,6 +1433,310 @@ static cudaError_t launch_typed(ChainModel::Impl *m, const ChainDevice<R> &d, co
     kern<<<grid, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Packed persistent launch of a batch of chains (FP32)
+//
+// One CTA of kPackWarps warps per SM for the whole batch.  A pack is up to
+// kPackWarps / G replicas of one batch item (a chain and its windows), each
+// simulated by its own team of G warps with its own named barrier, side by
+// side in the CTA's shared memory; G and so the number of chains per CTA
+// follow from the chain's length (its shared memory per replica).  Work
+// items are (segment, pack), segment-major, packs costliest first; a CTA
+// takes the next item from a device queue, and the item's segment waits
+// (bounded) until the pack's previous segment has stored its state.  Every
+// replica runs exactly the steps, noise and force schedule (of team size G)
+// it would run in a one-CTA-per-replica launch of G warps, so results are
+// bit-identical to the per-chain launches with that warp count.
+// ---------------------------------------------------------------------------
+constexpr int kPackWarps = 16;
+
+struct PackDesc {
+    int item;       // batch item
+    int first_rep;  // first replica (item-local index w * replicas + r)
+    int count;      // replicas in the pack (<= kPackWarps / G)
+    int G;          // warps per replica
+    int slot;       // shared-memory bytes of one replica team
+    int pad[3];
+};
+
+template <typename R> struct PackArgs {
+    const ChainArgs<R> *items;  // per batch item: its chain's and windows' arguments, schedule of team size G
+    const PackDesc *packs;      // [n_packs], costliest first
+    unsigned long long *queue;  // work counter (zeroed before the launch)
+    int *done;                  // [n_packs] segments finished (zeroed)
+    int *err;
+    const volatile int *abort;
+    unsigned long long wait_ns;
+    long long n_items, step_begin, step_end;
+    int n_packs, seg_steps;
+};
+
+template <typename R> __device__ long long next_pack_item(const PackArgs<R> &P)
+{
+    auto stopped = [&] { return *((volatile int *)P.err) != 0 || (P.abort != nullptr && *P.abort != 0); };
+    if (stopped()) return -1;
+    const unsigned long long it = atomicAdd(P.queue, 1ull);
+    if (it >= (unsigned long long)P.n_items) return -1;
+    const int pk = (int)(it % (unsigned long long)P.n_packs);
+    const int seg = (int)(it / (unsigned long long)P.n_packs);
+    if (seg > 0 && ld_acquire(P.done + pk) < seg) {
+        const unsigned long long t0 = global_ns();
+        while (ld_acquire(P.done + pk) < seg) {
+            if (stopped()) return -1;
+            if (global_ns() - t0 > P.wait_ns) {
+                atomicOr(P.err, kErrTimeout);
+                return -1;
+            }
+            __nanosleep(500);
+        }
+    }
+    return (long long)it;
+}
+
+template <typename R, int G>
+__device__ __forceinline__ bool pack_team(const ChainArgs<R> &a, unsigned char *base, int rep, long long s0,
+                                          long long s1, const Team &tm)
+{
+    unsigned char *tail = nullptr;
+    const Smem<R> s = carve_smem<R, G>(base, a, &tail);
+    return simulate<R, G, false>(a, s, rep, rep / a.replicas, rep % a.replicas, s0, s1, 0, tm);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kPackWarps * 32, 1) chain_pack_kernel(const PackArgs<R> P)
+{
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    __shared__ long long s_item;
+    __shared__ ChainArgs<R> s_args;
+    __shared__ PackDesc s_pack;
+    static_assert(sizeof(ChainArgs<R>) % sizeof(int) == 0 && sizeof(PackDesc) % sizeof(int) == 0, "copied as words");
+    for (;;) {
+        if (threadIdx.x == 0) s_item = next_pack_item(P);
+        __syncthreads();
+        const long long it = s_item;
+        if (it < 0) return;
+        const int pk = (int)(it % P.n_packs);
+        const long long seg = it / P.n_packs;
+        {
+            const PackDesc *dp = P.packs + pk;
+            const int *src = reinterpret_cast<const int *>(P.items + dp->item);
+            for (int q = threadIdx.x; q < (int)(sizeof(ChainArgs<R>) / sizeof(int)); q += blockDim.x)
+                reinterpret_cast<int *>(&s_args)[q] = src[q];
+            for (int q = threadIdx.x; q < (int)(sizeof(PackDesc) / sizeof(int)); q += blockDim.x)
+                reinterpret_cast<int *>(&s_pack)[q] = reinterpret_cast<const int *>(dp)[q];
+        }
+        __syncthreads();
+        const ChainArgs<R> &a = s_args;
+        const int G = s_pack.G, g = (int)(threadIdx.x >> 5) / G;
+        if (g < s_pack.count) {
+            const int rep = s_pack.first_rep + g;
+            const long long s0 = P.step_begin + seg * P.seg_steps;
+            long long s1 = s0 + P.seg_steps < P.step_end ? s0 + P.seg_steps : P.step_end;
+            const long long nsteps = a.nsteps_w[rep / a.replicas];
+            s1 = s1 < nsteps ? s1 : nsteps;
+            const Team tm{(int)threadIdx.x - g * G * 32, 1 + g, G * 32};
+            unsigned char *base = smem_raw + (size_t)g * s_pack.slot;
+            if (s0 < s1) {
+                switch (G) {
+                case 2: pack_team<R, 2>(a, base, rep, s0, s1, tm); break;
+                case 4: pack_team<R, 4>(a, base, rep, s0, s1, tm); break;
+                case 8: pack_team<R, 8>(a, base, rep, s0, s1, tm); break;
+                default: pack_team<R, 16>(a, base, rep, s0, s1, tm); break;
+                }
+            }
+        }
+        __syncthreads();  // every team has stored its replica's state
+        if (*((volatile int *)P.err) != 0) return;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(P.done + pk, (int)seg + 1);
+        }
+    }
+}
+
+const int kPackTeams[4] = {2, 4, 8, 16};
+
+cudaError_t ChainModel::team_schedule(int G, const int4 **units, const int **count, int *max_units)
+{
+    if (G < 1 || G > 16 || p->precision == 1) return cudaErrorInvalidValue;
+    Impl::TeamSched &t = p->team[G];
+    if (t.units == nullptr || t.variant != p->variant) {
+        cudaFree(t.units);
+        cudaFree(t.count);
+        t = Impl::TeamSched{};
+        const auto sched = chain_schedule(p->host.N, G, true, p->variant);
+        int mx = 1;
+        for (const auto &v : sched) mx = std::max<int>(mx, (int)v.size());
+        std::vector<int4> flat((size_t)G * mx, int4{0, 0, 0, 0});
+        std::vector<int> cnt(G);
+        for (int w = 0; w < G; ++w) {
+            cnt[w] = (int)sched[w].size();
+            for (size_t q = 0; q < sched[w].size(); ++q) {
+                const UnitDesc &u = sched[w][q];
+                flat[(size_t)w * mx + q] = int4{u.I1, u.I2, u.J, u.kind | (u.near1 << 8) | (u.near2 << 9)};
+            }
+        }
+        cudaError_t e;
+        if ((e = cudaMalloc(&t.units, sizeof(int4) * flat.size())) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&t.count, sizeof(int) * cnt.size())) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(t.units, flat.data(), sizeof(int4) * flat.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemcpy(t.count, cnt.data(), sizeof(int) * cnt.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        t.max_units = mx;
+        t.variant = p->variant;
+    }
+    *units = t.units;
+    *count = t.count;
+    *max_units = t.max_units;
+    return cudaSuccess;
+}
+
+size_t ChainModel::team_slot_bytes(int G) const
+{
+    // one replica team without the static copies (the packed kernel reads
+    // those from global memory), rounded to keep the next team 32-byte aligned
+    return (chain_base_smem_bytes<float>(p->geo, G) + 31) & ~(size_t)31;
+}
+
+int pack_team_choice(const ChainModel &m, int policy)
+{
+    // the smallest allowed team size whose kPackWarps / G replicas fit the
+    // CTA's shared memory (policy 0: G >= 4, the single-chain default;
+    // 1: G >= 2; 2: G >= 8); chains too long for a full CTA at any allowed
+    // size take the size that keeps the most warps busy (16 if it fits)
+    const int lo = policy == 1 ? 0 : (policy == 2 ? 2 : 1);
+    for (int q = lo; q < 4; ++q) {
+        const int G = kPackTeams[q];
+        if ((kPackWarps / G) * m.team_slot_bytes(G) <= kChainSmemLimit) return G;
+    }
+    for (int q = 3; q >= lo; --q)
+        if (m.team_slot_bytes(kPackTeams[q]) <= kChainSmemLimit) return kPackTeams[q];
+    return -1;
+}
+
+struct PackPlan {
+    PackArgs<float> args{};
+    ChainArgs<float> *d_items = nullptr;
+    PackDesc *d_packs = nullptr;
+    unsigned long long *d_queue = nullptr;
+    int *d_done = nullptr;
+    size_t smem = 0;
+    int grid = 0;
+    std::vector<int> teams;  // team size per item
+    ~PackPlan()
+    {
+        cudaFree(d_items);
+        cudaFree(d_packs);
+        cudaFree(d_queue);
+        cudaFree(d_done);
+    }
+};
+
+cudaError_t pack_plan_create(const std::vector<PackItemSpec> &items, const std::vector<int> &teams, int seg_steps,
+                             PackPlan **out)
+{
+    *out = nullptr;
+    if (items.empty() || teams.size() != items.size() || seg_steps < 1) return cudaErrorInvalidValue;
+    auto plan = std::make_unique<PackPlan>();
+    std::vector<ChainArgs<float>> hargs(items.size());
+    struct PC {
+        PackDesc d;
+        double cost;
+    };
+    std::vector<PC> packs;
+    for (size_t m = 0; m < items.size(); ++m) {
+        ChainModel &cm = *items[m].model;
+        const int G = teams[m];
+        if (cm.precision() == 1 || G < 2 || G > 16 || (G & (G - 1))) return cudaErrorInvalidValue;
+        const int4 *units = nullptr;
+        const int *count = nullptr;
+        int mx = 0;
+        cudaError_t e = cm.team_schedule(G, &units, &count, &mx);
+        if (e != cudaSuccess) return e;
+        const RunLaunch &L = items[m].L;
+        if (L.sequential || L.wout != nullptr || L.force_out != nullptr || L.start != nullptr)
+            return cudaErrorInvalidValue;
+        hargs[m] = fill_args<float>(cm.p, cm.p->df, L, units, count, mx);
+        const size_t slot32 = cm.team_slot_bytes(G);
+        const int per = std::max(1, std::min(kPackWarps / G, (int)(kChainSmemLimit / slot32)));
+        if (slot32 > kChainSmemLimit) return cudaErrorInvalidValue;
+        const int n_rep = L.n_blocks;
+        const double N = cm.n_beads();
+        for (int q = 0; q * per < n_rep; ++q) {
+            PackDesc d{};
+            d.item = (int)m;
+            d.first_rep = q * per;
+            d.count = std::min(per, n_rep - q * per);
+            d.G = G;
+            d.slot = (int)slot32;
+            packs.push_back(PC{d, (N * N * 0.5 + 40.0 * N) * d.count});
+            plan->smem = std::max(plan->smem, slot32 * (size_t)per);
+        }
+    }
+    std::stable_sort(packs.begin(), packs.end(), [](const PC &x, const PC &y) { return x.cost > y.cost; });
+    std::vector<PackDesc> hp(packs.size());
+    for (size_t q = 0; q < packs.size(); ++q) hp[q] = packs[q].d;
+    cudaError_t e;
+    if ((e = cudaMalloc(&plan->d_items, sizeof(ChainArgs<float>) * hargs.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&plan->d_packs, sizeof(PackDesc) * hp.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&plan->d_queue, sizeof(unsigned long long))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&plan->d_done, sizeof(int) * hp.size())) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(plan->d_items, hargs.data(), sizeof(ChainArgs<float>) * hargs.size(), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaMemcpy(plan->d_packs, hp.data(), sizeof(PackDesc) * hp.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    int dev = 0, optin = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    cudaFuncAttributes fa{};
+    if ((e = cudaFuncGetAttributes(&fa, chain_pack_kernel<float>)) != cudaSuccess) return e;
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;
+    if (plan->smem > (size_t)dyn_max) return cudaErrorInvalidValue;
+    if ((e = cudaFuncSetAttribute(chain_pack_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max)) !=
+        cudaSuccess)
+        return e;
+    int occ = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chain_pack_kernel<float>, kPackWarps * 32,
+                                                             plan->smem)) != cudaSuccess)
+        return e;
+    plan->grid = (int)std::min<long long>((long long)std::max(occ, 1) * sms, (long long)hp.size());
+    PackArgs<float> &A = plan->args;
+    A.items = plan->d_items;
+    A.packs = plan->d_packs;
+    A.queue = plan->d_queue;
+    A.done = plan->d_done;
+    A.err = items[0].L.err;
+    A.abort = items[0].L.abort;
+    A.wait_ns = items[0].L.wait_ns > 0 ? items[0].L.wait_ns : kDefaultSegmentWaitNs;
+    A.n_packs = (int)hp.size();
+    A.seg_steps = seg_steps;
+    plan->teams = teams;
+    *out = plan.release();
+    return cudaSuccess;
+}
+
+cudaError_t pack_plan_launch(PackPlan *plan, long long step_begin, long long step_end, cudaStream_t st)
+{
+    if (!plan || step_end <= step_begin) return cudaErrorInvalidValue;
+    PackArgs<float> A = plan->args;
+    A.step_begin = step_begin;
+    A.step_end = step_end;
+    A.n_items = (long long)A.n_packs * ((step_end - step_begin + A.seg_steps - 1) / A.seg_steps);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(plan->d_queue, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(plan->d_done, 0, sizeof(int) * (size_t)A.n_packs, st)) != cudaSuccess) return e;
+    chain_pack_kernel<float><<<plan->grid, kPackWarps * 32, plan->smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+void pack_plan_destroy(PackPlan *plan) { delete plan; }
+int pack_plan_packs(const PackPlan *plan) { return plan ? plan->args.n_packs : 0; }
+int pack_plan_grid(const PackPlan *plan) { return plan ? plan->grid : 0; }
+size_t pack_plan_smem(const PackPlan *plan) { return plan ? plan->smem : 0; }
 
 cudaError_t ChainModel::launch(const RunLaunch &L, cudaStream_t st)
 {

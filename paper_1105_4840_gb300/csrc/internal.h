@@ -81,6 +81,7 @@ struct RunLaunch {
     double k = 0, kT = 1, dt = 0, gamma = 1;
 };
 
+struct PackPlan;
 class ChainModel {
 public:
     struct Impl;
@@ -107,10 +108,36 @@ public:
     cudaError_t set_grid(int ctas, int seg_steps);
     int grid_ctas() const;
     int seg_steps() const;
+    // FP32 packed batch launch: the schedule of team size G (cached on the
+    // device) and the shared memory of one replica team of that size
+    cudaError_t team_schedule(int G, const int4 **units, const int **count, int *max_units);
+    size_t team_slot_bytes(int G) const;
 
 private:
     Impl *p;
+    friend cudaError_t pack_plan_create(const std::vector<struct PackItemSpec> &, const std::vector<int> &, int,
+                                        PackPlan **);
 };
+
+// Packed persistent launch of a batch (chain.cu): one CTA of 16 warps per
+// SM runs packs of 16 / G replicas of one item, G warps each (teams), from a
+// device queue of (segment, pack) items.  L: the item's one-CTA-per-replica
+// launch fields (state, sample layout, lambda, uid base, n_blocks =
+// replicas of the item).
+struct PackItemSpec {
+    ChainModel *model;
+    RunLaunch L;
+};
+// team size of a chain under packing policy 0 (smallest G >= 4 whose 16 / G
+// replicas fit a CTA), 1 (G >= 2) or 2 (G >= 8); -1: does not fit
+int pack_team_choice(const ChainModel &m, int policy);
+cudaError_t pack_plan_create(const std::vector<PackItemSpec> &items, const std::vector<int> &teams, int seg_steps,
+                             PackPlan **out);
+cudaError_t pack_plan_launch(PackPlan *plan, long long step_begin, long long step_end, cudaStream_t st);
+void pack_plan_destroy(PackPlan *plan);
+int pack_plan_packs(const PackPlan *plan);
+int pack_plan_grid(const PackPlan *plan);
+size_t pack_plan_smem(const PackPlan *plan);
 
 struct Od1dParams {
     double a = 2.0, x0 = -1.0;

@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "PMF_OK", 1: "PMF_EINVAL", 2: "PMF_ENOMEM", 3: "PMF_ECUDA", 4
 PMF_MODEL_1D_DOUBLEWELL, PMF_MODEL_CHAIN = 0, 1
 PMF_FP32, PMF_FP64 = 0, 1
 PMF_WORK_PER_WINDOW_INCREMENT, PMF_WORK_PAIRED_CUMULATIVE = 0, 1
+PMF_BATCH_GRAPH, PMF_BATCH_PACKED = 0, 1
 
 _D = C.POINTER(C.c_double)
 _F = C.POINTER(C.c_float)
@@ -134,6 +135,10 @@ def _load():
                                      C.POINTER(C.c_size_t), C.POINTER(C.c_int)]
     L.pmf_run_reduce.argtypes = [P]
     L.pmf_run_set_queue_start.argtypes = [P, C.c_int64]
+    L.pmf_run_set_batch_launch.argtypes = [P, C.c_int, C.c_int]
+    L.pmf_run_get_batch_launch.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                           C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]
+    L.pmf_run_batch_autotune.argtypes = [P, C.c_int64, _D]
     L.pmf_state_free_energy.argtypes = [P, _D, _D, _D, C.c_int]
     L.pmf_state_free_energy_from_samples.argtypes = [C.c_void_p, C.c_int, _D, C.c_int, C.c_int, _I64, C.c_double,
                                                      C.c_double, _D, _D, _D]
@@ -169,7 +174,8 @@ def _load():
                  "pmf_run_wait", "pmf_get_run_info", "pmf_x_samples", "pmf_work_samples",
                  "pmf_free_energy", "pmf_free_energy_from_samples", "pmf_final_state",
                  "pmf_run_partials", "pmf_free_energy_from_partials", "pmf_work_distributions", "pmf_philox",
-                 "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_run_set_queue_start", "pmf_state_free_energy",
+                 "pmf_chain_forces", "pmf_chain_schedule", "pmf_run_reduce", "pmf_run_set_queue_start", "pmf_run_set_batch_launch",
+                 "pmf_run_get_batch_launch", "pmf_run_batch_autotune", "pmf_state_free_energy",
                  "pmf_state_free_energy_from_samples", "pmf_free_energy_noalloc",
                  "pmf_mlp_create", "pmf_mlp_get_params", "pmf_mlp_predict", "pmf_mlp_gradient", "pmf_mlp_train",
                  "pmf_overlap", "pmf_run_adaptive", "pmf_chain_set_warps", "pmf_chain_set_grid", "pmf_chain_get_launch",
@@ -289,6 +295,26 @@ class Run:
 
     def reduce(self):
         _check(lib.pmf_run_reduce(self.handle), "pmf_run_reduce")
+
+    def set_batch_launch(self, mode, policy=0):
+        """Batched runs: PMF_BATCH_PACKED (one persistent launch per chunk,
+        packing policy 0, 1 or 2) or PMF_BATCH_GRAPH (per-item launches)."""
+        _check(lib.pmf_run_set_batch_launch(self.handle, mode, policy), "pmf_run_set_batch_launch")
+
+    def batch_launch(self):
+        """dict(mode, policy, packs, ctas, teams[item]) of a batched run."""
+        n = len(getattr(self, "item_windows", [1]))
+        mode, pol, packs, ctas = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        teams = np.zeros(n, dtype=np.int32)
+        _check(lib.pmf_run_get_batch_launch(self.handle, C.byref(mode), C.byref(pol), C.byref(packs), C.byref(ctas),
+                                            teams.ctypes.data_as(C.POINTER(C.c_int)), n), "pmf_run_get_batch_launch")
+        return dict(mode=mode.value, policy=pol.value, packs=packs.value, ctas=ctas.value, teams=teams)
+
+    def batch_autotune(self, probe_steps=2000):
+        """Time graph and packed launches of the batch (probe_steps each) and keep the fastest."""
+        ms = C.c_double()
+        _check(lib.pmf_run_batch_autotune(self.handle, int(probe_steps), C.byref(ms)), "pmf_run_batch_autotune")
+        return ms.value
 
     def set_queue_start(self, first_item):
         """Test hook of the bounded device wait (pmf_run_set_queue_start)."""

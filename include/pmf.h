@@ -506,8 +506,10 @@ pmf_status pmf_mlp_train(pmf_mlp *mlp, const pmf_run *run, int steps, int batch,
  * Sec. III, Sec. IV B, Sec. V (iii)).  Each inserted window's replicas start
  * from the stored end states of its two neighbours whose final x is nearest
  * the predicted mean (replica r takes the candidate of rank r mod count) and
- * run with the same parameters and fresh replica uids.  The estimators of
- * pmf_free_energy are then evaluated on the merged non-uniform grid.
+ * run with the same parameters and fresh replica uids (with
+ * continue_windows, every current window continues in the same launch).
+ * The estimators of pmf_free_energy are then evaluated on the merged
+ * non-uniform grid.
  * gpu_seconds sums the device time of the simulations, the training, the
  * predictions, the seeding and the reductions (CUDA events on the library
  * stream).  Unless the caller set the chain's warp count
@@ -549,6 +551,13 @@ typedef struct {
     uint64_t mlp_seed;
     const float *mlp_init;      /* PMF_MLP_PARAMS initial weights (host)      */
     pmf_adaptive_trace *trace;  /* optional decision record (NULL: none)      */
+    int continue_windows;       /* 1: every round runs all windows in one launch:
+                                   the current ones continue for another n_steps
+                                   from their own replicas' end states (replica
+                                   r from replica r; fresh uids and velocities),
+                                   the inserted ones start seeded; the estimate
+                                   uses each window's latest run.  0: later
+                                   rounds run the inserted windows only        */
 } pmf_adaptive_params;
 
 typedef struct {

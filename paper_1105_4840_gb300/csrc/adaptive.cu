@@ -49,7 +49,9 @@ cudaError_t overlap_launch(const double *mu, const double *log_var, int n, doubl
 // Seeding: block q fills the start states of inserted window q.  Its M
 // candidates are stored end states (positions of M replicas of the two
 // neighbouring windows); replica r starts from the candidate of rank r mod M
-// when candidates are ordered by |x_final - target_q| (ties by index).
+// when candidates are ordered by |x_final - target_q| (ties by index).  A
+// NaN target keeps the candidates in their order (a window continued from
+// its own replicas' end states).
 template <typename R>
 __global__ void seed_kernel(const SeedJob *jobs, int N, int Np, int replicas, int max_cand, double *start,
                             int *choice, double *cand_x)
@@ -72,9 +74,12 @@ __global__ void seed_kernel(const SeedJob *jobs, int N, int Np, int replicas, in
         if (cand_x) cand_x[(size_t)blockIdx.x * max_cand + c] = x;
     }
     __syncthreads();
+    const bool keep_order = !(J.target == J.target);  // NaN target: candidate c to replica c (continuation)
     for (int c = threadIdx.x; c < M; c += blockDim.x) {
         int rank = 0;
-        for (int d = 0; d < M; ++d) rank += (dist[d] < dist[c]) || (dist[d] == dist[c] && d < c);
+        if (keep_order) rank = c;
+        else
+            for (int d = 0; d < M; ++d) rank += (dist[d] < dist[c]) || (dist[d] == dist[c] && d < c);
         for (int r = rank; r < replicas; r += M) {
             if (choice) choice[(size_t)blockIdx.x * replicas + r] = c;
             double *out = start + ((size_t)blockIdx.x * replicas + r) * (N > 0 ? 3 * (size_t)N : 1);

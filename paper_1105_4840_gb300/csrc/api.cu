@@ -1607,23 +1607,48 @@ pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, cons
             tr->rounds = round + 1;
         }
         if (pick.empty()) break;
-        // seed jobs: candidates = end states of the two neighbours
-        std::vector<SeedJob> jobs(pick.size());
-        std::vector<double> new_lam(pick.size());
+        // the next launch: the inserted windows, seeded from the end states of
+        // their two neighbours, and (with continuation) every current window,
+        // continued from its own replicas' end states, all in one run
+        struct Next {
+            double lam;
+            int inserted;  // 1: midpoint pick[idx]; 0: current window win[idx]
+            int idx;
+        };
+        std::vector<Next> next;
+        for (size_t q = 0; q < pick.size(); ++q) next.push_back(Next{mids[pick[q]], 1, (int)q});
+        if (ap->continue_windows)
+            for (size_t i = 0; i < win.size(); ++i) next.push_back(Next{win[i].lam, 0, (int)i});
+        std::sort(next.begin(), next.end(), [&](const Next &a, const Next &b) { return dir * a.lam < dir * b.lam; });
+        std::vector<SeedJob> jobs(next.size());
+        std::vector<double> new_lam(next.size());
+        std::vector<int> job_of_pick(pick.size(), 0);
         int max_cand = 0;
-        for (size_t q = 0; q < pick.size(); ++q) {
-            const int i = pick[q];
-            new_lam[q] = mids[i];
-            jobs[q].target = mu_mid[i];
+        for (size_t j = 0; j < next.size(); ++j) {
+            new_lam[j] = next[j].lam;
             int nc = 0;
-            for (int side = 0; side < 2; ++side) {
-                const Window &nb = win[i + side];
+            if (next[j].inserted) {
+                const int i = pick[next[j].idx];
+                job_of_pick[next[j].idx] = (int)j;
+                jobs[j].target = mu_mid[i];
+                for (int side = 0; side < 2; ++side) {
+                    const Window &nb = win[i + side];
+                    for (int r = 0; r < R && nc < kMaxSeedCandidates; ++r) {
+                        const size_t rep = (size_t)nb.w * nb.run->replicas + r;
+                        jobs[j].cand[nc++] = static_cast<const char *>(nb.run->d_state) + rep * state_stride;
+                    }
+                }
+            } else {
+                // continuation: replica r resumes from replica r's end state
+                // (a NaN target keeps the candidates in order)
+                const Window &cw = win[next[j].idx];
+                jobs[j].target = NAN;
                 for (int r = 0; r < R && nc < kMaxSeedCandidates; ++r) {
-                    const size_t rep = (size_t)nb.w * nb.run->replicas + r;
-                    jobs[q].cand[nc++] = static_cast<const char *>(nb.run->d_state) + rep * state_stride;
+                    const size_t rep = (size_t)cw.w * cw.run->replicas + r;
+                    jobs[j].cand[nc++] = static_cast<const char *>(cw.run->d_state) + rep * state_stride;
                 }
             }
-            jobs[q].n_cand = nc;
+            jobs[j].n_cand = nc;
             max_cand = std::max(max_cand, nc);
         }
         pmf_run_params p2 = *p;
@@ -1652,10 +1677,11 @@ pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, cons
             e = cudaMemcpy(hc.data(), d_choice, sizeof(int) * hc.size(), cudaMemcpyDeviceToHost);
             if (e == cudaSuccess) e = cudaMemcpy(hx.data(), d_cx, sizeof(double) * hx.size(), cudaMemcpyDeviceToHost);
             const size_t o = (size_t)round * tr->max_windows;
-            for (size_t q = 0; e == cudaSuccess && q < jobs.size(); ++q) {
-                for (int r = 0; r < R && tr->seed; ++r) tr->seed[(o + q) * R + r] = hc[q * R + r];
+            for (size_t q = 0; e == cudaSuccess && q < pick.size(); ++q) {
+                const size_t j = (size_t)job_of_pick[q];
+                for (int r = 0; r < R && tr->seed; ++r) tr->seed[(o + q) * R + r] = hc[j * R + r];
                 for (int c = 0; c < 2 * R && tr->cand_x; ++c)
-                    tr->cand_x[(o + q) * 2 * R + c] = c < jobs[q].n_cand ? hx[q * max_cand + c] : NAN;
+                    tr->cand_x[(o + q) * 2 * R + c] = c < jobs[j].n_cand ? hx[j * max_cand + c] : NAN;
             }
         }
         cudaFree(d_choice);
@@ -1666,10 +1692,11 @@ pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, cons
         if ((st = pmf_run_launch(rn)) != PMF_OK) return st;
         if ((st = pmf_run_wait(rn)) != PMF_OK) return st;
         CK(timer.stop(), "timer");
+        if (ap->continue_windows) win.clear();  // every window's latest samples are in rn
         for (size_t q = 0; q < new_lam.size(); ++q) win.push_back(Window{new_lam[q], rn, (int)q});
         uid_next += (uint32_t)(new_lam.size() * R);
         info->rounds = round + 1;
-        info->inserted += (int)new_lam.size();
+        info->inserted += (int)pick.size();
     }
     std::sort(win.begin(), win.end(), [&](const Window &a, const Window &b) { return dir * a.lam < dir * b.lam; });
     Merged m;

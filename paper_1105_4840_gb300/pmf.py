@@ -88,7 +88,7 @@ class AdaptiveTrace(C.Structure):
 class AdaptiveParams(C.Structure):
     _fields_ = [("overlap_threshold", C.c_double), ("max_rounds", C.c_int), ("max_windows", C.c_int),
                 ("mlp_steps", C.c_int), ("mlp_batch", C.c_int), ("mlp_lr", C.c_double), ("mlp_seed", C.c_uint64),
-                ("mlp_init", _F), ("trace", C.POINTER(AdaptiveTrace))]
+                ("mlp_init", _F), ("trace", C.POINTER(AdaptiveTrace)), ("continue_windows", C.c_int)]
 
 
 class AdaptiveInfo(C.Structure):
@@ -633,7 +633,7 @@ def pmf_overlap(mu, log_var):
 
 
 def pmf_run_adaptive(system: System, lambda0, params, mlp_init, threshold=0.3, max_rounds=3, max_windows=64,
-                     mlp_steps=300, mlp_batch=512, mlp_lr=3e-3, mlp_seed=1, trace=False):
+                     mlp_steps=300, mlp_batch=512, mlp_lr=3e-3, mlp_seed=1, trace=False, continue_windows=False):
     """Surrogate-guided window insertion; returns (info dict, free-energy dict).
     With trace=True the info dict also holds "trace": one dict per round with
     the decisions of pmf_adaptive_trace (windows, predictions, overlaps,
@@ -651,7 +651,7 @@ def pmf_run_adaptive(system: System, lambda0, params, mlp_init, threshold=0.3, m
         tr = AdaptiveTrace(max_rounds=Q, max_windows=W, replicas=R, rounds=0,
                            **{k: (a.ctypes.data_as(_IP) if a.dtype == np.int32 else _dp(a)) for k, a in ta.items()})
     ap = AdaptiveParams(threshold, max_rounds, max_windows, mlp_steps, mlp_batch, mlp_lr, mlp_seed,
-                        w.ctypes.data_as(_F), C.pointer(tr) if tr is not None else None)
+                        w.ctypes.data_as(_F), C.pointer(tr) if tr is not None else None, int(bool(continue_windows)))
     info = AdaptiveInfo()
     res_arrays = {f: np.zeros(max_windows) for f in RESULT_FIELDS}
     res = FreeEnergyResult(capacity=max_windows,

@@ -184,3 +184,50 @@ def test_adaptive_decisions_match_oracle_chain(pmf):
     assert meta["inserted"] > 0
     _check_decisions(meta, 0.3, 9, run.replicas)
     assert np.all(np.isfinite(res["dF_JE"]))
+
+
+def test_adaptive_decisions_with_continuation(pmf):
+    """With continue_windows every round runs all windows in one launch; the
+    decisions are still the oracle's."""
+    w = inputs.od1d_workload()
+    run = w["run"]
+    lam0 = np.linspace(-1.5, 1.5, 6)
+    sysh = pmf.pmf_create_system_1d(w["a"], w["x0"])
+    init = pmf.pack_mlp_params(sg.init_params(2))
+    meta, res = pmf.pmf_run_adaptive(sysh, lam0, pmf.make_params(run), init, threshold=0.5, max_rounds=3,
+                                     max_windows=64, mlp_steps=400, mlp_batch=512, mlp_lr=3e-3, mlp_seed=5,
+                                     trace=True, continue_windows=True)
+    assert meta["inserted"] > 0
+    _check_decisions(meta, 0.5, 64, run.replicas)
+    last = meta["trace"][-1]
+    np.testing.assert_array_equal(meta["lambdas"], np.sort(np.concatenate([last["lambdas"], last["inserted"]])))
+    exact = np.array([quad.od1d_free_energy(l, run.k) for l in meta["lambdas"]])
+    exact -= exact[0]
+    assert np.max(np.abs(res["dF_JE"] - exact)) < 0.1
+
+
+def test_continued_windows_resume_their_replicas(pmf):
+    """One round with continuation on the 1D model: each original window's
+    replica r runs again from replica r's end state of the coarse run (fresh
+    uids after the coarse run's), so its mean x equals the oracle's from that
+    start with those uids."""
+    w = inputs.od1d_workload()
+    run = w["run"]
+    run.n_steps, run.n_equil = 6000, 600
+    lam0 = np.linspace(-1.5, 1.5, 6)
+    R = run.replicas
+    sysh = pmf.pmf_create_system_1d(w["a"], w["x0"])
+    coarse = pmf.pmf_run_windows(sysh, lam0, pmf.make_params(run))
+    x_end = coarse.final_state()[0].reshape(lam0.size, R)
+    init = pmf.pack_mlp_params(sg.init_params(2))
+    meta, res = pmf.pmf_run_adaptive(sysh, lam0, pmf.make_params(run), init, threshold=0.5, max_rounds=1,
+                                     max_windows=64, mlp_steps=200, mlp_batch=256, mlp_lr=3e-3, mlp_seed=5,
+                                     trace=True, continue_windows=True)
+    lam = meta["lambdas"]
+    assert meta["inserted"] > 0 and lam.size == lam0.size + meta["inserted"]
+    for i, l in enumerate(lam0):
+        j = int(np.where(lam == l)[0][0])
+        xs = [_clib.od1d_run(w["a"], l, run.k, run.kT, run.gamma, run.dt, run.n_steps, run.n_equil, run.stride,
+                             run.seed, lam0.size * R + j * R + r, x_end[i, r])[0] for r in range(R)]
+        want = float(np.mean(np.concatenate(xs).astype(np.float32).astype(np.float64)))
+        assert abs(res["mean_x"][j] - want) < 1e-6, (i, res["mean_x"][j], want)

@@ -226,6 +226,19 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _nvtx(torch, name):
+    """Open (name) or close (None) an NVTX range around a timed region, so
+    that a profiler can select exactly its launches; a torch build without
+    NVTX markers skips them."""
+    try:
+        if name is None:
+            torch.cuda.nvtx.range_pop()
+        else:
+            torch.cuda.nvtx.range_push(name)
+    except (RuntimeError, AttributeError):
+        pass
+
+
 def bench_batch(args, pmf, torch, stream):
     """Many uneven paths at once: 64 chains (40-400 beads), 21-61 windows
     each, 16 replicas, in the launch the batch autotuner picks (by default
@@ -258,6 +271,7 @@ def bench_batch(args, pmf, torch, stream):
     clocks.start()
     time.sleep(0.5)
     sim_ms, red_ms = [], []
+    _nvtx(torch, "timed")
     for i in range(args.steps):
         flush.fill_(float(i))
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -271,6 +285,7 @@ def bench_batch(args, pmf, torch, stream):
         torch.cuda.synchronize()
         sim_ms.append(e[0].elapsed_time(e[1]))
         red_ms.append(e[1].elapsed_time(e[2]))
+    _nvtx(torch, None)
     clocks.stop()
     rr.wait()
     t_step = statistics.mean(a + b for a, b in zip(sim_ms, red_ms))
@@ -353,9 +368,14 @@ def bench_precision(args, pmf, torch):
 
 def bench_adaptive(args, pmf, torch):
     """GPU-seconds to a path free energy within 0.2 kT of a converged
-    reference, learned window placement (11 windows + surrogate-guided
-    insertion with seeding) against the uniform 21-window grid, over a ladder
-    of window relaxation times and several dynamics seeds."""
+    reference: the learned window placement (11 windows, surrogate-guided
+    insertion with seeding; with continuation every round runs all windows in
+    one launch, the current ones resuming from their replicas' end states)
+    against the uniform 21-window grid, over a ladder of window relaxation
+    times and several dynamics seeds.  The reference continues a dense
+    uniform grid for a fixed number of rounds (each round resumes every
+    replica from its end state with fresh noise) and averages its last
+    rounds; their drift per round is reported beside it."""
     from paper_1105_4840_gb300 import inputs
 
     out = {"workload": "chain_adaptive_vs_uniform", "criterion_kT": 0.2, "chains": []}
@@ -363,51 +383,90 @@ def bench_adaptive(args, pmf, torch):
         aw = inputs.adaptive_workload(n_beads)
         if args.tau_ps:
             aw["tau_ps"] = list(args.tau_ps)
+        if args.tau_uniform_extra is not None:
+            aw["tau_uniform_extra"] = list(args.tau_uniform_extra)
         if args.seeds:
             aw["seeds"] = list(args.seeds)
         p, start, run = aw["params"], aw["start"], aw["run"]
+        R = args.adaptive_replicas or run.replicas
         kT = run.kT
         sysh = pmf.pmf_create_system_chain([p], [start])
 
         def steps_of(tau_ps):
             return int(round(tau_ps / run.dt))
 
-        def timed_uniform(s, R, n_steps, seed, uid_base=0):
-            lam = np.linspace(aw["lo"], aw["hi"], s)
-            run.replicas, run.n_steps, run.n_equil, run.seed = R, n_steps, n_steps // 10, seed
-            pr = pmf.make_params(run, uid_base=uid_base)
-            rr = pmf.pmf_run_prepare(sysh, lam, pr)
+        def timed(fn):
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
             torch.cuda.synchronize()
             ev[0].record()
-            rr.launch()
-            rr.reduce()
+            res = fn()
             ev[1].record()
-            rr.wait()
             torch.cuda.synchronize()
-            res = rr.free_energy()
-            rr.close()
             return res, ev[0].elapsed_time(ev[1]) / 1000.0
 
-        # converged reference: dense uniform grid, many replicas, long windows
-        ref, ref_s = timed_uniform(aw["s_reference"], aw["replicas_reference"], args.reference_steps, 1000)
-        F_ref, se_ref = float(ref["dF_JE"][-1]), float(ref["se_JE"][-1])
+        def uniform(s, reps, n_steps, seed, uid_base=0, starts=None):
+            lam = np.linspace(aw["lo"], aw["hi"], s)
+            run.replicas, run.n_steps, run.n_equil, run.seed = reps, n_steps, n_steps // 10, seed
+            pr = pmf.make_params(run, uid_base=uid_base)
+            if starts is None:
+                rr = pmf.pmf_run_prepare(sysh, lam, pr)
+            else:
+                rr = pmf.pmf_run_prepare_seeded(sysh, lam, pr, starts)
+
+            def go():
+                rr.launch()
+                rr.reduce()
+                rr.wait()
+                return rr.free_energy()
+
+            res, gs = timed(go)
+            return res, gs, rr
+
+        # converged reference: a dense uniform grid continued round after
+        # round from its own end states; the mean of its last rounds, with
+        # the least-squares drift per round over those rounds
+        s_ref = aw["s_reference_cont"]
+        r_ref = args.reference_replicas or aw["replicas_reference"]
+        n_rounds = args.reference_rounds or aw["reference_rounds"]
+        n_avg = min(aw["reference_average"], n_rounds)
+        tau_ref = steps_of(aw["reference_round_ps"]) if args.reference_steps is None else args.reference_steps
+        drift, ref_gpu_s, rr = [], 0.0, None
+        for rnd in range(n_rounds):
+            pos = None
+            if rr is not None:
+                pos, _ = rr.final_state()
+                rr.close()
+            res, gs, rr = uniform(s_ref, r_ref, tau_ref, 1000 + rnd, uid_base=rnd * s_ref * r_ref, starts=pos)
+            ref_gpu_s += gs
+            drift.append({"round": rnd, "dF": float(res["dF_JE"][-1]), "se": float(res["se_JE"][-1]), "gpu_s": gs})
+        rr.close()
+        last = drift[-n_avg:]
+        F_ref = float(np.mean([d["dF"] for d in last]))
+        se_ref = math.sqrt(sum(d["se"] ** 2 for d in last)) / n_avg
+        slope = float(np.polyfit(np.arange(n_avg), [d["dF"] for d in last], 1)[0]) if n_avg > 1 else 0.0
         init = pmf.pack_mlp_params(inputs.mlp_init_params(2))
         rows = {"uniform": [], "adaptive": []}
         for seed in aw["seeds"]:
-            for tau in aw["tau_ps"]:
+            for tau in sorted(set(aw["tau_ps"]) | set(aw["tau_uniform_extra"])):
                 n_steps = steps_of(tau)
-                res, gs = timed_uniform(aw["s_uniform"], 32, n_steps, seed)
+                res, gs, rr = uniform(aw["s_uniform"], R, n_steps, seed)
+                rr.close()
                 rows["uniform"].append({"seed": seed, "tau_ps": tau, "gpu_s": gs, "windows": aw["s_uniform"],
                                         "dF": float(res["dF_JE"][-1]), "se": float(res["se_JE"][-1])})
-                run.replicas, run.n_steps, run.n_equil, run.seed = 32, n_steps, n_steps // 10, seed
+                if tau not in aw["tau_ps"]:
+                    continue
+                run.replicas, run.n_steps, run.n_equil, run.seed = R, n_steps, n_steps // 10, seed
                 lam0 = np.linspace(aw["lo"], aw["hi"], aw["s_adaptive0"])
                 meta, ares = pmf.pmf_run_adaptive(sysh, lam0, pmf.make_params(run), init, threshold=0.3,
-                                                  max_rounds=3, max_windows=81, mlp_steps=400, mlp_batch=512,
-                                                  mlp_lr=3e-3, mlp_seed=5 + seed)
+                                                  max_rounds=args.adaptive_rounds, max_windows=81, mlp_steps=400,
+                                                  mlp_batch=512, mlp_lr=3e-3, mlp_seed=5 + seed,
+                                                  continue_windows=not args.no_continuation,
+                                                  train_on_gap=not args.no_train_gate)
                 rows["adaptive"].append({"seed": seed, "tau_ps": tau, "gpu_s": meta["gpu_seconds"],
                                          "windows": meta["n_windows"], "rounds": meta["rounds"],
                                          "dF": float(ares["dF_JE"][-1]), "se": float(ares["se_JE"][-1])})
+                print(json.dumps({"seed": seed, "tau_ps": tau, "uniform": rows["uniform"][-1],
+                                  "adaptive": rows["adaptive"][-1]}), flush=True)
 
         def summary(rs):
             per_seed = []
@@ -416,19 +475,28 @@ def bench_adaptive(args, pmf, torch):
                 ok = [abs(r["dF"] - F_ref) < 0.2 * kT for r in ladder]
                 first = next((i for i in range(len(ladder)) if all(ok[i:])), None)
                 per_seed.append(None if first is None else {"tau_ps": ladder[first]["tau_ps"],
-                                                            "gpu_s": ladder[first]["gpu_s"],
-                                                            "ladder_gpu_s": sum(r["gpu_s"] for r in ladder[:first + 1])})
+                                                            "gpu_s": ladder[first]["gpu_s"]})
             got = [x["gpu_s"] for x in per_seed if x is not None]
-            return {"median_gpu_s": statistics.median(got) if got else None,
-                    "seeds_converged": len(got), "per_seed": per_seed}
+            by_tau = []
+            for tau in sorted({r["tau_ps"] for r in rs}):
+                d = np.array([(r["dF"] - F_ref) / kT for r in rs if r["tau_ps"] == tau])
+                g = [r["gpu_s"] for r in rs if r["tau_ps"] == tau]
+                se = [r["se"] / kT for r in rs if r["tau_ps"] == tau]
+                by_tau.append({"tau_ps": tau, "bias_kT": float(d.mean()), "sd_kT": float(d.std(ddof=1)) if d.size > 1 else 0.0,
+                               "mean_se_kT": float(np.mean(se)), "gpu_s": float(np.mean(g))})
+            return {"median_gpu_s": statistics.median(got) if got else None, "seeds_converged": len(got),
+                    "per_seed": per_seed, "by_tau": by_tau}
 
-        out["chains"].append({"beads": n_beads, "lambda": [aw["lo"], aw["hi"]], "kT": kT,
-                              "reference": {"dF_JE": F_ref, "se": se_ref, "gpu_s": ref_s,
-                                            "windows": aw["s_reference"], "replicas": aw["replicas_reference"],
-                                            "md_steps": args.reference_steps},
+        out["chains"].append({"beads": n_beads, "lambda": [aw["lo"], aw["hi"]], "kT": kT, "replicas": R,
+                              "adaptive_rounds": args.adaptive_rounds, "continuation": not args.no_continuation,
+                              "train_gate": not args.no_train_gate,
+                              "reference": {"dF_JE": F_ref, "se": se_ref, "drift_kT_per_round": slope / kT,
+                                            "averaged_rounds": n_avg, "gpu_s": ref_gpu_s, "windows": s_ref,
+                                            "replicas": r_ref, "md_steps_per_round": tau_ref, "rounds": drift},
                               "uniform": summary(rows["uniform"]), "adaptive": summary(rows["adaptive"]),
                               "runs": rows})
         sysh.close()
+        print(json.dumps(out["chains"][-1]), flush=True)
     print(json.dumps(out), flush=True)
 
 
@@ -483,9 +551,12 @@ def bench_adaptive_1d(args, pmf, torch):
                                     "windows": 21, "dF": float(res["dF_JE"][-1])})
             meta, ares = pmf.pmf_run_adaptive(sysh, np.linspace(lo, hi, 11), pmf.make_params(run), init,
                                               threshold=0.3, max_rounds=3, max_windows=81, mlp_steps=400,
-                                              mlp_batch=512, mlp_lr=3e-3, mlp_seed=5 + seed)
+                                              mlp_batch=512, mlp_lr=3e-3, mlp_seed=5 + seed,
+                                              continue_windows=not args.no_continuation,
+                                              train_on_gap=not args.no_train_gate)
             rows["adaptive"].append({"seed": seed, "steps": n_steps, "gpu_s": meta["gpu_seconds"],
-                                     "windows": meta["n_windows"], "dF": float(ares["dF_JE"][-1])})
+                                     "windows": meta["n_windows"], "rounds": meta["rounds"],
+                                     "dF": float(ares["dF_JE"][-1])})
 
     def summary(rs):
         per_seed = []
@@ -504,7 +575,8 @@ def bench_adaptive_1d(args, pmf, torch):
                 "per_seed": per_seed, "by_steps": by_steps}
 
     out = {"workload": "od1d_adaptive_vs_uniform", "criterion_kT": 0.2, "lambda": [lo, hi],
-           "exact_dF": exact, "replicas": 32, "dt": run.dt,
+           "exact_dF": exact, "replicas": 32, "dt": run.dt, "continuation": not args.no_continuation,
+           "train_gate": not args.no_train_gate,
            "uniform": summary(rows["uniform"]), "adaptive": summary(rows["adaptive"]), "runs": rows}
     sysh.close()
     print(json.dumps(out), flush=True)
@@ -768,7 +840,18 @@ def main():
     ap.add_argument("--mlp-steps", type=int, default=2000, help="Adam steps per timed launch (mlp)")
     ap.add_argument("--mlp-batch", type=int, default=512, help="mini-batch (mlp)")
     ap.add_argument("--adaptive-beads", type=int, nargs="+", default=[104, 200], help="chain lengths (adaptive)")
-    ap.add_argument("--reference-steps", type=int, default=1200000, help="steps per window of the reference")
+    ap.add_argument("--reference-steps", type=int, default=None,
+                    help="steps per window and round of the continued reference (adaptive; default 0.4 ns)")
+    ap.add_argument("--reference-rounds", type=int, default=None, help="rounds of the continued reference")
+    ap.add_argument("--reference-replicas", type=int, default=None, help="replicas per reference window")
+    ap.add_argument("--adaptive-replicas", type=int, default=None, help="replicas per window (adaptive)")
+    ap.add_argument("--tau-uniform-extra", type=float, nargs="*", default=None,
+                    help="relaxation times run by the uniform grid only (adaptive)")
+    ap.add_argument("--adaptive-rounds", type=int, default=2, help="insertion rounds of the learned placement")
+    ap.add_argument("--no-continuation", action="store_true",
+                    help="learned placement: later rounds run the inserted windows only")
+    ap.add_argument("--no-train-gate", action="store_true",
+                    help="learned placement: train in every round, even without a measured overlap gap")
     ap.add_argument("--tau-ps", type=float, nargs="+", default=None, help="relaxation-time ladder (adaptive)")
     ap.add_argument("--seeds", type=int, nargs="+", default=None, help="dynamics seeds (adaptive)")
     args = ap.parse_args()
@@ -888,10 +971,12 @@ def main():
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    _nvtx(torch, "timed")  # lets a profiler capture exactly the timed launches
     for i in range(args.steps):
         flush.fill_(float(i))  # L2 flush (256 MB) between timed steps, outside the events
         one_step(evs[i])
     torch.cuda.synchronize()
+    _nvtx(torch, None)
     if dist is not None:
         dist.barrier()
     clocks.stop()

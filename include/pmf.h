@@ -530,6 +530,11 @@ pmf_status pmf_mlp_train(pmf_mlp *mlp, const pmf_run *run, int steps, int batch,
  *                        neighbour, else replica c - replicas of the right);
  *   seed                 [q][max_windows][replicas]: the candidate each replica
  *                        of the inserted window started from.
+ * With train_on_gap, data_ovl [q][max_windows] holds the OVL of windows i
+ * and i + 1 from the measured moments of their samples, and trained[q] is 1
+ * if round q trained the surrogate (a gap was found), else 0 (the round
+ * stopped the protocol; its mu, log_var and ovl are NaN).  Without it
+ * trained[q] is 1 and data_ovl is not written.
  * rounds receives the number of rounds recorded (the last one may insert
  * nothing).  max_windows must be >= pmf_adaptive_params.max_windows and
  * replicas = pmf_run_params.replicas (<= 2048), else PMF_EINVAL. */
@@ -540,6 +545,8 @@ typedef struct {
     double *lambda, *mu, *log_var, *ovl;
     double *inserted, *target, *cand_x;
     int *seed;
+    double *data_ovl;
+    int *trained;
 } pmf_adaptive_trace;
 
 typedef struct {
@@ -558,6 +565,13 @@ typedef struct {
                                    the inserted ones start seeded; the estimate
                                    uses each window's latest run.  0: later
                                    rounds run the inserted windows only        */
+    int train_on_gap;           /* 1: a round first measures the Gaussian
+                                   moments (mean, population variance) of every
+                                   window's samples and the OVL of each
+                                   adjacent pair; if none is below
+                                   overlap_threshold the protocol stops there
+                                   without training (no window would need a
+                                   neighbour).  0: every round trains.         */
 } pmf_adaptive_params;
 
 typedef struct {

@@ -12,7 +12,10 @@ distribution as a Gaussian with mean <x_i> and variance gamma_i^2 kT / k
   * the overlap coefficient OVL = int min(p_1, p_2) of two Gaussians;
   * insertion of the midpoint of every adjacent pair whose predicted OVL is
     below a threshold, and seeding of each new window's replicas from the
-    stored end states whose final x is closest to the predicted mean.
+    stored end states whose final x is closest to the predicted mean;
+  * optionally, a gate before training: the measured moments of every
+    window's samples give the adjacent OVLs, and only a pair below the
+    threshold makes the round train and insert.
 
 Plain numpy, FP64, written to be read against the definitions above.
 """
@@ -129,6 +132,29 @@ def insert_windows(lambdas, mu, log_var, threshold):
         if gaussian_overlap(mu[i], sd[i], mu[i + 1], sd[i + 1]) < threshold:
             new.append(0.5 * (lam[i] + lam[i + 1]))
     return np.array(new)
+
+
+def window_moments(x_windows):
+    """Mean and population variance of each window's samples (all replicas
+    pooled): the measured Gaussian of the window."""
+    mu = np.array([math.fsum(np.ravel(x).tolist()) / np.size(x) for x in x_windows])
+    var = np.array([math.fsum(((np.ravel(x).astype(np.float64) - m) ** 2).tolist()) / np.size(x)
+                    for x, m in zip(x_windows, mu)])
+    return mu, var
+
+
+def measured_overlaps(x_windows):
+    """OVL of each adjacent pair of windows from their measured moments."""
+    mu, var = window_moments(x_windows)
+    sd = np.sqrt(var)
+    return np.array([gaussian_overlap(mu[i], sd[i], mu[i + 1], sd[i + 1]) for i in range(mu.size - 1)])
+
+
+def needs_training(x_windows, threshold) -> bool:
+    """The gate of a round: train the surrogate (and so consider inserting
+    windows) only if some adjacent pair's measured overlap is below the
+    threshold."""
+    return bool(np.any(measured_overlaps(x_windows) < threshold))
 
 
 def seed_order(final_x, target):

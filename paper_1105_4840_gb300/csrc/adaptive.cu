@@ -46,6 +46,56 @@ cudaError_t overlap_launch(const double *mu, const double *log_var, int n, doubl
     return cudaGetLastError();
 }
 
+// Measured Gaussian moments of the windows (the gate that decides whether a
+// round needs the surrogate at all): block w reads the replicas x T_w
+// samples of window w of a merged store and writes mu[w] = their mean and
+// log_var[w] = log of their population variance, both in FP64 (two passes:
+// the mean, then the mean squared deviation from it).
+constexpr int kMomentThreads = 256;
+
+__device__ double moment_block_sum(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();  // red may still be read by a previous call
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0;
+    for (int i = 0; i < kMomentThreads / 32; ++i) t += red[i];
+    return t;
+}
+
+__global__ void __launch_bounds__(kMomentThreads) moments_kernel(const float *x, const long long *off,
+                                                                 const long long *tw, int replicas, double *mu,
+                                                                 double *log_var)
+{
+    __shared__ double red[kMomentThreads / 32];
+    const int w = blockIdx.x;
+    const long long n = tw[w] * replicas;
+    const float *xw = x + off[w];
+    double s = 0;
+    for (long long i = threadIdx.x; i < n; i += kMomentThreads) s += (double)xw[i];
+    const double m = n > 0 ? moment_block_sum(s, red) / (double)n : NAN;
+    double q = 0;
+    for (long long i = threadIdx.x; i < n; i += kMomentThreads) {
+        const double d = (double)xw[i] - m;
+        q += d * d;
+    }
+    const double v = n > 0 ? moment_block_sum(q, red) / (double)n : NAN;
+    if (threadIdx.x == 0) {
+        mu[w] = m;
+        log_var[w] = log(v);
+    }
+}
+
+cudaError_t moments_launch(const float *x, const long long *off, const long long *tw, int replicas, int n,
+                           double *mu, double *log_var, cudaStream_t st)
+{
+    if (n < 1) return cudaSuccess;
+    moments_kernel<<<n, kMomentThreads, 0, st>>>(x, off, tw, replicas, mu, log_var);
+    return cudaGetLastError();
+}
+
 // Seeding: block q fills the start states of inserted window q.  Its M
 // candidates are stored end states (positions of M replicas of the two
 // neighbouring windows); replica r starts from the candidate of rank r mod M

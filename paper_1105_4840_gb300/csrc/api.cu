@@ -1540,6 +1540,51 @@ pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, cons
         Merged m;
         timer.start();
         CK(merge_windows(win, R, m), "merge samples");
+        const bool rec = tr && round < tr->max_rounds;
+        if (ap->train_on_gap) {
+            // the measured moments first: without a gap between neighbours no
+            // window would be inserted, so the round ends the protocol untrained
+            std::vector<double> dovl(m.n > 1 ? m.n - 1 : 0);
+            double *d_mu = nullptr, *d_lv = nullptr, *d_ovl = nullptr;
+            cudaError_t e = cudaMalloc(&d_mu, sizeof(double) * m.n);
+            if (e == cudaSuccess) e = cudaMalloc(&d_lv, sizeof(double) * m.n);
+            if (e == cudaSuccess) e = cudaMalloc(&d_ovl, sizeof(double) * std::max<size_t>(1, dovl.size()));
+            if (e == cudaSuccess) e = moments_launch(m.x, m.off, m.tw, R, m.n, d_mu, d_lv, g_stream);
+            if (e == cudaSuccess) e = overlap_launch(d_mu, d_lv, m.n, d_ovl, g_stream);
+            if (e == cudaSuccess && !dovl.empty())
+                e = cudaMemcpyAsync(dovl.data(), d_ovl, sizeof(double) * dovl.size(), cudaMemcpyDeviceToHost, g_stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+            cudaFree(d_mu);
+            cudaFree(d_lv);
+            cudaFree(d_ovl);
+            if (e != cudaSuccess) return cuda_fail(e, "measured overlap");
+            bool gap = false;
+            for (double v : dovl) gap = gap || v < ap->overlap_threshold;
+            if (rec) {
+                const size_t o = (size_t)round * tr->max_windows;
+                if (tr->data_ovl)
+                    for (size_t i = 0; i < dovl.size(); ++i) tr->data_ovl[o + i] = dovl[i];
+                if (tr->trained) tr->trained[round] = gap ? 1 : 0;
+            }
+            if (!gap) {
+                CK(timer.stop(), "timer");
+                if (rec) {
+                    const size_t o = (size_t)round * tr->max_windows;
+                    if (tr->n_windows) tr->n_windows[round] = m.n;
+                    if (tr->n_inserted) tr->n_inserted[round] = 0;
+                    for (int i = 0; i < m.n; ++i) {
+                        if (tr->lambda) tr->lambda[o + i] = win[i].lam;
+                        if (tr->mu) tr->mu[o + i] = NAN;
+                        if (tr->log_var) tr->log_var[o + i] = NAN;
+                        if (tr->ovl && i + 1 < m.n) tr->ovl[o + i] = NAN;
+                    }
+                    tr->rounds = round + 1;
+                }
+                break;
+            }
+        } else if (rec && tr->trained) {
+            tr->trained[round] = 1;
+        }
         MlpLaunch L;
         L.mode = 2;
         L.adam_t = mlp->t;
@@ -1589,7 +1634,6 @@ pmf_status pmf_run_adaptive(pmf_system *sys, const double *lambda0, int n0, cons
         std::vector<int> pick;
         for (size_t i = 0; i < mids.size(); ++i)
             if (ovl[i] < ap->overlap_threshold && (int)(win.size() + pick.size()) < ap->max_windows) pick.push_back((int)i);
-        const bool rec = tr && round < tr->max_rounds;
         if (rec) {
             const size_t o = (size_t)round * tr->max_windows;
             if (tr->n_windows) tr->n_windows[round] = m.n;

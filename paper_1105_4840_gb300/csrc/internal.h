@@ -215,6 +215,10 @@ cudaError_t mlp_launch(const MlpLaunch &L, cudaStream_t st);
 
 // Learned window placement (adaptive.cu)
 cudaError_t overlap_launch(const double *mu, const double *log_var, int n, double *ovl, cudaStream_t st);
+// mu[w], log_var[w]: mean and log population variance of window w's samples
+// x[off[w] .. off[w] + tw[w] * replicas) (a merged sample store)
+cudaError_t moments_launch(const float *x, const long long *off, const long long *tw, int replicas, int n,
+                           double *mu, double *log_var, cudaStream_t st);
 constexpr int kMaxSeedCandidates = 4096;
 struct SeedJob {
     double target;                         // predicted mean x at the inserted window

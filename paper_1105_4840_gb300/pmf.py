@@ -82,13 +82,15 @@ _IP = C.POINTER(C.c_int)
 class AdaptiveTrace(C.Structure):
     _fields_ = [("max_rounds", C.c_int), ("max_windows", C.c_int), ("replicas", C.c_int), ("rounds", C.c_int),
                 ("n_windows", _IP), ("n_inserted", _IP), ("lambda_", _D), ("mu", _D), ("log_var", _D),
-                ("ovl", _D), ("inserted", _D), ("target", _D), ("cand_x", _D), ("seed", _IP)]
+                ("ovl", _D), ("inserted", _D), ("target", _D), ("cand_x", _D), ("seed", _IP),
+                ("data_ovl", _D), ("trained", _IP)]
 
 
 class AdaptiveParams(C.Structure):
     _fields_ = [("overlap_threshold", C.c_double), ("max_rounds", C.c_int), ("max_windows", C.c_int),
                 ("mlp_steps", C.c_int), ("mlp_batch", C.c_int), ("mlp_lr", C.c_double), ("mlp_seed", C.c_uint64),
-                ("mlp_init", _F), ("trace", C.POINTER(AdaptiveTrace)), ("continue_windows", C.c_int)]
+                ("mlp_init", _F), ("trace", C.POINTER(AdaptiveTrace)), ("continue_windows", C.c_int),
+                ("train_on_gap", C.c_int)]
 
 
 class AdaptiveInfo(C.Structure):
@@ -633,12 +635,14 @@ def pmf_overlap(mu, log_var):
 
 
 def pmf_run_adaptive(system: System, lambda0, params, mlp_init, threshold=0.3, max_rounds=3, max_windows=64,
-                     mlp_steps=300, mlp_batch=512, mlp_lr=3e-3, mlp_seed=1, trace=False, continue_windows=False):
+                     mlp_steps=300, mlp_batch=512, mlp_lr=3e-3, mlp_seed=1, trace=False, continue_windows=False,
+                     train_on_gap=False):
     """Surrogate-guided window insertion; returns (info dict, free-energy dict).
     With trace=True the info dict also holds "trace": one dict per round with
     the decisions of pmf_adaptive_trace (windows, predictions, overlaps,
-    inserted centres, seeding targets, candidates' final x and the candidate
-    each replica of an inserted window started from)."""
+    inserted centres, seeding targets, candidates' final x, the candidate
+    each replica of an inserted window started from, whether the round
+    trained and, with train_on_gap, the measured overlaps)."""
     lam = np.ascontiguousarray(lambda0, dtype=np.float64)
     w = np.ascontiguousarray(mlp_init, dtype=np.float32)
     p, keep = params
@@ -647,11 +651,13 @@ def pmf_run_adaptive(system: System, lambda0, params, mlp_init, threshold=0.3, m
         R, Q, W = p.replicas, max(max_rounds, 1), max_windows
         ta = dict(n_windows=np.zeros(Q, np.int32), n_inserted=np.zeros(Q, np.int32), lambda_=np.zeros((Q, W)),
                   mu=np.zeros((Q, W)), log_var=np.zeros((Q, W)), ovl=np.zeros((Q, W)), inserted=np.zeros((Q, W)),
-                  target=np.zeros((Q, W)), cand_x=np.zeros((Q, W, 2 * R)), seed=np.zeros((Q, W, R), np.int32))
+                  target=np.zeros((Q, W)), cand_x=np.zeros((Q, W, 2 * R)), seed=np.zeros((Q, W, R), np.int32),
+                  data_ovl=np.full((Q, W), np.nan), trained=np.full(Q, -1, np.int32))
         tr = AdaptiveTrace(max_rounds=Q, max_windows=W, replicas=R, rounds=0,
                            **{k: (a.ctypes.data_as(_IP) if a.dtype == np.int32 else _dp(a)) for k, a in ta.items()})
     ap = AdaptiveParams(threshold, max_rounds, max_windows, mlp_steps, mlp_batch, mlp_lr, mlp_seed,
-                        w.ctypes.data_as(_F), C.pointer(tr) if tr is not None else None, int(bool(continue_windows)))
+                        w.ctypes.data_as(_F), C.pointer(tr) if tr is not None else None, int(bool(continue_windows)),
+                        int(bool(train_on_gap)))
     info = AdaptiveInfo()
     res_arrays = {f: np.zeros(max_windows) for f in RESULT_FIELDS}
     res = FreeEnergyResult(capacity=max_windows,
@@ -669,7 +675,8 @@ def pmf_run_adaptive(system: System, lambda0, params, mlp_init, threshold=0.3, m
             rounds.append(dict(lambdas=ta["lambda_"][q, :nw].copy(), mu=ta["mu"][q, :nw].copy(),
                                log_var=ta["log_var"][q, :nw].copy(), ovl=ta["ovl"][q, :max(nw - 1, 0)].copy(),
                                inserted=ta["inserted"][q, :ni].copy(), target=ta["target"][q, :ni].copy(),
-                               cand_x=ta["cand_x"][q, :ni].copy(), seed=ta["seed"][q, :ni].copy()))
+                               cand_x=ta["cand_x"][q, :ni].copy(), seed=ta["seed"][q, :ni].copy(),
+                               trained=int(ta["trained"][q]), data_ovl=ta["data_ovl"][q, :max(nw - 1, 0)].copy()))
         meta["trace"] = rounds
     return meta, out
 

@@ -135,6 +135,12 @@ def _check_decisions(meta, threshold, max_windows, R):
     assert len(tr) >= 1
     for q, rd in enumerate(tr):
         lam, mu, lv = rd["lambdas"], rd["mu"], rd["log_var"]
+        if rd["trained"] == 0:
+            # the gate closed: no measured gap, no training, nothing inserted
+            assert q == len(tr) - 1 and rd["inserted"].size == 0
+            assert np.all(rd["data_ovl"] >= threshold) and np.all(np.isnan(mu))
+            continue
+        assert rd["trained"] == 1
         sd = np.exp(0.5 * lv)
         ovl_o = np.array([sg.gaussian_overlap(mu[i], sd[i], mu[i + 1], sd[i + 1]) for i in range(lam.size - 1)])
         np.testing.assert_allclose(rd["ovl"], ovl_o, rtol=0, atol=1e-10)
@@ -231,3 +237,66 @@ def test_continued_windows_resume_their_replicas(pmf):
                              run.seed, lam0.size * R + j * R + r, x_end[i, r])[0] for r in range(R)]
         want = float(np.mean(np.concatenate(xs).astype(np.float32).astype(np.float64)))
         assert abs(res["mean_x"][j] - want) < 1e-6, (i, res["mean_x"][j], want)
+
+
+def _uniform_samples(pmf, sysh, lam0, run):
+    """The coarse run a protocol starts with (uids from 0), run on its own."""
+    return pmf.pmf_run_windows(sysh, lam0, pmf.make_params(run)).x_samples()
+
+
+def test_gate_skips_training_without_a_gap(pmf):
+    """11 windows on the 1D well (spacing 0.3): every measured neighbour
+    overlap is above 0.3, so the gated protocol stops in round 0 without
+    training; its measured overlaps are the oracle's from the same samples,
+    and its final profile is the coarse run's."""
+    w = inputs.od1d_workload()
+    run = w["run"]
+    lam0 = np.linspace(-1.5, 1.5, 11)
+    sysh = pmf.pmf_create_system_1d(w["a"], w["x0"])
+    init = pmf.pack_mlp_params(sg.init_params(2))
+    xs = _uniform_samples(pmf, sysh, lam0, run)
+    want_ovl = sg.measured_overlaps(xs)
+    assert not sg.needs_training(xs, 0.3)
+    meta, res = pmf.pmf_run_adaptive(sysh, lam0, pmf.make_params(run), init, threshold=0.3, max_rounds=3,
+                                     max_windows=64, mlp_steps=400, mlp_batch=512, mlp_lr=3e-3, mlp_seed=5,
+                                     trace=True, train_on_gap=True)
+    tr = meta["trace"]
+    assert len(tr) == 1 and tr[0]["trained"] == 0 and meta["inserted"] == 0 and meta["rounds"] == 0
+    np.testing.assert_allclose(tr[0]["data_ovl"], want_ovl, rtol=0, atol=1e-10)
+    plain = pmf.pmf_run_windows(sysh, lam0, pmf.make_params(run)).free_energy()
+    np.testing.assert_allclose(res["dF_JE"], plain["dF_JE"], rtol=1e-12, atol=1e-12)
+    _check_decisions(meta, 0.3, 64, run.replicas)
+    # ungated, the same protocol trains in round 0 and takes longer
+    meta2, _ = pmf.pmf_run_adaptive(sysh, lam0, pmf.make_params(run), init, threshold=0.3, max_rounds=3,
+                                    max_windows=64, mlp_steps=400, mlp_batch=512, mlp_lr=3e-3, mlp_seed=5,
+                                    trace=True)
+    assert meta2["trace"][0]["trained"] == 1
+    assert meta["gpu_seconds"] < meta2["gpu_seconds"]
+
+
+def test_gate_opens_on_a_gap_and_decides_as_ungated(pmf):
+    """6 windows (spacing 0.6) with threshold 0.5: the measured overlaps
+    (the oracle's, from the coarse run's samples) show a gap, so round 0
+    trains and inserts exactly what the ungated protocol inserts; every
+    later round either trains on a measured gap or ends the protocol."""
+    w = inputs.od1d_workload()
+    run = w["run"]
+    lam0 = np.linspace(-1.5, 1.5, 6)
+    sysh = pmf.pmf_create_system_1d(w["a"], w["x0"])
+    init = pmf.pack_mlp_params(sg.init_params(2))
+    xs = _uniform_samples(pmf, sysh, lam0, run)
+    assert sg.needs_training(xs, 0.5)
+    kw = dict(threshold=0.5, max_rounds=4, max_windows=64, mlp_steps=400, mlp_batch=512, mlp_lr=3e-3, mlp_seed=5,
+              trace=True, continue_windows=True)
+    meta, res = pmf.pmf_run_adaptive(sysh, lam0, pmf.make_params(run), init, train_on_gap=True, **kw)
+    ref, _ = pmf.pmf_run_adaptive(sysh, lam0, pmf.make_params(run), init, **kw)
+    tr = meta["trace"]
+    assert tr[0]["trained"] == 1
+    np.testing.assert_allclose(tr[0]["data_ovl"], sg.measured_overlaps(xs), rtol=0, atol=1e-10)
+    for key in ("mu", "log_var", "ovl", "inserted", "target", "seed"):
+        np.testing.assert_array_equal(tr[0][key], ref["trace"][0][key])
+    _check_decisions(meta, 0.5, 64, run.replicas)
+    for rd in tr:
+        assert rd["trained"] == int(np.any(rd["data_ovl"] < 0.5))
+    exact = np.array([quad.od1d_free_energy(l, run.k) for l in meta["lambdas"]])
+    assert np.max(np.abs(res["dF_JE"] - (exact - exact[0]))) < 0.1

@@ -150,3 +150,25 @@ def test_training_recovers_a_linear_gaussian_model():
     ln, xn = sg.normalise(lam_all, store, c, h)
     loss = sg.nll(sg.forward(p, ln)["out"], xn)
     assert abs(loss - 0.5 * (math.log((sig / h) ** 2) + 1.0)) < 0.03
+
+
+def test_gate_on_measured_overlaps():
+    """Samples mu +- sigma (equal counts) have mean mu and population
+    variance sigma^2 exactly, so the measured OVL of two such windows is
+    the equal-width closed form 2 Phi(-|d| / (2 sigma)); the gate opens
+    exactly when that value is below the threshold."""
+    from scipy.stats import norm
+
+    sigma = 0.25
+    def win(mu):
+        return np.array([[mu - sigma, mu + sigma], [mu + sigma, mu - sigma]])
+
+    for d in (0.1, 0.5, 1.0):
+        xw = [win(0.0), win(d), win(2 * d)]
+        mu, var = sg.window_moments(xw)
+        np.testing.assert_allclose(mu, [0.0, d, 2 * d], atol=1e-15)
+        np.testing.assert_allclose(var, sigma ** 2, rtol=1e-14)
+        want = 2.0 * norm.cdf(-d / (2.0 * sigma))
+        np.testing.assert_allclose(sg.measured_overlaps(xw), [want, want], rtol=1e-12)
+        for thr in (want - 1e-6, want + 1e-6):
+            assert sg.needs_training(xw, thr) == (want < thr)

@@ -444,6 +444,8 @@ def bench_adaptive(args, pmf, torch):
         F_ref = float(np.mean([d["dF"] for d in last]))
         se_ref = math.sqrt(sum(d["se"] ** 2 for d in last)) / n_avg
         slope = float(np.polyfit(np.arange(n_avg), [d["dF"] for d in last], 1)[0]) if n_avg > 1 else 0.0
+        print(json.dumps({"beads": n_beads, "reference": {"dF_JE": F_ref, "se": se_ref, "drift_kT_per_round": slope / kT,
+                                                          "rounds": drift}}), flush=True)
         init = pmf.pack_mlp_params(inputs.mlp_init_params(2))
         rows = {"uniform": [], "adaptive": []}
         for seed in aw["seeds"]:
@@ -454,6 +456,7 @@ def bench_adaptive(args, pmf, torch):
                 rows["uniform"].append({"seed": seed, "tau_ps": tau, "gpu_s": gs, "windows": aw["s_uniform"],
                                         "dF": float(res["dF_JE"][-1]), "se": float(res["se_JE"][-1])})
                 if tau not in aw["tau_ps"]:
+                    print(json.dumps({"seed": seed, "tau_ps": tau, "uniform": rows["uniform"][-1]}), flush=True)
                     continue
                 run.replicas, run.n_steps, run.n_equil, run.seed = R, n_steps, n_steps // 10, seed
                 lam0 = np.linspace(aw["lo"], aw["hi"], aw["s_adaptive0"])
@@ -585,7 +588,8 @@ def bench_adaptive_1d(args, pmf, torch):
 def bench_mlp(args, pmf, torch, stream):
     """Surrogate training throughput: Adam steps of the 1 -> 64 -> 64 -> 2
     network (64 x 64 layer on tcgen05, BF16 operands, FP32 accumulators in
-    TMEM) on mini-batches drawn from a 1D run's sample store."""
+    TMEM) on mini-batches drawn from a 1D run's sample store, split (a CTA
+    per 128-sample tile, then an update launch, per step) and in one CTA."""
     from paper_1105_4840_gb300 import inputs
 
     w = inputs.od1d_workload()
@@ -593,28 +597,33 @@ def bench_mlp(args, pmf, torch, stream):
     sysh = pmf.pmf_create_system_1d(w["a"], w["x0"])
     rr = pmf.pmf_run_windows(sysh, run.lambdas, pmf.make_params(run))
     lam = run.lambdas
-    mlp = pmf.Mlp(pmf.pack_mlp_params(inputs.mlp_init_params(2)), 0.5 * (lam[0] + lam[-1]),
-                  0.5 * (lam[-1] - lam[0]))
     batch, steps = args.mlp_batch, args.mlp_steps
-    for _ in range(args.warmup):
-        mlp.train(rr, 50, batch, 3e-3, 1)
-    times = []
-    for i in range(args.steps):
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        e[0].record(stream)
-        loss = mlp.train(rr, steps, batch, 3e-3, 100 + i)
-        e[1].record(stream)
-        torch.cuda.synchronize()
-        times.append(e[0].elapsed_time(e[1]) / 1000.0)
-    t = statistics.median(times)
     tiles = (batch + 127) // 128
     flops = steps * tiles * 3 * 2 * 128 * 64 * 64  # Z2, dH1, dW2 of the 64 x 64 layer
     peak = float(_peaks().get("bf16_tflops", 1939.8))
-    line = {"workload": "surrogate_training", "metric": "adam_steps/s", "value": steps / t, "unit": "steps/s",
-            "batch": batch, "steps_per_launch": steps, "samples_per_s": steps * batch / t,
-            "us_per_step": 1e6 * t / steps, "loss": loss, "ctas": 1,
-            "tensor": {"achieved": flops / t / 1e12, "unit": "TFLOP/s", "peak": peak,
-                       "frac": flops / t / 1e12 / peak, "note": "one CTA by design; latency bound"}}
+    lines = {}
+    for split in (1, 0):
+        mlp = pmf.Mlp(pmf.pack_mlp_params(inputs.mlp_init_params(2)), 0.5 * (lam[0] + lam[-1]),
+                      0.5 * (lam[-1] - lam[0]))
+        mlp.set_split(split)
+        for _ in range(args.warmup):
+            mlp.train(rr, 50, batch, 3e-3, 1)
+        times = []
+        for i in range(args.steps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record(stream)
+            loss = mlp.train(rr, steps, batch, 3e-3, 100 + i)
+            e[1].record(stream)
+            torch.cuda.synchronize()
+            times.append(e[0].elapsed_time(e[1]) / 1000.0)
+        t = statistics.median(times)
+        lines[split] = {"value": steps / t, "us_per_step": 1e6 * t / steps, "samples_per_s": steps * batch / t,
+                        "loss": loss, "ctas": tiles if split else 1,
+                        "tensor_tflops": flops / t / 1e12, "tensor_frac": flops / t / 1e12 / peak}
+        mlp.close()
+    line = {"workload": "surrogate_training", "metric": "adam_steps/s", "value": lines[1]["value"], "unit": "steps/s",
+            "batch": batch, "steps_per_launch": steps, "split": lines[1], "one_cta": lines[0],
+            "tensor_peak_tflops": peak, "note": "latency bound: a 4418-parameter network, 4 tiles per step"}
     print(json.dumps(line), flush=True)
 
 

@@ -495,6 +495,15 @@ pmf_status pmf_mlp_gradient(pmf_mlp *mlp, const double *lambda, const float *x, 
  * memory). */
 pmf_status pmf_mlp_train(pmf_mlp *mlp, const pmf_run *run, int steps, int batch, double lr, uint64_t seed,
                          double *loss);
+/* How training (pmf_mlp_train and the adaptive protocol's rounds) runs on
+ * the GPU.  split = 1 (the default): every Adam step is one launch with a
+ * CTA per 128-sample tile of the batch, each writing its tile's gradient,
+ * then an update launch that sums the tiles in tile order and applies Adam;
+ * the scratch ([tiles][PMF_MLP_PARAMS] floats) is allocated on first use and
+ * kept with the surrogate.  split = 0: one CTA runs all steps, the tiles of
+ * a step one after another.  Both draw the same mini-batches; they differ
+ * only in FP32 summation order.  PMF_EINVAL for other values. */
+pmf_status pmf_mlp_set_split(pmf_mlp *mlp, int split);
 
 /* ---- adaptive protocol: surrogate-guided window insertion -----------------
  * Starting from windows lambda0[n0] (a coarse PPP run from x_o), repeat up

@@ -1265,12 +1265,18 @@ struct pmf_mlp {
     int *err = nullptr;
     int t = 0;
     double c = 0, h = 1;
+    int split = 1;                   // training: one CTA per 128-sample tile
+    float *tile_grad = nullptr;      // [tile_cap][kMlpParams]
+    double *tile_loss = nullptr;     // [tile_cap]
+    int tile_cap = 0;
     ~pmf_mlp()
     {
         cudaFree(params);
         cudaFree(m);
         cudaFree(v);
         cudaFree(err);
+        cudaFree(tile_grad);
+        cudaFree(tile_loss);
     }
 };
 
@@ -1314,6 +1320,23 @@ static pmf_status mlp_run(pmf_mlp *mlp, MlpLaunch &L, const char *where)
     L.c = mlp->c;
     L.h = mlp->h;
     L.err = mlp->err;
+    if (L.mode == 2 && mlp->split) {
+        const int tiles = (L.batch + kMlpTile - 1) / kMlpTile;
+        if (tiles > mlp->tile_cap) {
+            cudaFree(mlp->tile_grad);
+            cudaFree(mlp->tile_loss);
+            mlp->tile_grad = nullptr;
+            mlp->tile_loss = nullptr;
+            mlp->tile_cap = 0;
+            CK(cudaMalloc(&mlp->tile_grad, sizeof(float) * kMlpParams * tiles), where);
+            CK(cudaMalloc(&mlp->tile_loss, sizeof(double) * tiles), where);
+            mlp->tile_cap = tiles;
+        }
+        L.split = true;
+        L.tile_grad = mlp->tile_grad;
+        L.tile_loss = mlp->tile_loss;
+        L.tile_cap = mlp->tile_cap;
+    }
     CK(cudaMemsetAsync(mlp->err, 0, sizeof(int), g_stream), where);
     cudaError_t e = mlp_launch(L, g_stream);
     if (e != cudaSuccess) return cuda_fail(e, where);
@@ -1369,6 +1392,13 @@ pmf_status pmf_mlp_gradient(pmf_mlp *mlp, const double *lambda, const float *x, 
     if (pmf_status s = mlp_run(mlp, L, "pmf_mlp_gradient")) return s;
     CK(cudaMemcpy(grad, t.g, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost), "copy");
     if (loss) CK(cudaMemcpy(loss, t.loss, sizeof(double), cudaMemcpyDeviceToHost), "copy");
+    return PMF_OK;
+}
+
+pmf_status pmf_mlp_set_split(pmf_mlp *mlp, int split)
+{
+    if (!mlp || (split != 0 && split != 1)) return fail(PMF_EINVAL, "pmf_mlp_set_split: bad argument");
+    mlp->split = split;
     return PMF_OK;
 }
 

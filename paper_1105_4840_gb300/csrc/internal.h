@@ -192,6 +192,7 @@ cudaError_t work_samples_launch(const ReduceLayout &L, int mode, long long sampl
 
 // Surrogate MLP (mlp.cu)
 constexpr int kMlpParams = 64 + 64 + 64 * 64 + 64 + 2 * 64 + 2;
+constexpr int kMlpTile = 128;  // samples per tcgen05 tile (one CTA's rows)
 struct MlpLaunch {
     float *params = nullptr, *adam_m = nullptr, *adam_v = nullptr;
     int adam_t = 0;
@@ -210,6 +211,13 @@ struct MlpLaunch {
     float *out_grad = nullptr;
     double *out_loss = nullptr;
     int *err = nullptr;
+    // training (mode 2) with split: one CTA per 128-sample tile and an
+    // update kernel per step; tile_grad [tile_cap][kMlpParams] and
+    // tile_loss [tile_cap] are the caller's scratch
+    bool split = false;
+    float *tile_grad = nullptr;
+    double *tile_loss = nullptr;
+    int tile_cap = 0;
 };
 cudaError_t mlp_launch(const MlpLaunch &L, cudaStream_t st);
 

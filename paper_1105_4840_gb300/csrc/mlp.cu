@@ -26,7 +26,7 @@ namespace pmf {
 namespace {
 
 constexpr int kH = 64;
-constexpr int kTile = 128;
+constexpr int kTile = kMlpTile;
 // parameter offsets in the packed FP32 vector
 constexpr int oW1 = 0, oB1 = 64, oW2 = 128, oB2 = 128 + 4096, oW3 = oB2 + 64, oB3 = oW3 + 128;
 static_assert(oB3 + 2 == kMlpParams, "parameter packing");
@@ -160,12 +160,14 @@ struct MlpArgs {
     const long long *win_tw;    // [n_windows]
     int n_windows, replicas;
     long long total;
-    int mode;                   // 0 forward, 1 gradient, 2 train
+    int mode;                   // 0 forward, 1 gradient, 2 train, 3 one tile of a training step
     int steps, batch;
     unsigned long long seed;
     double *out_mu, *out_logvar;  // forward outputs [n]
     float *out_grad;            // gradient mode [kMlpParams]
     double *out_loss;           // gradient / train: last batch loss
+    float *tile_grad;           // mode 3: [tiles][kMlpParams] gradient of each CTA's tile
+    double *tile_loss;          // mode 3: [tiles] loss sum of each CTA's tile
     int *err;
 };
 
@@ -384,8 +386,11 @@ __global__ void __launch_bounds__(kTile, 1) mlp_kernel(const MlpArgs a)
     __shared__ double loss_acc;
 
     const int t = threadIdx.x, warp = t >> 5;
+    // a split training step after a failed one does nothing (the host has
+    // queued every step's launches; the failure is already flagged)
+    if (a.mode == 3 && *(volatile int *)a.err) return;
     for (int e = t; e < kMlpParams; e += kTile) s.w[e] = a.params[e];
-    if (a.mode == 2 && a.n_windows <= kMaxSmemWindows)
+    if ((a.mode == 2 || a.mode == 3) && a.n_windows <= kMaxSmemWindows)
         for (int e = t; e < a.n_windows; e += kTile) s.win_off[e] = a.win_off[e];
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(s.mbar)) : "memory");
@@ -427,6 +432,33 @@ __global__ void __launch_bounds__(kTile, 1) mlp_kernel(const MlpArgs a)
             collect_dw2(s, tmem);
             for (int e = t; e < kMlpParams; e += kTile) a.out_grad[e] = s.grad[e];
             if (t == 0 && a.out_loss) *a.out_loss = loss_acc / a.n;
+        }
+    } else if (a.mode == 3) {
+        // one 128-sample tile of Adam step adam_t per CTA (tile = blockIdx.x
+        // of gridDim.x): the same mini-batch draw as the one-CTA training,
+        // its gradient and loss sum to this tile's slot; adam_kernel then
+        // sums the tiles in a fixed order and updates the weights
+        const int tile = blockIdx.x;
+        const float inv_batch = 1.f / (float)(gridDim.x * kTile);
+        for (int e = t; e < kMlpParams; e += kTile) s.grad[e] = 0.f;
+        if (t == 0) loss_acc = 0.0;
+        __syncthreads();
+        const long long idx = pick_sample(a.seed, a.adam_t, tile * kTile + t, a.total);
+        const long long *off = a.n_windows <= kMaxSmemWindows ? s.win_off : a.win_off;
+        int lo = 0, hi = a.n_windows - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= idx) lo = mid;
+            else hi = mid - 1;
+        }
+        s.lam[t] = (float)((a.win_lambda[lo] - a.c) * ih);
+        s.dout[2 * t] = (float)(((double)a.xs[idx] - a.c) * ih);
+        __syncthreads();
+        ok = mlp_tile(a, s, tmem, phase, kTile, inv_batch, true, true, &loss_acc);
+        if (ok) {
+            collect_dw2(s, tmem);
+            for (int e = t; e < kMlpParams; e += kTile) a.tile_grad[(size_t)tile * kMlpParams + e] = s.grad[e];
+            if (t == 0) a.tile_loss[tile] = loss_acc;
         }
     } else {
         // training: Adam steps on mini-batches drawn from the run's samples
@@ -481,6 +513,33 @@ __global__ void __launch_bounds__(kTile, 1) mlp_kernel(const MlpArgs a)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
+// The update half of a split training step: the tiles' gradients summed in
+// tile order, then Adam (Kingma & Ba) with bias correction for step tt on
+// the FP32 master weights in global memory; the last step also writes the
+// batch loss.  Skipped after a failed tile launch.
+__global__ void adam_kernel(float *params, float *adam_m, float *adam_v, const float *tile_grad,
+                            const double *tile_loss, int tiles, int tt, float lr, double *out_loss, const int *err)
+{
+    if (*(const volatile int *)err) return;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < kMlpParams) {
+        float g = 0.f;
+        for (int b = 0; b < tiles; ++b) g += tile_grad[(size_t)b * kMlpParams + e];
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - powf(b1, (float)tt), c2 = 1.f - powf(b2, (float)tt);
+        const float m = b1 * adam_m[e] + (1.f - b1) * g;
+        const float v = b2 * adam_v[e] + (1.f - b2) * g * g;
+        adam_m[e] = m;
+        adam_v[e] = v;
+        params[e] -= lr * (m / c1) / (sqrtf(v / c2) + 1e-8f);
+    }
+    if (out_loss && e == 0) {
+        double l = 0.0;
+        for (int b = 0; b < tiles; ++b) l += tile_loss[b];
+        *out_loss = l / (double)(tiles * kTile);
+    }
+}
+
 }  // namespace
 
 cudaError_t mlp_launch(const MlpLaunch &L, cudaStream_t st)
@@ -511,9 +570,27 @@ cudaError_t mlp_launch(const MlpLaunch &L, cudaStream_t st)
     a.out_logvar = L.out_logvar;
     a.out_grad = L.out_grad;
     a.out_loss = L.out_loss;
+    a.tile_grad = L.tile_grad;
+    a.tile_loss = L.tile_loss;
     a.err = L.err;
     cudaError_t e = cudaFuncSetAttribute(mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
+    const int tiles = (L.batch + kTile - 1) / kTile;
+    if (L.mode == 2 && L.split && tiles >= 2) {
+        // one CTA per tile: per step a tile launch and an update launch
+        if (!L.tile_grad || !L.tile_loss || tiles > L.tile_cap) return cudaErrorInvalidValue;
+        a.mode = 3;
+        for (int step = 0; step < L.steps; ++step) {
+            a.adam_t = L.adam_t + step;
+            mlp_kernel<<<tiles, kTile, kSmemBytes, st>>>(a);
+            adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, st>>>(L.params, L.adam_m, L.adam_v, L.tile_grad,
+                                                                  L.tile_loss, tiles, L.adam_t + step + 1,
+                                                                  (float)L.lr,
+                                                                  step + 1 == L.steps ? L.out_loss : nullptr, L.err);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     mlp_kernel<<<1, kTile, kSmemBytes, st>>>(a);
     return cudaGetLastError();
 }

@@ -153,6 +153,7 @@ def _load():
     L.pmf_mlp_predict.argtypes = [P, _D, C.c_int, _D, _D]
     L.pmf_mlp_gradient.argtypes = [P, _D, _F, C.c_int, _F, _D]
     L.pmf_mlp_train.argtypes = [P, P, C.c_int, C.c_int, C.c_double, C.c_uint64, _D]
+    L.pmf_mlp_set_split.argtypes = [P, C.c_int]
     L.pmf_overlap.argtypes = [_D, _D, C.c_int, _D]
     L.pmf_run_adaptive.argtypes = [P, _D, C.c_int, C.POINTER(RunParams), C.POINTER(AdaptiveParams),
                                    C.POINTER(AdaptiveInfo), C.POINTER(FreeEnergyResult)]
@@ -619,6 +620,9 @@ class Mlp:
         _check(lib.pmf_mlp_gradient(self.handle, _dp(lam), x.ctypes.data_as(_F), lam.size, g.ctypes.data_as(_F),
                                     C.byref(loss)), "pmf_mlp_gradient")
         return g, loss.value
+
+    def set_split(self, split):
+        _check(lib.pmf_mlp_set_split(self.handle, int(split)), "pmf_mlp_set_split")
 
     def train(self, run, steps, batch, lr, seed):
         loss = C.c_double()

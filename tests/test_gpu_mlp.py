@@ -76,9 +76,11 @@ def test_gradient_matches_oracle(pmf):
         off += n
 
 
-def test_training_on_1d_run_matches_oracle_training(pmf):
+@pytest.mark.parametrize("split", [1, 0])
+def test_training_on_1d_run_matches_oracle_training(pmf, split):
     """Adam on identical Philox mini-batches of the 1D workload's samples:
-    GPU and oracle surrogates agree, and both fit the window statistics."""
+    GPU and oracle surrogates agree, and both fit the window statistics
+    (split: a CTA per tile and an update launch per step; else one CTA)."""
     w = inputs.od1d_workload()
     run = w["run"]
     sysh = pmf.pmf_create_system_1d(w["a"], w["x0"])
@@ -90,6 +92,7 @@ def test_training_on_1d_run_matches_oracle_training(pmf):
     p0 = _params(11, jitter=0.0)
     steps, batch, lr, seed = 300, 512, 3e-3, 7
     m = pmf.Mlp(pmf.pack_mlp_params(p0), c, h)
+    m.set_split(split)
     loss_g = m.train(rr, steps, batch, lr, seed)
     po, _, loss_o = sg.train({k: v.copy() for k, v in p0.items()}, store, info["sample_offset"], run.lambdas,
                              steps, batch, lr, seed, c, h, _clib.philox_bulk)
@@ -101,3 +104,33 @@ def test_training_on_1d_run_matches_oracle_training(pmf):
     assert np.max(np.abs(lv_g - lv_o)) < 0.25
     mean = np.array([b.mean() for b in xo])
     assert np.median(np.abs(mu_g - mean) / sd) < 0.3
+
+
+def test_split_training_matches_one_cta_step_by_step(pmf):
+    """The same mini-batches, one Adam step: the split launch's weights equal
+    the one-CTA kernel's up to FP32 summation order of the tile gradients
+    (Adam's first step moves every weight by lr sign(g), so any difference
+    beyond rounding is a wrong gradient); then 200 steps stay close."""
+    w = inputs.od1d_workload()
+    run = w["run"]
+    sysh = pmf.pmf_create_system_1d(w["a"], w["x0"])
+    rr = pmf.pmf_run_windows(sysh, run.lambdas, pmf.make_params(run))
+    p0 = pmf.pack_mlp_params(_params(11, jitter=0.0))
+    out = {}
+    for split in (1, 0):
+        m = pmf.Mlp(p0, 0.0, 1.5)
+        m.set_split(split)
+        m.train(rr, 1, 512, 3e-3, 7)
+        one = m.params()
+        m.train(rr, 199, 512, 3e-3, 8)
+        out[split] = (one, m.params(), m.predict(run.lambdas))
+        m.close()
+    d1 = np.abs(out[1][0] - out[0][0])
+    assert np.mean(d1 > 1e-6) < 0.01 and d1.max() <= 2 * 3e-3
+    mu1, lv1 = out[1][2]
+    mu0, lv0 = out[0][2]
+    sd = np.array([b.std() for b in rr.x_samples()])
+    assert np.max(np.abs(mu1 - mu0) / sd) < 0.1 and np.max(np.abs(lv1 - lv0)) < 0.1
+    with pytest.raises(pmf.PmfError) as e:
+        pmf.Mlp(p0, 0.0, 1.0).set_split(2)
+    assert e.value.status == pmf.PMF_EINVAL

@@ -427,10 +427,12 @@ def bench_adaptive(args, pmf, torch):
         # the least-squares drift per round over those rounds
         s_ref = aw["s_reference_cont"]
         r_ref = args.reference_replicas or aw["replicas_reference"]
-        n_rounds = args.reference_rounds or aw["reference_rounds"]
-        n_avg = min(aw["reference_average"], n_rounds)
+        n_rounds = aw["reference_rounds"] if args.reference_rounds is None else args.reference_rounds
+        n_avg = min(args.reference_average or aw["reference_average"], n_rounds)
         tau_ref = steps_of(aw["reference_round_ps"]) if args.reference_steps is None else args.reference_steps
         drift, ref_gpu_s, rr = [], 0.0, None
+        if n_rounds == 0:  # no reference (the protocols' values alone)
+            n_avg = 0
         for rnd in range(n_rounds):
             pos = None
             if rr is not None:
@@ -439,16 +441,17 @@ def bench_adaptive(args, pmf, torch):
             res, gs, rr = uniform(s_ref, r_ref, tau_ref, 1000 + rnd, uid_base=rnd * s_ref * r_ref, starts=pos)
             ref_gpu_s += gs
             drift.append({"round": rnd, "dF": float(res["dF_JE"][-1]), "se": float(res["se_JE"][-1]), "gpu_s": gs})
-        rr.close()
-        last = drift[-n_avg:]
-        F_ref = float(np.mean([d["dF"] for d in last]))
-        se_ref = math.sqrt(sum(d["se"] ** 2 for d in last)) / n_avg
+        if rr is not None:
+            rr.close()
+        last = drift[-n_avg:] if n_avg else []
+        F_ref = float(np.mean([d["dF"] for d in last])) if last else math.nan
+        se_ref = math.sqrt(sum(d["se"] ** 2 for d in last)) / n_avg if last else math.nan
         slope = float(np.polyfit(np.arange(n_avg), [d["dF"] for d in last], 1)[0]) if n_avg > 1 else 0.0
         print(json.dumps({"beads": n_beads, "reference": {"dF_JE": F_ref, "se": se_ref, "drift_kT_per_round": slope / kT,
                                                           "rounds": drift}}), flush=True)
         init = pmf.pack_mlp_params(inputs.mlp_init_params(2))
         rows = {"uniform": [], "adaptive": []}
-        for seed in aw["seeds"]:
+        for seed in ([] if args.reference_only else aw["seeds"]):
             for tau in sorted(set(aw["tau_ps"]) | set(aw["tau_uniform_extra"])):
                 n_steps = steps_of(tau)
                 res, gs, rr = uniform(aw["s_uniform"], R, n_steps, seed)
@@ -851,7 +854,10 @@ def main():
     ap.add_argument("--adaptive-beads", type=int, nargs="+", default=[104, 200], help="chain lengths (adaptive)")
     ap.add_argument("--reference-steps", type=int, default=None,
                     help="steps per window and round of the continued reference (adaptive; default 0.4 ns)")
-    ap.add_argument("--reference-rounds", type=int, default=None, help="rounds of the continued reference")
+    ap.add_argument("--reference-rounds", type=int, default=None,
+                    help="rounds of the continued reference (adaptive; 0: none)")
+    ap.add_argument("--reference-average", type=int, default=None, help="last reference rounds averaged")
+    ap.add_argument("--reference-only", action="store_true", help="adaptive: run the reference alone")
     ap.add_argument("--reference-replicas", type=int, default=None, help="replicas per reference window")
     ap.add_argument("--adaptive-replicas", type=int, default=None, help="replicas per window (adaptive)")
     ap.add_argument("--tau-uniform-extra", type=float, nargs="*", default=None,

@@ -52,6 +52,7 @@ def test_batch_matches_oracle(pmf):
     params, starts, lams, run = _small_batch()
     sysh = pmf.pmf_create_system_chain(params, starts)
     rr = pmf.pmf_run_batch_prepare(sysh, list(enumerate(lams)), pmf.make_params(run))
+    rr.set_batch_launch(pmf.PMF_BATCH_PACKED, policy)
     rr.launch()
     rr.wait()
     pos = _final_positions(rr, params, lams, run.replicas)
@@ -171,11 +172,13 @@ def test_batch_rejects_bad_items(pmf):
     assert e.value.status == pmf.PMF_EINVAL
 
 
-def test_full_batch_sampled_replicas(pmf):
+@pytest.mark.parametrize("policy", [0, 1])
+def test_full_batch_sampled_replicas(pmf, policy):
     """The 64-chain batch (N 40-400, 21-61 windows, 16 replicas; 2669
     windows, 42,704 replicas) in the launch configuration the benchmark
-    times, shortened to 200 steps: sampled replicas of the shortest,
-    longest and four other chains against the oracle."""
+    times (one packed launch; policy 0 is the default, 1 the one the
+    benchmark's autotuner picks), shortened to 200 steps: sampled replicas
+    of the shortest, longest and four other chains against the oracle."""
     bw = inputs.batch_workload()
     run = bw["run"]
     run.n_steps, run.n_equil, run.stride = 200, 100, 100
@@ -183,6 +186,7 @@ def test_full_batch_sampled_replicas(pmf):
     starts = [f32(s) for s in bw["starts"]]
     sysh = pmf.pmf_create_system_chain(params, starts)
     rr = pmf.pmf_run_batch_prepare(sysh, list(enumerate(lams)), pmf.make_params(run))
+    rr.set_batch_launch(pmf.PMF_BATCH_PACKED, policy)
     rr.launch()
     rr.wait()
     pos = _final_positions(rr, params, lams, run.replicas)

@@ -450,16 +450,41 @@ def bench_adaptive(args, pmf, torch):
         print(json.dumps({"beads": n_beads, "reference": {"dF_JE": F_ref, "se": se_ref, "drift_kT_per_round": slope / kT,
                                                           "rounds": drift}}), flush=True)
         init = pmf.pack_mlp_params(inputs.mlp_init_params(2))
-        rows = {"uniform": [], "adaptive": []}
+        protocols = args.protocols
+        rows = {k: [] for k in protocols}
+
+        def continued(s_win, n_steps, seed):
+            """s_win uniform windows for n_steps, then every replica continued
+            from its end state for n_steps more (fresh uids); the estimate is
+            the second run's, the GPU time both runs'."""
+            res, gs1, rr = uniform(s_win, R, n_steps, seed)
+            pos, _ = rr.final_state()
+            rr.close()
+            res, gs2, rr = uniform(s_win, R, n_steps, seed, uid_base=s_win * R, starts=pos)
+            rr.close()
+            return res, gs1 + gs2
+
         for seed in ([] if args.reference_only else aw["seeds"]):
             for tau in sorted(set(aw["tau_ps"]) | set(aw["tau_uniform_extra"])):
                 n_steps = steps_of(tau)
-                res, gs, rr = uniform(aw["s_uniform"], R, n_steps, seed)
-                rr.close()
-                rows["uniform"].append({"seed": seed, "tau_ps": tau, "gpu_s": gs, "windows": aw["s_uniform"],
-                                        "dF": float(res["dF_JE"][-1]), "se": float(res["se_JE"][-1])})
+                line = {"seed": seed, "tau_ps": tau}
+                if "uniform" in protocols:
+                    res, gs, rr = uniform(aw["s_uniform"], R, n_steps, seed)
+                    rr.close()
+                    rows["uniform"].append({"seed": seed, "tau_ps": tau, "gpu_s": gs, "windows": aw["s_uniform"],
+                                            "dF": float(res["dF_JE"][-1]), "se": float(res["se_JE"][-1])})
+                    line["uniform"] = rows["uniform"][-1]
                 if tau not in aw["tau_ps"]:
-                    print(json.dumps({"seed": seed, "tau_ps": tau, "uniform": rows["uniform"][-1]}), flush=True)
+                    print(json.dumps(line), flush=True)
+                    continue
+                for name, s_win in (("uniform_continued", aw["s_uniform"]), ("coarse_continued", aw["s_adaptive0"])):
+                    if name in protocols:
+                        res, gs = continued(s_win, n_steps, seed)
+                        rows[name].append({"seed": seed, "tau_ps": tau, "gpu_s": gs, "windows": s_win,
+                                           "dF": float(res["dF_JE"][-1]), "se": float(res["se_JE"][-1])})
+                        line[name] = rows[name][-1]
+                if "adaptive" not in protocols:
+                    print(json.dumps(line), flush=True)
                     continue
                 run.replicas, run.n_steps, run.n_equil, run.seed = R, n_steps, n_steps // 10, seed
                 lam0 = np.linspace(aw["lo"], aw["hi"], aw["s_adaptive0"])
@@ -471,8 +496,8 @@ def bench_adaptive(args, pmf, torch):
                 rows["adaptive"].append({"seed": seed, "tau_ps": tau, "gpu_s": meta["gpu_seconds"],
                                          "windows": meta["n_windows"], "rounds": meta["rounds"],
                                          "dF": float(ares["dF_JE"][-1]), "se": float(ares["se_JE"][-1])})
-                print(json.dumps({"seed": seed, "tau_ps": tau, "uniform": rows["uniform"][-1],
-                                  "adaptive": rows["adaptive"][-1]}), flush=True)
+                line["adaptive"] = rows["adaptive"][-1]
+                print(json.dumps(line), flush=True)
 
         def summary(rs):
             per_seed = []
@@ -499,8 +524,7 @@ def bench_adaptive(args, pmf, torch):
                               "reference": {"dF_JE": F_ref, "se": se_ref, "drift_kT_per_round": slope / kT,
                                             "averaged_rounds": n_avg, "gpu_s": ref_gpu_s, "windows": s_ref,
                                             "replicas": r_ref, "md_steps_per_round": tau_ref, "rounds": drift},
-                              "uniform": summary(rows["uniform"]), "adaptive": summary(rows["adaptive"]),
-                              "runs": rows})
+                              **{k: summary(v) for k, v in rows.items()}, "runs": rows})
         sysh.close()
         print(json.dumps(out["chains"][-1]), flush=True)
     print(json.dumps(out), flush=True)
@@ -858,6 +882,9 @@ def main():
                     help="rounds of the continued reference (adaptive; 0: none)")
     ap.add_argument("--reference-average", type=int, default=None, help="last reference rounds averaged")
     ap.add_argument("--reference-only", action="store_true", help="adaptive: run the reference alone")
+    ap.add_argument("--protocols", nargs="+", default=["uniform", "adaptive"],
+                    choices=["uniform", "adaptive", "uniform_continued", "coarse_continued"],
+                    help="adaptive: protocols to run (the continued ones run tau twice, the second run estimating)")
     ap.add_argument("--reference-replicas", type=int, default=None, help="replicas per reference window")
     ap.add_argument("--adaptive-replicas", type=int, default=None, help="replicas per window (adaptive)")
     ap.add_argument("--tau-uniform-extra", type=float, nargs="*", default=None,

@@ -52,7 +52,6 @@ def test_batch_matches_oracle(pmf):
     params, starts, lams, run = _small_batch()
     sysh = pmf.pmf_create_system_chain(params, starts)
     rr = pmf.pmf_run_batch_prepare(sysh, list(enumerate(lams)), pmf.make_params(run))
-    rr.set_batch_launch(pmf.PMF_BATCH_PACKED, policy)
     rr.launch()
     rr.wait()
     pos = _final_positions(rr, params, lams, run.replicas)

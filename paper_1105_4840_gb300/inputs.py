@@ -220,7 +220,7 @@ def adaptive_workload(n_beads: int = 104, param_seed: int | None = None) -> dict
     protocol starts from 11 uniform windows, the uniform protocol uses 21;
     window relaxation times tau of 0.2, 0.4, 0.8, 1.6 ns (the uniform grid
     also at 3.2 ns); dynamics seeds 0..2.  The converged reference is 41
-    uniform windows x 256 replicas continued for 8 rounds of 0.4 ns, each
+    uniform windows x 256 replicas continued for 16 rounds of 0.4 ns, each
     round resuming every replica from its end state, averaged over its last
     4 rounds (s_reference: the earlier single-run reference of 81 windows)."""
     ps = param_seed if param_seed is not None else (1 if n_beads == 104 else 2)
@@ -233,7 +233,7 @@ def adaptive_workload(n_beads: int = 104, param_seed: int | None = None) -> dict
     return {"params": p, "start": start, "lo": lo, "hi": hi, "run": run,
             "tau_ps": [200.0, 400.0, 800.0, 1600.0], "tau_uniform_extra": [3200.0], "seeds": [0, 1, 2],
             "s_uniform": 21, "s_adaptive0": 11, "s_reference": 81, "s_reference_cont": 41,
-            "replicas_reference": 256, "reference_round_ps": 400.0, "reference_rounds": 8, "reference_average": 4}
+            "replicas_reference": 256, "reference_round_ps": 400.0, "reference_rounds": 16, "reference_average": 4}
 
 
 def mlp_init_params(seed: int, hidden: int = 64, scale_in: float = 1.0) -> dict:

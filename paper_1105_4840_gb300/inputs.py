@@ -216,24 +216,29 @@ def adaptive_workload(n_beads: int = 104, param_seed: int | None = None) -> dict
     """Learned window placement against the uniform grid: an n-bead chain
     (parameter seed 1 for 104 beads, 2 otherwise) pulled from lo to hi =
     (1.3, 3.3) nm x sqrt(n / 104) with the 104-bead workload's trap,
-    temperature and integrator; 256 replicas per window; the adaptive
-    protocol starts from 11 uniform windows, the uniform protocol uses 21;
-    window relaxation times tau of 0.2, 0.4, 0.8, 1.6 ns (the uniform grid
-    also at 3.2 ns); dynamics seeds 0..2.  The converged reference is 41
-    uniform windows x 256 replicas continued for 16 rounds of 0.4 ns, each
-    round resuming every replica from its end state, averaged over its last
-    4 rounds (s_reference: the earlier single-run reference of 81 windows)."""
+    temperature and integrator; the adaptive protocol starts from 11 uniform
+    windows, the uniform protocol uses 21.  Below 200 beads: 256 replicas per
+    window, window relaxation times tau of 0.2, 0.4, 0.8, 1.6 ns (the
+    uniform grid also at 3.2 ns), dynamics seeds 0..2; from 200 beads on:
+    128 replicas, tau of 0.4, 0.8, 1.6 ns (uniform also 3.2 ns), seeds 0..1.
+    The converged reference is 41 uniform windows with the same replica
+    count, continued for 16 rounds of 0.4 ns, each round resuming every
+    replica from its end state, averaged over its last 4 rounds
+    (s_reference: the earlier single-run reference of 81 windows)."""
     ps = param_seed if param_seed is not None else (1 if n_beads == 104 else 2)
     p = chain_params(n_beads, ps)
     scale = math.sqrt(n_beads / 104.0)
     lo, hi = 1.3 * scale, 3.3 * scale
     start = chain_start(p, ps + 1000, target_x=lo)
+    long_chain = n_beads >= 200
+    R = 128 if long_chain else 256
     run = RunSettings(k=500.0, kT=kT_of(300.0), dt=0.001, gamma=5.0, n_steps=0, n_equil=0, stride=100,
-                      replicas=256, seed=0)
+                      replicas=R, seed=0)
     return {"params": p, "start": start, "lo": lo, "hi": hi, "run": run,
-            "tau_ps": [200.0, 400.0, 800.0, 1600.0], "tau_uniform_extra": [3200.0], "seeds": [0, 1, 2],
+            "tau_ps": [400.0, 800.0, 1600.0] if long_chain else [200.0, 400.0, 800.0, 1600.0],
+            "tau_uniform_extra": [3200.0], "seeds": [0, 1] if long_chain else [0, 1, 2],
             "s_uniform": 21, "s_adaptive0": 11, "s_reference": 81, "s_reference_cont": 41,
-            "replicas_reference": 256, "reference_round_ps": 400.0, "reference_rounds": 16, "reference_average": 4}
+            "replicas_reference": R, "reference_round_ps": 400.0, "reference_rounds": 16, "reference_average": 4}
 
 
 def mlp_init_params(seed: int, hidden: int = 64, scale_in: float = 1.0) -> dict:

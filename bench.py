@@ -366,6 +366,39 @@ def bench_precision(args, pmf, torch):
     print(json.dumps(line), flush=True)
 
 
+def ladder_summary(rs, seeds, F_ref, kT, tolerances=(0.2, 0.3, 0.5, 1.0)):
+    """GPU-seconds to a path free energy within eps of the reference: per
+    seed, the run at the shortest tau from which this and every longer run
+    stays within eps * kT of F_ref (None if none does); the median over the
+    seeds only when every seed got there.  Also the mean deviation, its
+    spread over the seeds, the mean jackknife SE and the mean GPU-seconds
+    per tau.  rs: rows {"seed", "tau_ps", "gpu_s", "dF", "se"}."""
+    def reach(eps):
+        per_seed = []
+        for seed in seeds:
+            ladder = sorted([r for r in rs if r["seed"] == seed], key=lambda r: r["tau_ps"])
+            ok = [abs(r["dF"] - F_ref) < eps * kT for r in ladder]
+            first = next((i for i in range(len(ladder)) if all(ok[i:])), None)
+            per_seed.append(None if first is None else {"tau_ps": ladder[first]["tau_ps"],
+                                                        "gpu_s": ladder[first]["gpu_s"]})
+        got = [x["gpu_s"] for x in per_seed if x is not None]
+        return per_seed, (statistics.median(got) if got and len(got) == len(per_seed) else None), len(got)
+
+    per_seed, med, n_ok = reach(0.2)
+    by_tau = []
+    for tau in sorted({r["tau_ps"] for r in rs}):
+        d = np.array([(r["dF"] - F_ref) / kT for r in rs if r["tau_ps"] == tau])
+        g = [r["gpu_s"] for r in rs if r["tau_ps"] == tau]
+        se = [r["se"] / kT for r in rs if r["tau_ps"] == tau]
+        by_tau.append({"tau_ps": tau, "bias_kT": float(d.mean()), "sd_kT": float(d.std(ddof=1)) if d.size > 1 else 0.0,
+                       "mean_se_kT": float(np.mean(se)), "gpu_s": float(np.mean(g))})
+    by_eps = []
+    for eps in tolerances:
+        ps, m, k = reach(eps)
+        by_eps.append({"eps_kT": eps, "median_gpu_s": m, "seeds_within": k, "per_seed": ps})
+    return {"median_gpu_s": med, "seeds_converged": n_ok, "per_seed": per_seed, "by_tau": by_tau, "by_eps": by_eps}
+
+
 def bench_adaptive(args, pmf, torch):
     """GPU-seconds to a path free energy within 0.2 kT of a converged
     reference: the learned window placement (11 windows, surrogate-guided
@@ -500,23 +533,7 @@ def bench_adaptive(args, pmf, torch):
                 print(json.dumps(line), flush=True)
 
         def summary(rs):
-            per_seed = []
-            for seed in aw["seeds"]:
-                ladder = sorted([r for r in rs if r["seed"] == seed], key=lambda r: r["tau_ps"])
-                ok = [abs(r["dF"] - F_ref) < 0.2 * kT for r in ladder]
-                first = next((i for i in range(len(ladder)) if all(ok[i:])), None)
-                per_seed.append(None if first is None else {"tau_ps": ladder[first]["tau_ps"],
-                                                            "gpu_s": ladder[first]["gpu_s"]})
-            got = [x["gpu_s"] for x in per_seed if x is not None]
-            by_tau = []
-            for tau in sorted({r["tau_ps"] for r in rs}):
-                d = np.array([(r["dF"] - F_ref) / kT for r in rs if r["tau_ps"] == tau])
-                g = [r["gpu_s"] for r in rs if r["tau_ps"] == tau]
-                se = [r["se"] / kT for r in rs if r["tau_ps"] == tau]
-                by_tau.append({"tau_ps": tau, "bias_kT": float(d.mean()), "sd_kT": float(d.std(ddof=1)) if d.size > 1 else 0.0,
-                               "mean_se_kT": float(np.mean(se)), "gpu_s": float(np.mean(g))})
-            return {"median_gpu_s": statistics.median(got) if got else None, "seeds_converged": len(got),
-                    "per_seed": per_seed, "by_tau": by_tau}
+            return ladder_summary(rs, aw["seeds"], F_ref, kT)
 
         out["chains"].append({"beads": n_beads, "lambda": [aw["lo"], aw["hi"]], "kT": kT, "replicas": R,
                               "adaptive_rounds": args.adaptive_rounds, "continuation": not args.no_continuation,

@@ -1,6 +1,6 @@
 // FP64 reductions of the recorded x samples into the paper's estimators.
 //
-// Stage 1 (one CTA per (window i, replica r), one pass over the samples):
+// Stage 1 (one CTA per (window i, replica r), two passes over the samples):
 //   work increments of Eq. (9),
 //   w = k/2 (lambda_{i+1} - lambda_i)(lambda_{i+1} + lambda_i - 2 x),
 //   the replica's minimum m_ir, the max-shifted exponential sum
@@ -73,41 +73,153 @@ template <int NT> __device__ double block_min(double v, double *red)
 
 constexpr int kPartialThreads = 256;
 
+// ---- the exponential of stage 1 in double-float arithmetic on the FP32 pipe
+//
+// GB300's FP64 unit retires 1/64 of the FP32 rate, and an FP64 exp per
+// sample made stage 1 FP64-bound.  The exponent is linear in x: with the
+// work increment w = k/2 (lambda_{i+1} - lambda_i)(lambda_{i+1} + lambda_i - 2x)
+// and its minimum at the sample x_ref (the largest x when lambda_{i+1} >
+// lambda_i, the smallest otherwise), -(w - min w)/kT = c (x - x_ref) <= 0 with
+// c = k (lambda_{i+1} - lambda_i)/kT.  x - x_ref is exact as a pair of floats
+// (TwoSum), c (x - x_ref) is formed as a pair of floats, and exp of that pair
+// follows Tang's table-driven method (P. T. P. Tang, ACM TOMS 15 (1989)
+// 144-157): a = n ln2/32 + r with |r| <= ln2/64, exp(a) = 2^(n div 32)
+// 2^((n mod 32)/32) (1 + p(r)), p the Taylor series of e^r - 1 to r^6 (the
+// next term is below 2e-18), 2^(j/32) as a pair of floats from the FP64 exp2,
+// ln2/32 split in three floats whose first has 12 significant bits so that
+// n times it is exact.  The relative error of a term, weighted by its size,
+// stays near 1e-14; terms below e^-80 of the largest are dropped (the largest
+// is 1).  The sums over the samples stay in FP64.
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void fast_two_sum_f(float a, float b, float &s, float &e)  // |a| >= |b|
+{
+    s = a + b;
+    e = b - (s - a);
+}
+
+struct ExpConsts {
+    float inv_l;          // 32 / ln 2
+    float l1, l2, l3;     // ln2/32 = l1 + l2 + l3, l1 with 12 significant bits
+};
+
+__device__ __forceinline__ ExpConsts exp_consts()
+{
+    // ln 2 as the double nearest to it plus the remainder
+    const double ln2_hi = 0.6931471805599453, ln2_lo = 2.319046813846299558e-17;
+    const double l = ln2_hi / 32.0;  // exact: a power-of-two scaling
+    ExpConsts k;
+    k.inv_l = (float)(32.0 / ln2_hi);
+    k.l1 = __int_as_float(__float_as_int((float)l) & ~0xFFF);
+    const double r1 = l - (double)k.l1;
+    k.l2 = (float)r1;
+    k.l3 = (float)((r1 - (double)k.l2) + ln2_lo / 32.0);
+    return k;
+}
+
+// exp(ah + al) for ah + al <= 0 (tab: 2^(j/32) = tab_hi[j] + tab_lo[j]).
+__device__ __forceinline__ double exp_ff(float ah, float al, const ExpConsts &k, const float *tab_hi,
+                                         const float *tab_lo)
+{
+    if (ah < -80.f) return 0.0;
+    const float kf = rintf(ah * k.inv_l);
+    const int n = (int)kf;
+    // r = a - n ln2/32: n l1 is exact and close to ah, n l2 exact as p2 + e2
+    const float t1 = fmaf(-kf, k.l1, ah);
+    const float p2 = kf * k.l2;
+    const float e2 = fmaf(kf, k.l2, -p2);
+    float rh, rl;
+    two_sum_f(t1, -p2, rh, rl);
+    rl += (al - e2) - kf * k.l3;
+    fast_two_sum_f(rh, rl, rh, rl);
+    // e^r - 1 = r + r^2/2 + r^3 (1/6 + r (1/24 + r (1/120 + r/720)))
+    const float sh = rh * rh;
+    const float sl = fmaf(rh, rh, -sh) + 2.f * rh * rl;
+    const float q = rh * sh * fmaf(rh, fmaf(rh, fmaf(rh, 1.f / 720.f, 1.f / 120.f), 1.f / 24.f), 1.f / 6.f);
+    float ph, pl;
+    two_sum_f(rh, 0.5f * sh, ph, pl);
+    pl += (rl + 0.5f * sl) + q;
+    fast_two_sum_f(ph, pl, ph, pl);
+    // 2^(j/32) (1 + p), then the power of two 2^(n div 32) (exact)
+    const int j = n & 31, m = n >> 5;
+    const float th = tab_hi[j], tl = tab_lo[j];
+    const float uh = th * ph;
+    const float ul = fmaf(th, ph, -uh) + (th * pl + tl * ph);
+    float hh, hl;
+    two_sum_f(th, uh, hh, hl);
+    hl += tl + ul;
+    const float sc = __int_as_float((m + 127) << 23);
+    return (double)(hh * sc) + (double)(hl * sc);
+}
+
+template <int NT> __device__ float block_max_f(float v, float *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float t = red[0];
+    for (int q = 1; q < NT / 32; ++q) t = fmaxf(t, red[q]);
+    return t;
+}
+
 __global__ void __launch_bounds__(kPartialThreads) partial_kernel(const ReduceLayout L, Partial *out)
 {
-    // One pass over the replica's samples (x read once): every thread keeps
-    // its own minimum m_t of w and S_t = sum exp(-(w - m_t)/kT), rescaled on
-    // the rare occasions the minimum drops, and plain sums of (x - lambda_i)
-    // and its square (a few terms per thread, then a tree over the threads:
-    // rounding stays near 1e-15 relative without per-term compensation).
-    // The FP64 unit, not HBM, bounds this kernel on GB300 (one FP64 exp per
-    // sample), so the single pass halves its FP64 work as well as its reads.
+    // Two passes over the replica's samples (the second mostly from cache):
+    // the extreme x that minimises w, then per thread the exponential sum
+    // (terms by exp_ff) and the sums of (x - lambda_i) and its square in
+    // FP64, then trees over the threads.
     __shared__ double red[kPartialThreads / 32 + 1];
+    __shared__ float redf[kPartialThreads / 32];
+    __shared__ float tab_hi[32], tab_lo[32];
     const int w = blockIdx.x, r = blockIdx.y;
     const long long T = L.tw[w];
     const float *x = L.x + L.off_w[w] + (long long)r * T;
     const double li = L.lambda[w];
     const double ln = (w + 1 < L.n_windows) ? L.lambda[w + 1] : li;
     const double hkd = 0.5 * L.k * (ln - li), ssum = ln + li, beta = 1.0 / L.kT;
-    double m = INFINITY, S = 0, s1 = 0, s2 = 0;
-    for (long long t = threadIdx.x; t < T; t += kPartialThreads) {
-        const double xv = (double)x[t];
-        const double wv = hkd * (ssum - 2.0 * xv);
-        if (wv < m) {  // new minimum: the terms so far shrink by exp(-(m - wv)/kT)
-            S = (m == INFINITY ? 0.0 : S * exp((wv - m) * beta)) + 1.0;
-            m = wv;
-        } else {
-            S += exp((m - wv) * beta);
-        }
-        const double d = xv - li;
-        s1 += d;
-        s2 += d * d;
+    if (threadIdx.x < 32) {
+        const double t = exp2((double)threadIdx.x / 32.0);
+        tab_hi[threadIdx.x] = (float)t;
+        tab_lo[threadIdx.x] = (float)(t - (double)(float)t);
     }
-    const double mb = block_min<kPartialThreads>(m, red);
-    const double St = m == INFINITY ? 0.0 : S * exp((mb - m) * beta);  // onto the replica's minimum
-    const double Sb = block_sum<kPartialThreads>(St, red);
+    if (T == 0) {
+        if (threadIdx.x == 0) out[(size_t)w * L.replicas + r] = Partial{INFINITY, 0.0, 0.0, 0.0, 0.0};
+        return;
+    }
+    // x_ref: the largest x if w falls with x (hkd > 0), else the smallest
+    const float sgn = hkd < 0 ? -1.f : 1.f;
+    float mx = -INFINITY;
+    for (long long t = threadIdx.x; t < T; t += kPartialThreads) mx = fmaxf(mx, sgn * x[t]);
+    const float xref = sgn * block_max_f<kPartialThreads>(mx, redf);  // also orders the table writes
+    const double c = 2.0 * hkd * beta;
+    const float ch = (float)c, cl = (float)(c - (double)ch);
+    const ExpConsts k = exp_consts();
+    double S = 0, s1 = 0, s2 = 0;
+    for (long long t = threadIdx.x; t < T; t += kPartialThreads) {
+        const float xv = x[t];
+        float dh, dl;
+        two_sum_f(xv, -xref, dh, dl);  // x - x_ref exactly
+        float ah = ch * dh;
+        float al = fmaf(ch, dh, -ah) + (ch * dl + cl * dh);
+        fast_two_sum_f(ah, al, ah, al);
+        S += exp_ff(ah, al, k, tab_hi, tab_lo);
+        const double d = (double)xv - li;
+        s1 += d;
+        s2 = fma(d, d, s2);
+    }
+    const double Sb = block_sum<kPartialThreads>(S, red);
     const double sdx = block_sum<kPartialThreads>(s1, red);
     const double sdx2 = block_sum<kPartialThreads>(s2, red);
+    // the minimum of w, taken at x_ref, in the FP64 form of Eq. (9)
+    const double mb = hkd * (ssum - 2.0 * (double)xref);
     if (threadIdx.x == 0) out[(size_t)w * L.replicas + r] = Partial{mb, Sb, (double)T, sdx, sdx2};
 }
 

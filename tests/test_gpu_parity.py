@@ -137,6 +137,31 @@ def test_reduction_parity(pmf, s, R, T):
     _compare_profiles(g, o, kT)
 
 
+@pytest.mark.parametrize("case", ["decreasing", "wide", "flat_step", "sign_change"])
+def test_reduction_exponent_range(pmf, case):
+    """The stage-1 exponential on the FP32 pipe against the oracle's FP64
+    one, <= 1e-12 relative: a path pulled towards smaller lambda (the
+    minimum of w at the smallest x), samples spread so far beyond the trap's
+    width that exponents pass -80 (those terms are dropped), two equal
+    neighbouring centres (w = 0 for every sample), and samples on both
+    sides of zero."""
+    g = np.random.default_rng(["decreasing", "wide", "flat_step", "sign_change"].index(case) + 77)
+    R, T = 6, 700
+    kT = inputs.kT_of(300.0)
+    if case == "decreasing":
+        lam, k, sd = inputs.lambda_grid(3.3, 1.3, 11), 500.0, 0.07
+    elif case == "wide":
+        lam, k, sd = inputs.lambda_grid(1.3, 2.3, 11), 20000.0, 0.05
+    elif case == "flat_step":
+        lam, k, sd = np.array([1.3, 1.5, 1.5, 1.7, 1.9]), 500.0, 0.07
+    else:
+        lam, k, kT, sd = inputs.lambda_grid(-1.5, 1.5, 9), 20.0, 1.0, 0.3
+    x = (lam[:, None, None] + sd * g.standard_normal((lam.size, R, T))).astype(np.float32)
+    gpu = pmf.pmf_free_energy_from_samples(x.ravel(), lam, R, [T] * lam.size, k, kT)
+    o = est.free_energy_profile([x[i].astype(np.float64) for i in range(lam.size)], lam, k, kT)
+    _compare_profiles(gpu, o, kT)
+
+
 @pytest.mark.parametrize("R", [300, 16384, 20000])
 def test_combination_many_replicas(pmf, R):
     """The per-window combination and its delete-one-replica jackknife on

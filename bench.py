@@ -142,15 +142,17 @@ def samples_per_replica(run):
 
 def _reduction_roofline(ms, n_samples, peaks, fp64_tflops):
     """The reductions of one step against HBM (4 bytes of x per sample, read
-    once by each of stage 1's two passes) and beside the measured FP64 rate:
-    the exponentials run in double-float arithmetic on the FP32 pipe, the
-    per-sample FP64 sums keep stage 1 FP64-bound on this GPU."""
+    by each of stage 1's two passes) and beside the measured FP64 rate:
+    stage 1 forms its exponentials and per-thread sums in double-float
+    arithmetic on the FP32 pipe; three dependent launches of a few tens of
+    microseconds, not HBM, bound the whole."""
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     gbs = 4.0 * n_samples / (ms * 1e-3) / 1e9
     return {"kernels": "partial_kernel, window_kernel, profile_kernel", "ms": ms, "samples": n_samples,
-            "bound": "fp64", "achieved_gbs": gbs, "hbm_peak_gbs": hbm, "hbm_frac": gbs / hbm,
+            "bound": "latency", "achieved_gbs": gbs, "hbm_peak_gbs": hbm, "hbm_frac": gbs / hbm,
             "ns_per_sample": ms * 1e6 / n_samples, "fp64_tflops_measured": fp64_tflops,
-            "note": "double-float exponentials on the FP32 pipe; the FP64 sums per sample, not HBM, bound stage 1"}
+            "note": "stage 1 in double-float arithmetic on the FP32 pipe (FP64 per flush of 16 samples and in the "
+                    "block trees); three dependent launches, not HBM, bound the reduction"}
 
 
 def cpu_baseline(budget_s=12.0, n_steps=200, single_thread=True):

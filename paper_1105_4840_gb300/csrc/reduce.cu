@@ -89,7 +89,7 @@ constexpr int kPartialThreads = 256;
 // ln2/32 split in three floats whose first has 12 significant bits so that
 // n times it is exact.  The relative error of a term, weighted by its size,
 // stays near 1e-14; terms below e^-80 of the largest are dropped (the largest
-// is 1).  The sums over the samples stay in FP64.
+// is 1).
 
 __device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e)
 {
@@ -123,11 +123,15 @@ __device__ __forceinline__ ExpConsts exp_consts()
     return k;
 }
 
-// exp(ah + al) for ah + al <= 0 (tab: 2^(j/32) = tab_hi[j] + tab_lo[j]).
-__device__ __forceinline__ double exp_ff(float ah, float al, const ExpConsts &k, const float *tab_hi,
-                                         const float *tab_lo)
+// exp(ah + al) for ah + al <= 0 as a pair of floats eh + el (tab: 2^(j/32)
+// = tab_hi[j] + tab_lo[j]).
+__device__ __forceinline__ void exp_ff(float ah, float al, const ExpConsts &k, const float *tab_hi,
+                                       const float *tab_lo, float &eh, float &el)
 {
-    if (ah < -80.f) return 0.0;
+    if (ah < -80.f) {
+        eh = el = 0.f;
+        return;
+    }
     const float kf = rintf(ah * k.inv_l);
     const int n = (int)kf;
     // r = a - n ln2/32: n l1 is exact and close to ah, n l2 exact as p2 + e2
@@ -155,8 +159,24 @@ __device__ __forceinline__ double exp_ff(float ah, float al, const ExpConsts &k,
     two_sum_f(th, uh, hh, hl);
     hl += tl + ul;
     const float sc = __int_as_float((m + 127) << 23);
-    return (double)(hh * sc) + (double)(hl * sc);
+    eh = hh * sc;
+    el = hl * sc;
 }
+
+// (h, l) += (bh, bl) in double-float arithmetic.
+__device__ __forceinline__ void ff_add(float &h, float &l, float bh, float bl)
+{
+    float s, e;
+    two_sum_f(h, bh, s, e);
+    e += l + bl;
+    fast_two_sum_f(s, e, h, l);
+}
+
+// Per-thread sums kept as pairs of floats and flushed into FP64 every
+// kFlushSamples terms: within a flush the pair's error stays near
+// kFlushSamples x 2^-47 of the partial sum, and the FP64 unit does a few
+// operations per flush instead of several per sample.
+constexpr int kFlushSamples = 16;
 
 template <int NT> __device__ float block_max_f(float v, float *red)
 {
@@ -170,39 +190,63 @@ template <int NT> __device__ float block_max_f(float v, float *red)
     return t;
 }
 
+// Per-window constants of stage 1, set once per CTA by one thread (the FP64
+// unit is the scarce one: per-thread setup in FP64 would cost more than the
+// samples themselves at a few samples per thread).
+struct WindowConsts {
+    double hkd, ssum;       // w = hkd (ssum - 2 x)
+    float ch, cl;           // c = 2 hkd / kT as a pair of floats
+    float li_h, li_m, li_l; // lambda_i as three floats
+    float sgn;              // +1: x_ref is the largest x, -1: the smallest
+    ExpConsts k;
+};
+
 __global__ void __launch_bounds__(kPartialThreads) partial_kernel(const ReduceLayout L, Partial *out)
 {
     // Two passes over the replica's samples (the second mostly from cache):
     // the extreme x that minimises w, then per thread the exponential sum
-    // (terms by exp_ff) and the sums of (x - lambda_i) and its square in
-    // FP64, then trees over the threads.
+    // (terms by exp_ff) and the sums of (x - lambda_i) and its square as
+    // pairs of floats flushed into FP64, then trees over the threads.
     __shared__ double red[kPartialThreads / 32 + 1];
     __shared__ float redf[kPartialThreads / 32];
     __shared__ float tab_hi[32], tab_lo[32];
+    __shared__ WindowConsts wc;
     const int w = blockIdx.x, r = blockIdx.y;
     const long long T = L.tw[w];
     const float *x = L.x + L.off_w[w] + (long long)r * T;
-    const double li = L.lambda[w];
-    const double ln = (w + 1 < L.n_windows) ? L.lambda[w + 1] : li;
-    const double hkd = 0.5 * L.k * (ln - li), ssum = ln + li, beta = 1.0 / L.kT;
     if (threadIdx.x < 32) {
         const double t = exp2((double)threadIdx.x / 32.0);
         tab_hi[threadIdx.x] = (float)t;
         tab_lo[threadIdx.x] = (float)(t - (double)(float)t);
+    } else if (threadIdx.x == 32) {
+        const double li = L.lambda[w];
+        const double ln = (w + 1 < L.n_windows) ? L.lambda[w + 1] : li;
+        wc.hkd = 0.5 * L.k * (ln - li);
+        wc.ssum = ln + li;
+        const double c = 2.0 * wc.hkd / L.kT;
+        wc.ch = (float)c;
+        wc.cl = (float)(c - (double)wc.ch);
+        wc.li_h = (float)li;
+        wc.li_m = (float)(li - (double)wc.li_h);
+        wc.li_l = (float)((li - (double)wc.li_h) - (double)wc.li_m);
+        wc.sgn = wc.hkd < 0 ? -1.f : 1.f;
+        wc.k = exp_consts();
     }
     if (T == 0) {
         if (threadIdx.x == 0) out[(size_t)w * L.replicas + r] = Partial{INFINITY, 0.0, 0.0, 0.0, 0.0};
         return;
     }
+    __syncthreads();
     // x_ref: the largest x if w falls with x (hkd > 0), else the smallest
-    const float sgn = hkd < 0 ? -1.f : 1.f;
+    const float sgn = wc.sgn;
     float mx = -INFINITY;
     for (long long t = threadIdx.x; t < T; t += kPartialThreads) mx = fmaxf(mx, sgn * x[t]);
-    const float xref = sgn * block_max_f<kPartialThreads>(mx, redf);  // also orders the table writes
-    const double c = 2.0 * hkd * beta;
-    const float ch = (float)c, cl = (float)(c - (double)ch);
-    const ExpConsts k = exp_consts();
+    const float xref = sgn * block_max_f<kPartialThreads>(mx, redf);
+    const float ch = wc.ch, cl = wc.cl, li_h = wc.li_h, li_m = wc.li_m, li_l = wc.li_l;
+    const ExpConsts k = wc.k;
     double S = 0, s1 = 0, s2 = 0;
+    float Sh = 0, Sl = 0, ah1 = 0, al1 = 0, ah2 = 0, al2 = 0;
+    int cnt = 0;
     for (long long t = threadIdx.x; t < T; t += kPartialThreads) {
         const float xv = x[t];
         float dh, dl;
@@ -210,17 +254,34 @@ __global__ void __launch_bounds__(kPartialThreads) partial_kernel(const ReduceLa
         float ah = ch * dh;
         float al = fmaf(ch, dh, -ah) + (ch * dl + cl * dh);
         fast_two_sum_f(ah, al, ah, al);
-        S += exp_ff(ah, al, k, tab_hi, tab_lo);
-        const double d = (double)xv - li;
-        s1 += d;
-        s2 = fma(d, d, s2);
+        float eh, el;
+        exp_ff(ah, al, k, tab_hi, tab_lo, eh, el);
+        ff_add(Sh, Sl, eh, el);
+        // d = x - lambda_i: x - li_h exactly, then the rest of lambda_i
+        float qh, ql;
+        two_sum_f(xv, -li_h, qh, ql);
+        ff_add(qh, ql, -li_m, -li_l);
+        ff_add(ah1, al1, qh, ql);
+        const float ph = qh * qh;
+        const float pl = fmaf(qh, qh, -ph) + 2.f * qh * ql;
+        ff_add(ah2, al2, ph, pl);
+        if (++cnt == kFlushSamples) {
+            S += (double)Sh + (double)Sl;
+            s1 += (double)ah1 + (double)al1;
+            s2 += (double)ah2 + (double)al2;
+            Sh = Sl = ah1 = al1 = ah2 = al2 = 0.f;
+            cnt = 0;
+        }
     }
+    S += (double)Sh + (double)Sl;
+    s1 += (double)ah1 + (double)al1;
+    s2 += (double)ah2 + (double)al2;
     const double Sb = block_sum<kPartialThreads>(S, red);
     const double sdx = block_sum<kPartialThreads>(s1, red);
     const double sdx2 = block_sum<kPartialThreads>(s2, red);
     // the minimum of w, taken at x_ref, in the FP64 form of Eq. (9)
-    const double mb = hkd * (ssum - 2.0 * (double)xref);
-    if (threadIdx.x == 0) out[(size_t)w * L.replicas + r] = Partial{mb, Sb, (double)T, sdx, sdx2};
+    if (threadIdx.x == 0)
+        out[(size_t)w * L.replicas + r] = Partial{wc.hkd * (wc.ssum - 2.0 * (double)xref), Sb, (double)T, sdx, sdx2};
 }
 
 constexpr int kWindowThreads = 256;

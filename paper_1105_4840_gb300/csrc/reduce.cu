@@ -426,40 +426,77 @@ __global__ void __launch_bounds__(kWindowThreads) window_kernel(const ReduceLayo
     }
 }
 
-__global__ void profile_kernel(const ReduceLayout L, const WindowOut *wo, double *out)
+// Stage 3: the profiles are prefix sums over the windows of the per-window
+// increments (and a prefix minimum of the sample counts); one CTA scans them
+// kProfileThreads windows at a time (warp shuffles, then the warps' totals),
+// carrying the running totals from one chunk to the next, and every thread
+// writes its window's fields.
+constexpr int kProfileThreads = 256;
+constexpr int kProfileSums = 7;  // je, fl, g, wmean, jk_je, jk_fl, varw
+
+__global__ void __launch_bounds__(kProfileThreads) profile_kernel(const ReduceLayout L, const WindowOut *wo,
+                                                                  double *out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int s = L.n_windows;
-    double *f[kResFields];
-    for (int q = 0; q < kResFields; ++q) f[q] = out + (size_t)q * s;
-    double je = 0, fl = 0, g = 0, wm = 0, vje = 0, vfl = 0, vw = 0, Q = INFINITY;
-    for (int j = 0; j < s; ++j) {
-        if (j > 0) {
+    __shared__ double wsum[kProfileThreads / 32][kProfileSums + 1];
+    __shared__ double carry[kProfileSums + 1];
+    const int s = L.n_windows, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid <= kProfileSums) carry[tid] = tid < kProfileSums ? 0.0 : INFINITY;
+    __syncthreads();
+    for (int base = 0; base < s; base += kProfileThreads) {
+        const int j = base + tid;
+        // window j's own terms: the increment of the pair (j - 1, j)
+        double v[kProfileSums + 1];
+        if (j > 0 && j < s) {
             const WindowOut &o = wo[j - 1];
-            je += o.je;
-            fl += o.fl;
-            g += o.g;
-            wm += o.wmean;
-            vje += o.jk_je;
-            vfl += o.jk_fl;
-            vw += o.varw;
-            Q = fmin(Q, o.n);
+            v[0] = o.je; v[1] = o.fl; v[2] = o.g; v[3] = o.wmean; v[4] = o.jk_je; v[5] = o.jk_fl; v[6] = o.varw;
+            v[7] = o.n;
+        } else {
+            for (int q = 0; q < kProfileSums; ++q) v[q] = 0.0;
+            v[kProfileSums] = INFINITY;
         }
-        const double lam = L.lambda[j];
-        f[kResLambda][j] = lam;
-        f[kResJE][j] = je;
-        f[kResFluct][j] = fl;
-        f[kResG][j] = g;
-        f[kResCom][j] = 0.5 * (je + fl);
-        f[kResUnc][j] = 0.5 * (je - fl);
-        f[kResSeJE][j] = j > 0 ? sqrt(vje) : 0.0;
-        f[kResSeFluct][j] = j > 0 ? sqrt(vfl) : 0.0;
-        f[kResVarZW][j] = (j > 0 && Q > 1) ? vw / Q + vw * vw / (2.0 * L.kT * L.kT * (Q - 1.0)) : (j > 0 ? NAN : 0.0);
-        f[kResWMean][j] = wm;
-        f[kResAccForce][j] = j > 0 ? fl / (lam - L.lambda[0]) : 0.0;
-        f[kResMeanX][j] = wo[j].mean;
-        f[kResVarX][j] = wo[j].var;
-        f[kResGamma2][j] = L.k * wo[j].var / L.kT;
+        // inclusive scan inside the warp
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int q = 0; q <= kProfileSums; ++q) {
+                const double u = __shfl_up_sync(0xffffffffu, v[q], o);
+                if (lane >= o) v[q] = q < kProfileSums ? v[q] + u : fmin(v[q], u);
+            }
+        }
+        if (lane == 31)
+            for (int q = 0; q <= kProfileSums; ++q) wsum[warp][q] = v[q];
+        __syncthreads();
+        // add the earlier warps' totals and the carry of the earlier chunks
+        double pre[kProfileSums + 1];
+        for (int q = 0; q <= kProfileSums; ++q) pre[q] = carry[q];
+        for (int w = 0; w < warp; ++w)
+            for (int q = 0; q <= kProfileSums; ++q)
+                pre[q] = q < kProfileSums ? pre[q] + wsum[w][q] : fmin(pre[q], wsum[w][q]);
+        for (int q = 0; q <= kProfileSums; ++q) v[q] = q < kProfileSums ? pre[q] + v[q] : fmin(pre[q], v[q]);
+        if (j < s) {
+            double *f[kResFields];
+            for (int q = 0; q < kResFields; ++q) f[q] = out + (size_t)q * s;
+            const double je = v[0], fl = v[1], Q = v[7];
+            const double lam = L.lambda[j];
+            f[kResLambda][j] = lam;
+            f[kResJE][j] = je;
+            f[kResFluct][j] = fl;
+            f[kResG][j] = v[2];
+            f[kResCom][j] = 0.5 * (je + fl);
+            f[kResUnc][j] = 0.5 * (je - fl);
+            f[kResSeJE][j] = j > 0 ? sqrt(v[4]) : 0.0;
+            f[kResSeFluct][j] = j > 0 ? sqrt(v[5]) : 0.0;
+            f[kResVarZW][j] = (j > 0 && Q > 1) ? v[6] / Q + v[6] * v[6] / (2.0 * L.kT * L.kT * (Q - 1.0))
+                                               : (j > 0 ? NAN : 0.0);
+            f[kResWMean][j] = v[3];
+            f[kResAccForce][j] = j > 0 ? fl / (lam - L.lambda[0]) : 0.0;
+            f[kResMeanX][j] = wo[j].mean;
+            f[kResVarX][j] = wo[j].var;
+            f[kResGamma2][j] = L.k * wo[j].var / L.kT;
+        }
+        __syncthreads();  // every thread has read carry and wsum
+        if (tid == kProfileThreads - 1)
+            for (int q = 0; q <= kProfileSums; ++q) carry[q] = v[q];
+        __syncthreads();
     }
 }
 
@@ -609,7 +646,7 @@ cudaError_t combine_launch(const ReduceLayout &L, const void *P, void *window_sc
         window_kernel<false><<<L.n_windows, kWindowThreads, 0, st>>>(L, pp, wo);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    profile_kernel<<<1, 32, 0, st>>>(L, wo, out);
+    profile_kernel<<<1, kProfileThreads, 0, st>>>(L, wo, out);
     return cudaGetLastError();
 }
 
